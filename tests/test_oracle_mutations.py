@@ -1,0 +1,96 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a temporary copy of ``oracle/bte_oracle.c``
+(on the CPU), builds it, and checks that the battery of pins used by
+``test_oracle_pins.py`` / ``test_oracle_adjoint.py`` rejects it.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import bte_inputs as bi
+import oracle
+import oracle.dense as dense
+from tests import physics
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "bte_oracle.c")
+
+MUTATIONS = {
+    "source_without_4pi": ("p->phi[c] / (FOUR_PI * Csum);", "p->phi[c] / Csum;"),
+    "collision_sign": ("double rhs = p->C[b] * T[c] / (FOUR_PI * tc)",
+                       "double rhs = -p->C[b] * T[c] / (FOUR_PI * tc)"),
+    "temperature_without_tau": ("num += acc / tc;", "num += acc;"),
+    "upwind_side_swapped": ("> 0.0) ? 2 * a : 2 * a + 1;", "> 0.0) ? 2 * a + 1 : 2 * a;"),
+    "diffuse_from_incoming": ("if (sn > 0.0) acc += p->w[d] * sn * E(e_old",
+                              "if (sn < 0.0) acc += p->w[d] * sn * E(e_old"),
+    "diffuse_norm_pi": ("return acc / diffuse_norm(p, side);\n}\n\n/* One exact",
+                        "return acc / M_PI;\n}\n\n/* One exact"),
+    "coef_without_velocity": ("double coef = p->v[b] * fabs(sa) / p->h[a];   /* v|s.n| S / V */",
+                              "double coef = fabs(sa) / p->h[a];"),
+    "coef_wrong_axis": ("double coef = p->v[b] * fabs(sa) / p->h[a];   /* v|s.n| S / V */",
+                        "double coef = p->v[b] * fabs(sa) / p->h[0];"),
+    "adjoint_source_without_weight": ("double rhs = p->w[d] * Th[c] / tc;",
+                                      "double rhs = Th[c] / tc;"),
+    "adjoint_without_diffuse": ("rhs += p->w[d] * fabs(sa) * adj_diffuse_sum",
+                                "rhs += 0.0 * adj_diffuse_sum"),
+    "tau_gradient_sign": ("g_tau[b] += acc / (tc * p->tau[b]);",
+                          "g_tau[b] -= acc / (tc * p->tau[b]);"),
+    "theta_without_capacity": ("acc += p->C[b] / (FOUR_PI * tau_cb(p, c, b)) * sm;",
+                               "acc += 1.0 / (FOUR_PI * tau_cb(p, c, b)) * sm;"),
+}
+
+
+def _battery(lib):
+    """Run the pins against a build; return the names of those that fail."""
+    failed = []
+    # ballistic closed form
+    p = bi.gray_slab(nx=20, tau=1e3)
+    r = oracle.solve(p, max_iter=50, tol=1e-14, lib=lib)
+    mu = p.s[:, 0]
+    qd = p.C[0] * p.v[0] * 2.0 / (4 * np.pi) * np.sum(p.w[mu > 0] * mu[mu > 0])
+    if not (np.allclose(r["T"], 300.0, rtol=1e-12) and np.allclose(r["q"][:, 0], qd, rtol=1e-10)):
+        failed.append("ballistic")
+    # iteration vs direct solve, energy balance, adjoint on masked cases
+    for dim, kw in [(2, dict(n=(5, 4, 1), B=3, masked=True, diffuse=(2, 3), source=True,
+                             two_regions=True)),
+                    (3, dict(n=(4, 3, 3), B=2, masked=True, diffuse=(0, 3, 5), source=True,
+                             two_regions=True))]:
+        p = bi.tiny(dim, **kw)
+        sysm = dense.System(p)
+        ref = sysm.solve()
+        r = oracle.solve(p, max_iter=20000, tol=1e-15, lib=lib)
+        act = p.mask > 0
+        if not np.allclose(r["T"][act], ref["T"][act], rtol=1e-11, atol=0):
+            failed.append(f"direct{dim}")
+        out, per_face = physics.boundary_outflow(p, r["e"])
+        if not abs(out - physics.heat_input(p)) < 1e-9 * np.abs(per_face).sum():
+            failed.append(f"energy{dim}")
+        rng = np.random.default_rng(3)
+        probes = np.sort(rng.choice(np.flatnonzero(act), 4, replace=False))
+        T_obs = ref["T"][probes] - 1.0
+        g = np.zeros(p.n_cells)
+        np.add.at(g, probes, ref["T"][probes] - T_obs)
+        a = oracle.adjoint(p, ref["e"], ref["T"], g, max_iter=20000, tol=1e-15, lib=lib)
+        fd = dense.fd_gradients(p, probes, T_obs)
+        ok = (np.allclose(a["g_tau"], fd["g_tau"], rtol=1e-4)
+              and np.allclose(a["g_Tw"], fd["g_Tw"], rtol=1e-4, atol=1e-8)
+              and abs(a["g_Q"] - fd["g_Q"]) <= 1e-4 * abs(fd["g_Q"]))
+        if not ok:
+            failed.append(f"adjoint{dim}")
+    return failed
+
+
+def test_unmutated_oracle_passes_battery():
+    assert _battery(oracle.load_library(oracle.build())) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib = oracle.load_library(oracle.compile_c(str(path), str(tmp_path / "mutant.so")))
+    assert _battery(lib), f"planted mistake {name} was not detected"
