@@ -1,0 +1,213 @@
+/*
+ * libbte -- steady nongray phonon Boltzmann transport (relaxation-time
+ * approximation) on a masked Cartesian grid, solved on one GB300 GPU.
+ *
+ * Method (arXiv 2503.23657, Methods section):
+ *   - Eq. (bte-2): v_b s.grad e_bs = -(e_bs - e0_b)/tau_b + Q_b, the RTA sign
+ *     of the discretised equation (the first statement of the BTE in the
+ *     paper prints the collision term with the opposite sign);
+ *   - Eq. (updatee0_t): e0_b = C_b T/(4 pi), T = sum_b sum_s w_s e_bs/tau_b
+ *     divided by sum_b C_b/tau_b;
+ *   - Eq. (fvm-1) with first-order (step) upwind face values, i.e. the
+ *     matrix A of Eq. (A_matrix) (face area S_ij included off the diagonal);
+ *   - boundary conditions of the "Boundary conditions" subsection:
+ *     isothermal walls and diffusely reflecting walls; faces between solid
+ *     and void cells reflect diffusely;
+ *   - the per-band source Q_b = C_b Q / (4 pi sum_b C_b) per steradian;
+ *   - the outer iteration of the solution procedure (Methods, steps 1-4)
+ *     with the convergence criterion eps_T of the same list.
+ * Each (band, direction) transport problem is solved exactly by an upwind
+ * wavefront sweep (A is triangular in sweep order on a Cartesian grid), so
+ * the paper's incremental pseudo-time update reduces to source iteration.
+ * The diffuse inflow of one iteration uses the previous iterate's outgoing
+ * energy; the converged fixed point is unchanged.
+ *
+ * Conventions shared by every entry point
+ *   - cells c = i + nx*(j + ny*k), x fastest; N = nx*ny*nz;
+ *   - domain faces 0:x- 1:x+ 2:y- 3:y+ 4:z- 5:z+ (faces of axes >= dim are
+ *     ignored);
+ *   - e is laid out [cell][band][direction] with the directions in the
+ *     caller's order;
+ *   - all floating-point inputs are FP64; the solver sweeps in FP32 or FP64
+ *     (bte_solve_opts.precision) and always reduces T, residuals and
+ *     gradients in FP64.
+ *
+ * Ownership: bte_create copies every input (host memory); the caller may
+ * free them on return.  Output buffers are caller-owned and may be host or
+ * device memory (detected per pointer).  The plan owns its device memory.
+ *
+ * Errors: every int-returning call returns BTE_OK (0) or a negative code
+ * below; bte_last_error() describes the last failure of a plan.  Nothing
+ * aborts, traps or exits the process.  Device-side waits are bounded and
+ * report BTE_ETIMEOUT instead of hanging.
+ *
+ * Threading: a plan is not thread-safe; use one plan per host thread.
+ */
+#ifndef BTE_H
+#define BTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BTE_OK 0
+#define BTE_EINVAL (-1)        /* invalid argument (see bte_last_error) */
+#define BTE_ENOMEM (-2)        /* host or device allocation failed */
+#define BTE_ECUDA (-3)         /* CUDA runtime error */
+#define BTE_ENOTCONVERGED (-4) /* max_iter reached; outputs hold the last iterate */
+#define BTE_ETIMEOUT (-5)      /* a bounded device-side wait expired */
+#define BTE_ENUMERIC (-6)      /* NaN/Inf in the temperature update */
+#define BTE_ESTATE (-7)        /* call order violated (e.g. adjoint before solve) */
+
+#define BTE_BC_ISOTHERMAL 0
+#define BTE_BC_DIFFUSE 1
+
+#define BTE_FP32 0
+#define BTE_FP64 1
+
+typedef struct bte_plan bte_plan; /* opaque, library-owned */
+
+/* Grid: dim in {1,2,3}; n[a] cells and length[a] metres per axis; axes
+ * a >= dim must have n[a] == 1 (their length is a unit depth). */
+typedef struct {
+    int dim;
+    int n[3];
+    double length[3];
+} bte_grid;
+
+/* Band table (Methods, band discretisation): B bands with heat capacity
+ * C[b] J/(m^3 K) > 0, group speed v[b] m/s > 0, relaxation time tau[b] s > 0;
+ * R regions, region r (mask value r+1) uses tau[b]*tau_scale[r] (> 0). */
+typedef struct {
+    int B;
+    const double *C;
+    const double *v;
+    const double *tau;
+    int R;
+    const double *tau_scale;
+} bte_bands;
+
+/* Discrete ordinates (Methods, angle discretisation): D unit vectors
+ * s[3*d+a] and weights w[d] > 0 with sum w = 4 pi (checked to 1e-10). */
+typedef struct {
+    int D;
+    const double *s;
+    const double *w;
+} bte_quad;
+
+/* Per domain face: type BTE_BC_ISOTHERMAL (wall temperature T[f], K) or
+ * BTE_BC_DIFFUSE.  At least one isothermal face must touch the solid. */
+typedef struct {
+    int type[6];
+    double T[6];
+} bte_bcs;
+
+/*
+ * bte_create -- validate the problem, build the sweep plan, copy the inputs
+ * to the device.
+ *   mask      N bytes, 0 = void, r >= 1 = solid of region r (r <= R)
+ *   q_profile N doubles, W/m^3 per unit source amplitude, or NULL (no source)
+ *   out       receives the plan (NULL on failure)
+ * Returns BTE_OK, BTE_EINVAL (bad sizes, sum w != 4 pi, tau <= 0, mask value
+ * > R, no isothermal face touching the solid), BTE_ENOMEM or BTE_ECUDA.
+ * Uses the current CUDA device.  On failure nothing is leaked.
+ */
+int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands,
+               const bte_quad *quad, const bte_bcs *bcs, const double *q_profile,
+               bte_plan **out);
+
+typedef struct {
+    int precision;          /* BTE_FP32 (FP32 sweeps, FP64 reductions) or BTE_FP64 */
+    double tol;             /* stop when eps_T < tol; tol <= 0 runs exactly max_iter */
+    int max_iter;           /* > 0 */
+    const double *T_init;   /* N doubles (host or device) or NULL */
+    double T_init_uniform;  /* used when T_init == NULL (K, > 0) */
+    double Q_amp;           /* source amplitude multiplying q_profile */
+    const double *tau;      /* B overrides of bands->tau (host), or NULL */
+    const double *T_wall;   /* 6 overrides of bcs->T (host), or NULL */
+    void *stream;           /* cudaStream_t to run on (NULL = legacy default) */
+    int poll_every;         /* iterations per device->host convergence poll (0 = auto) */
+    int dirs_per_lane;      /* sweep tile: directions held per lane (0 = autotuned) */
+    int store_e_every_iter; /* 1: write e to HBM on every sweep; 0: only the final one */
+} bte_solve_opts;
+
+typedef struct {
+    int iterations;         /* outer iterations run */
+    int converged;          /* eps_T < tol reached */
+    double eps_T;           /* last eps_T (Methods, convergence criterion) */
+    double T_max;           /* max T of the last iterate (K) */
+    double seconds;         /* device time of the iteration loop */
+    double updates_per_s;   /* iterations * solid cells * B * D / seconds */
+    int dirs_per_lane;      /* tile used */
+    long long kernel_launches; /* kernels launched by the call (incl. early-exit ones) */
+} bte_stats;
+
+/* Fill opts with defaults: FP32, tol 1e-6, max_iter 100000, T_init 300 K,
+ * Q_amp 1, autotuned tile, poll every 16 iterations. */
+void bte_default_opts(bte_solve_opts *o);
+
+/*
+ * bte_solve -- outer source iteration to eps_T < tol (or max_iter).
+ *   T_out  N doubles: final lattice temperature (void cells 0), required
+ *   q_out  3N doubles: heat flux q = sum_b v_b sum_d w_d s_d e of the final
+ *          iterate, or NULL
+ *   e_out  N*B*D values of the final iterate, FP32 if precision is FP32 and
+ *          FP64 otherwise, [cell][band][direction], or NULL
+ *   st     statistics, or NULL
+ * The final e is the iterate from which T_out was computed.  The converged
+ * state is kept in the plan for bte_adjoint.  Returns BTE_OK,
+ * BTE_ENOTCONVERGED (outputs still written), BTE_EINVAL, BTE_ENUMERIC,
+ * BTE_ECUDA.
+ */
+int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, void *e_out,
+              bte_stats *st);
+
+/*
+ * bte_adjoint -- discrete adjoint of the last bte_solve (Forward and inverse
+ * modelling workflow: implicit solves differentiated by a discrete adjoint).
+ * Given dJ/dT (N doubles, host or device) of a loss J(T), solves
+ * (L - P W - R)^T mu = W^T dJ/dT by the transposed (downwind-ordered)
+ * fixed-point iteration and returns
+ *   g_tau[B]   dJ/dtau_b (B doubles, host), or NULL
+ *   g_Twall[6] dJ/dT_f for isothermal domain faces (0 elsewhere), or NULL
+ *   g_Qamp[1]  dJ/dQ_amp, or NULL
+ * tol/max_iter apply to the relative RMS change of the adjoint temperature
+ * Theta.  Runs on the stream of the preceding bte_solve.  Returns BTE_ESTATE
+ * if no solve preceded it.
+ */
+int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau,
+                double *g_Twall, double *g_Qamp, bte_stats *st);
+
+/*
+ * bte_profile_sweep -- time the dominant kernel: `reps` forward sweep
+ * launches (all bands x directions x cells, the tile of the last solve) on
+ * the last solve's state and stream, bracketed by CUDA events after two
+ * untimed launches.  Writes the mean duration of one launch (ms) to
+ * *ms_per_sweep.  The plan's state is not modified.  Returns BTE_ESTATE if
+ * no solve preceded it.
+ */
+int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep);
+
+/* Copy the eps_T history of the last bte_solve (one value per iteration,
+ * at most n, the first 65536 iterations) into out (host).  Returns the
+ * number of values copied or a negative code. */
+int bte_eps_history(const bte_plan *p, double *out, int n);
+
+/* Release every resource of the plan (NULL is a no-op). */
+void bte_destroy(bte_plan *p);
+
+/* Text of the last error on this plan, or of the last failed bte_create
+ * when p is NULL.  Valid until the next call on the same plan. */
+const char *bte_last_error(const bte_plan *p);
+
+/* Library version string. */
+const char *bte_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTE_H */

@@ -1,0 +1,233 @@
+"""ctypes binding of libbte (include/bte.h).
+
+Argument marshalling only: every step of the solve runs in libbte's CUDA
+kernels.  There is no CPU fallback -- ``load()`` raises if the shared
+library is missing or no CUDA device is visible.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbte.so")
+
+BTE_OK = 0
+BTE_EINVAL = -1
+BTE_ENOMEM = -2
+BTE_ECUDA = -3
+BTE_ENOTCONVERGED = -4
+BTE_ETIMEOUT = -5
+BTE_ENUMERIC = -6
+BTE_ESTATE = -7
+BTE_FP32 = 0
+BTE_FP64 = 1
+
+ERROR_NAMES = {
+    BTE_EINVAL: "EINVAL", BTE_ENOMEM: "ENOMEM", BTE_ECUDA: "ECUDA",
+    BTE_ENOTCONVERGED: "ENOTCONVERGED", BTE_ETIMEOUT: "ETIMEOUT",
+    BTE_ENUMERIC: "ENUMERIC", BTE_ESTATE: "ESTATE",
+}
+
+# every entry point declared in include/bte.h
+EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_error",
+           "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep"]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("length", ctypes.c_double * 3)]
+
+
+class Bands(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int), ("C", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("tau", ctypes.c_void_p), ("R", ctypes.c_int), ("tau_scale", ctypes.c_void_p)]
+
+
+class Quad(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("s", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class BCs(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int * 6), ("T", ctypes.c_double * 6)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("T_init", ctypes.c_void_p), ("T_init_uniform", ctypes.c_double),
+                ("Q_amp", ctypes.c_double), ("tau", ctypes.c_void_p), ("T_wall", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p), ("poll_every", ctypes.c_int),
+                ("dirs_per_lane", ctypes.c_int), ("store_e_every_iter", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("eps_T", ctypes.c_double),
+                ("T_max", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("updates_per_s", ctypes.c_double), ("dirs_per_lane", ctypes.c_int),
+                ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbte.so (built in-tree by ``paper_2503_23657_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libbte.so not built ({path}); run paper_2503_23657_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.bte_create.argtypes = [ctypes.POINTER(Grid), vp, ctypes.POINTER(Bands), ctypes.POINTER(Quad),
+                               ctypes.POINTER(BCs), vp, ctypes.POINTER(vp)]
+    lib.bte_create.restype = ip
+    lib.bte_solve.argtypes = [vp, ctypes.POINTER(SolveOpts), vp, vp, vp, ctypes.POINTER(Stats)]
+    lib.bte_solve.restype = ip
+    lib.bte_adjoint.argtypes = [vp, vp, dp, ip, vp, vp, vp, ctypes.POINTER(Stats)]
+    lib.bte_adjoint.restype = ip
+    lib.bte_destroy.argtypes = [vp]
+    lib.bte_destroy.restype = None
+    lib.bte_last_error.argtypes = [vp]
+    lib.bte_last_error.restype = ctypes.c_char_p
+    lib.bte_version.argtypes = []
+    lib.bte_version.restype = ctypes.c_char_p
+    lib.bte_default_opts.argtypes = [ctypes.POINTER(SolveOpts)]
+    lib.bte_default_opts.restype = None
+    lib.bte_eps_history.argtypes = [vp, vp, ip]
+    lib.bte_eps_history.restype = ip
+    lib.bte_profile_sweep.argtypes = [vp, ip, ctypes.POINTER(dp)]
+    lib.bte_profile_sweep.restype = ip
+    _lib = lib
+    return lib
+
+
+class BTEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _addr(x):
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+class Plan:
+    """A libbte plan for one problem (``bte_inputs.Problem`` layout)."""
+
+    def __init__(self, problem):
+        lib = load()
+        p = problem
+        self.problem = p
+        self._keep = dict(
+            mask=np.ascontiguousarray(p.mask, dtype=np.uint8),
+            C=np.ascontiguousarray(p.C, dtype=np.float64),
+            v=np.ascontiguousarray(p.v, dtype=np.float64),
+            tau=np.ascontiguousarray(p.tau, dtype=np.float64),
+            tau_scale=np.ascontiguousarray(p.tau_scale, dtype=np.float64),
+            s=np.ascontiguousarray(p.s, dtype=np.float64).reshape(-1),
+            w=np.ascontiguousarray(p.w, dtype=np.float64),
+            phi=None if p.phi is None else np.ascontiguousarray(p.phi, dtype=np.float64),
+        )
+        k = self._keep
+        g = Grid()
+        g.dim = p.dim
+        for a in range(3):
+            g.n[a] = int(p.n[a])
+            g.length[a] = float(p.length[a])
+        bands = Bands(p.B, _addr(k["C"]), _addr(k["v"]), _addr(k["tau"]), int(k["tau_scale"].size),
+                      _addr(k["tau_scale"]))
+        quad = Quad(p.D, _addr(k["s"]), _addr(k["w"]))
+        bcs = BCs()
+        for f in range(6):
+            bcs.type[f] = int(p.bc_type[f])
+            bcs.T[f] = float(p.bc_T[f])
+        out = ctypes.c_void_p()
+        rc = lib.bte_create(ctypes.byref(g), _addr(k["mask"]), ctypes.byref(bands), ctypes.byref(quad),
+                            ctypes.byref(bcs), _addr(k["phi"]), ctypes.byref(out))
+        if rc != BTE_OK:
+            raise BTEError(rc, lib.bte_last_error(None).decode())
+        self._h = out.value
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bte_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self) -> str:
+        return self._lib.bte_last_error(self._h).decode()
+
+    def solve(self, T_out, q_out=None, e_out=None, precision=BTE_FP32, tol=1e-6, max_iter=100000,
+              T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None,
+              poll_every=32, dirs_per_lane=0, store_e_every_iter=False, check=True):
+        """Run bte_solve.  Buffers are numpy arrays (host) or torch tensors
+        (host or CUDA) of the documented sizes.  Returns (rc, stats dict)."""
+        p = self.problem
+        o = SolveOpts()
+        self._lib.bte_default_opts(ctypes.byref(o))
+        o.precision = precision
+        o.tol = tol
+        o.max_iter = max_iter
+        o.T_init = _addr(T_init)
+        o.T_init_uniform = p.T_init if T_init_uniform is None else T_init_uniform
+        o.Q_amp = p.Q_amp if Q_amp is None else Q_amp
+        tau_a = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
+        tw_a = None if T_wall is None else np.ascontiguousarray(T_wall, dtype=np.float64)
+        o.tau = _addr(tau_a)
+        o.T_wall = _addr(tw_a)
+        o.stream = stream
+        o.poll_every = poll_every
+        o.dirs_per_lane = dirs_per_lane
+        o.store_e_every_iter = 1 if store_e_every_iter else 0
+        st = Stats()
+        rc = self._lib.bte_solve(self._h, ctypes.byref(o), _addr(T_out), _addr(q_out), _addr(e_out),
+                                 ctypes.byref(st))
+        if check and rc not in (BTE_OK,):
+            raise BTEError(rc, self.error())
+        return rc, st.as_dict()
+
+    def adjoint(self, dJ_dT, tol=1e-10, max_iter=100000, check=True):
+        """Run bte_adjoint; returns (rc, g_tau [B], g_Twall [6], g_Qamp, stats)."""
+        p = self.problem
+        g_tau = np.zeros(p.B)
+        g_Tw = np.zeros(6)
+        g_Q = np.zeros(1)
+        st = Stats()
+        rc = self._lib.bte_adjoint(self._h, _addr(dJ_dT), tol, max_iter, _addr(g_tau), _addr(g_Tw),
+                                   _addr(g_Q), ctypes.byref(st))
+        if check and rc != BTE_OK:
+            raise BTEError(rc, self.error())
+        return rc, g_tau, g_Tw, float(g_Q[0]), st.as_dict()
+
+    def profile_sweep(self, reps=20):
+        """Mean duration (ms) of one forward sweep launch (CUDA events)."""
+        ms = ctypes.c_double()
+        rc = self._lib.bte_profile_sweep(self._h, reps, ctypes.byref(ms))
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
+        return ms.value
+
+    def eps_history(self, n):
+        out = np.zeros(n)
+        m = self._lib.bte_eps_history(self._h, _addr(out), n)
+        if m < 0:
+            raise BTEError(m, "eps history")
+        return out[:m]

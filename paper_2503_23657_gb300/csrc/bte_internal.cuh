@@ -1,0 +1,146 @@
+// Internal declarations of libbte: device data layout, kernel parameter
+// blocks and launchers.  Not part of the public C ABI (include/bte.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bte {
+
+// ---------------------------------------------------------------------------
+// cell flags (second word of the per-cell int2; first word = face base index)
+//   bits 0..3  region id (0 = void, r >= 1 solid of region r)
+//   bits 4..9  side s (0:x- 1:x+ 2:y- 3:y+ 4:z- 5:z+) is a boundary face
+//              (outside the domain or next to a void cell)
+// ---------------------------------------------------------------------------
+constexpr int kRegionMask = 0xF;
+constexpr int kSideShift = 4;
+constexpr int kMaxRegions = 15;
+
+__host__ __device__ inline int face_of(int base, int flags, int side) {
+    const unsigned bm = (unsigned)(flags >> kSideShift) & 63u;
+    return base + __builtin_popcount(bm & ((1u << side) - 1u));
+}
+
+// A subset of directions that share one sweep orientation (the signs of the
+// resolved components of s), processed by one CTA per band.
+struct Subset {
+    int d0;    // first internal direction index
+    int cnt;   // number of directions (<= directions per lane)
+    int neg;   // bit a set: traversal runs from high to low index on axis a
+    int pad;
+};
+
+// Parameters of one sweep launch (forward or transposed).  One CTA handles
+// one (subset, band) pair over the whole grid; see sweep.cuh.
+template <typename real>
+struct SweepParams {
+    int nx, ny, nz;
+    int B, D, F, S, R;
+    int WY, WZ;                       // warps along y, warp groups along z
+    long long N;                      // nx*ny*nz
+    const int2 *__restrict__ cell;    // {face base, flags}
+    const real *__restrict__ tsrc;    // fwd: T - T_ref; adj: Theta   [N]
+    const real *__restrict__ phi;     // fwd source profile [N] or null
+    const real *__restrict__ ein;     // [B][F] boundary values
+    real *__restrict__ part;          // [S][B][N] per-subset reduction
+    real *__restrict__ fsum;          // [S][B][F] per-subset face sums
+    real *__restrict__ e;             // [N][B][D] store (fwd) / read (adj)
+    real *__restrict__ gpart;         // [S][B][N] adj: sum_d mu_d e_d
+    const Subset *__restrict__ sub;   // [S]
+    const real *__restrict__ coef;    // [B][D][8]: a_x a_y a_z w ws_x ws_y ws_z pad
+    const real *__restrict__ invdiag; // [R][B][D]
+    const real *__restrict__ srck;    // [R][B]  fwd C_b/(4 pi tau_rb); adj 1/tau_rb
+    const real *__restrict__ qb;      // [B]     fwd Q_b per unit profile
+    const real *__restrict__ tfwd;    // adj + read_e: forward T - T_ref [N]
+    const real *__restrict__ cb4pi;   // adj + read_e: C_b/(4 pi) [B]
+    const int *__restrict__ done;     // early exit when *done != 0 (nullable)
+    int store_e;                      // fwd: write e
+    int read_e;                       // adj: accumulate (mu-w Theta)(e-e0) into gpart
+    int ein_smem;                     // stage this band's boundary values in shared memory
+};
+
+// Temperature (forward) / adjoint-temperature (adjoint) update, FP64.
+template <typename real>
+struct UpdateParams {
+    long long N;
+    int B, S, F, R;
+    int adjoint;
+    double T_ref;
+    const int2 *__restrict__ cell;
+    const Subset *__restrict__ sub;
+    const real *__restrict__ part;    // [S][B][N]
+    const real *__restrict__ fsum;    // [S][B][F]
+    const double *__restrict__ x_in;  // fwd T_old / adj Theta_old [N]
+    double *__restrict__ x_out;       // [N]
+    real *__restrict__ xdev_out;      // fwd T - T_ref / adj Theta, as real [N]
+    const double *__restrict__ g;     // adj: dJ/dT [N]
+    const double *__restrict__ wgt;   // [R][B] fwd 1/tau_rb ; adj C_b/(4 pi tau_rb)
+    const double *__restrict__ Kinv;  // [R]   1 / sum_b C_b/tau_rb
+    const int *__restrict__ face_cell;
+    const int *__restrict__ face_side;
+    const int *__restrict__ face_kind;   // 0 isothermal domain face, 1 diffuse
+    const real *__restrict__ ein_fixed;  // [B][F] isothermal inflow (fwd)
+    real *__restrict__ ein_out;          // [B][F]
+    double *__restrict__ fsum_total;     // [B][F] raw face sums (adj, for gradients) or null
+    const double *__restrict__ side_scale; // [6][B] fwd 1/N_side ; adj h_a/(v_b N_side)
+    // residual bookkeeping
+    double *__restrict__ blockpart;   // [gridDim] x {sum sq, max}
+    unsigned int *__restrict__ counter;
+    int *__restrict__ done;
+    int *__restrict__ iter;
+    double *__restrict__ eps_hist;    // [max_iter] or null
+    double *__restrict__ last;        // {eps, xmax, ss}
+    int *__restrict__ status;
+    double tol;
+    long long n_active;
+    int max_hist;
+    int ignore_done;                  // final replay passes
+};
+
+// Launchers (sweep_*.cu / update.cu).  launch_sweep returns
+// cudaErrorInvalidConfiguration for a (dirs_per_lane, layers_per_lane, 3D)
+// combination that is not instantiated or exceeds the tile's thread limit.
+template <typename real>
+cudaError_t launch_sweep(const SweepParams<real> &p, int dirs_per_lane, int layers_per_lane, bool three_d,
+                         bool adjoint, cudaStream_t st);
+
+// Largest CTA (threads) the sweep tile supports, or 0 if not instantiated.
+int sweep_max_threads(int dirs_per_lane, int layers_per_lane, bool three_d);
+
+template <typename real>
+cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_flux(long long N, int B, int D, const int2 *cell, const real *e,
+                        const double *vws /*[B][D][3] v_b w_d s_d*/, const double *qshift /*[3]*/,
+                        double *q, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_permute_e(long long N, int B, int D, const real *e_int, const int *perm,
+                             const double *shift /*[B]*/, real *e_user, cudaStream_t st);
+
+// Gradient reduction after the final adjoint sweep (all FP64 accumulation).
+template <typename real>
+struct GradParams {
+    long long N;
+    int B, S, F;
+    const int2 *__restrict__ cell;
+    const real *__restrict__ apart;     // [S][B][N] sum_d mu_d
+    const real *__restrict__ gpart;     // [S][B][N] sum_d (mu_d - w_d Theta)(e_d - e0)
+    const double *__restrict__ phi;     // [N] source profile or null
+    const double *__restrict__ inv_tt;  // [R][B] 1/(tau_rb tau_b)
+    const double *__restrict__ qcoef;   // [B] Q_amp derivative weight C_b/(4 pi sum C)
+    const double *__restrict__ cb4pi;   // [B] C_b/(4 pi)
+    const int *__restrict__ face_side;
+    const int *__restrict__ face_kind;  // 0 isothermal domain face
+    const double *__restrict__ msum;    // [B][F] raw adjoint face sums sum_d a_d mu_d
+    double *__restrict__ blockpart;     // [gridDim][B+7]
+    unsigned int *__restrict__ counter;
+    double *__restrict__ out;           // [B + 6 + 1]: dJ/dtau_b, dJ/dT_wall[6], dJ/dQ_amp
+};
+
+template <typename real>
+cudaError_t launch_grad(const GradParams<real> &g, cudaStream_t st);
+
+}  // namespace bte

@@ -1,0 +1,1107 @@
+// Host runtime of libbte: the C ABI declared in include/bte.h.
+//
+// bte_create builds the sweep plan once (direction ordering by octant, cell
+// flags, boundary-face table, per-side normalisers) and uploads it.  bte_solve
+// runs the outer source iteration of the paper's solution procedure (Methods,
+// steps 1-4): every iteration is one sweep launch (all bands x directions x
+// cells) followed by one FP64 update launch (temperature, diffuse inflow,
+// eps_T).  Iterations are replayed from a captured CUDA graph, polled every
+// few iterations through a device-side convergence flag.  Iteration i reads
+// state set i%2 and writes set (i+1)%2, so after n iterations the inputs of
+// the last sweep are still available; the final e is regenerated from them by
+// one more sweep (outer-iterate checkpointing: T and the diffuse inflow
+// determine e).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bte.h"
+#include "bte_internal.cuh"
+
+using namespace bte;
+
+namespace {
+
+constexpr double kFourPi = 4.0 * M_PI;
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    template <typename T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct Status {
+    int done;
+    int iter;
+    int status;
+    int pad;
+    double last[3];
+};
+
+template <typename real>
+struct Workspace {
+    bool init = false;
+    DevBuf tdev[2], ein[2], T[2];      // forward state sets
+    DevBuf thdev[2], mein[2], theta[2];  // adjoint state sets
+    DevBuf ein_fixed, part, fsum, e, gpart, phi, coef, invdiag, srck_f, srck_a, qb, cb4pi;
+    DevBuf wgt_f, wgt_a, Kinv, scale_f, scale_a, msum, g, grad_out, inv_tt, qcoef, phi64, vws, qshift, q,
+        eshift, tfwd_dummy;
+    // direction subsets per tile width
+    std::map<int, std::pair<std::vector<Subset>, std::vector<Subset>>> subsets;  // dw -> (fwd, adj)
+    std::map<int, std::pair<DevBuf *, DevBuf *>> dsub;
+    std::vector<std::unique_ptr<DevBuf>> subbufs;
+    int tuned_dw = 0;
+    // graph cache
+    cudaGraphExec_t graph = nullptr;
+    std::tuple<int, int, double, int> graph_key{-1, -1, 0.0, -1};
+    cudaGraphExec_t agraph = nullptr;
+    std::tuple<int, int, double, int> agraph_key{-1, -1, 0.0, -1};
+    ~Workspace() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (agraph) cudaGraphExecDestroy(agraph);
+    }
+};
+
+}  // namespace
+
+struct bte_plan {
+    // problem
+    int dim = 0, nx = 1, ny = 1, nz = 1;
+    long long N = 0, n_active = 0;
+    double h[3] = {1, 1, 1};
+    int B = 0, D = 0, R = 0;
+    std::vector<double> C, v, tau, tau_scale;
+    std::vector<double> s, w;  // internal direction order (sorted by octant)
+    std::vector<int> perm;     // internal d -> caller's d
+    std::vector<int> groups_d0, groups_cnt, groups_neg;
+    int bc_type[6];
+    double bc_T[6];
+    std::vector<double> phi;  // empty: no source
+    std::vector<uint8_t> mask;
+    std::vector<int2> cellinfo;
+    int F = 0;
+    std::vector<int> face_cell, face_side, face_kind;
+    double side_norm[6], side_out[6];  // sum over entering / leaving dirs of w |s.n|
+    // device, precision independent
+    DevBuf d_cell, d_face_cell, d_face_side, d_face_kind, d_perm, d_status, d_counter, d_blockpart, d_hist;
+    int hist_cap = 0;
+    Status *h_status = nullptr;  // pinned
+    Workspace<float> ws32;
+    Workspace<double> ws64;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+    // last forward solve
+    bool solved = false;
+    int solved_precision = -1;
+    int solved_iters = 0;
+    int solved_dw = 0;
+    bool e_current = false;
+    cudaStream_t stream = nullptr;  // stream of the last solve (used by the adjoint)
+    double T_ref = 300.0;
+    std::vector<double> cur_tau, cur_Tw;
+    double cur_Q = 0.0;
+    int sm_count = 0;
+
+    ~bte_plan() {
+        if (h_status) cudaFreeHost(h_status);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+namespace {
+
+int fail(bte_plan *p, int code, const std::string &msg) {
+    if (p)
+        p->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+#define CK(plan, expr)                                                                              \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess) {                                                                    \
+            return fail(plan, _e == cudaErrorMemoryAllocation ? BTE_ENOMEM : BTE_ECUDA,             \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));                        \
+        }                                                                                           \
+    } while (0)
+
+template <typename T>
+cudaError_t upload(DevBuf &d, const std::vector<T> &h) {
+    cudaError_t e = d.ensure(sizeof(T) * std::max<size_t>(h.size(), 1));
+    if (e != cudaSuccess) return e;
+    if (h.empty()) return cudaSuccess;
+    return cudaMemcpy(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+}
+
+bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+long long cell_index(const bte_plan *p, int i, int j, int k) { return i + (long long)p->nx * (j + (long long)p->ny * k); }
+
+// Directions of one orientation group split into subsets of at most dw.
+std::vector<Subset> make_subsets(const bte_plan *p, int dw, bool flip) {
+    std::vector<Subset> out;
+    const int resolved = (1 << p->dim) - 1;
+    for (size_t g = 0; g < p->groups_d0.size(); ++g) {
+        for (int o = 0; o < p->groups_cnt[g]; o += dw) {
+            Subset s;
+            s.d0 = p->groups_d0[g] + o;
+            s.cnt = std::min(dw, p->groups_cnt[g] - o);
+            s.neg = flip ? (p->groups_neg[g] ^ resolved) : p->groups_neg[g];
+            s.pad = 0;
+            out.push_back(s);
+        }
+    }
+    return out;
+}
+
+int tile_layers(const bte_plan *p) {
+    // 1D/2D: one layer; 3D: the fewest register layers that fit 32 warps
+    if (p->dim < 3) return 1;
+    const int WY = (p->ny + 31) / 32;
+    for (int lz : {1, 2, 4, 8})
+        if (WY * ((p->nz + lz - 1) / lz) <= 32) return lz;
+    return 0;
+}
+
+std::vector<int> tile_candidates(const bte_plan *p) {
+    std::vector<int> out;
+    const int lz = tile_layers(p);
+    if (lz == 0) return out;
+    const bool z = p->dim == 3;
+    const int WY = (p->ny + 31) / 32;
+    const int WZ = z ? (p->nz + lz - 1) / lz : 1;
+    for (int dw : {4, 8, 16}) {
+        const int mt = sweep_max_threads(dw, lz, z);
+        if (mt > 0 && WY * WZ * 32 <= mt) out.push_back(dw);
+    }
+    return out;
+}
+
+template <typename real>
+Workspace<real> &ws_of(bte_plan *p);
+template <>
+Workspace<float> &ws_of<float>(bte_plan *p) { return p->ws32; }
+template <>
+Workspace<double> &ws_of<double>(bte_plan *p) { return p->ws64; }
+
+template <typename real>
+int ensure_subsets(bte_plan *p, Workspace<real> &ws, int dw) {
+    if (ws.dsub.count(dw)) return BTE_OK;
+    auto f = make_subsets(p, dw, false);
+    auto a = make_subsets(p, dw, true);
+    ws.subsets[dw] = {f, a};
+    ws.subbufs.emplace_back(new DevBuf());
+    DevBuf *bf = ws.subbufs.back().get();
+    ws.subbufs.emplace_back(new DevBuf());
+    DevBuf *ba = ws.subbufs.back().get();
+    CK(p, upload(*bf, f));
+    CK(p, upload(*ba, a));
+    ws.dsub[dw] = {bf, ba};
+    return BTE_OK;
+}
+
+int max_subsets(const bte_plan *p) {
+    int s = 0;
+    for (size_t g = 0; g < p->groups_cnt.size(); ++g) s += (p->groups_cnt[g] + 3) / 4;
+    return s;
+}
+
+// Per-solve tables (depend on tau overrides, wall temperatures, Q_amp, T_ref).
+template <typename real>
+int upload_tables(bte_plan *p, Workspace<real> &ws) {
+    const int B = p->B, D = p->D, R = p->R;
+    const std::vector<double> &tau = p->cur_tau;
+    std::vector<real> coef((size_t)B * D * 8), invd((size_t)R * B * D), srf((size_t)R * B), sra((size_t)R * B),
+        qb(B), cb(B);
+    std::vector<double> wf((size_t)R * B), wa((size_t)R * B), Kinv(R), scf(6 * B), sca(6 * B), itt((size_t)R * B),
+        qc(B), vws((size_t)B * D * 3), qsh(3, 0.0), esh(B);
+    double Csum = 0.0;
+    for (int b = 0; b < B; ++b) Csum += p->C[b];
+    for (int b = 0; b < B; ++b) {
+        for (int d = 0; d < D; ++d) {
+            double a[3] = {0, 0, 0};
+            for (int ax = 0; ax < p->dim; ++ax) a[ax] = p->v[b] * std::fabs(p->s[3 * d + ax]) / p->h[ax];
+            real *cf = &coef[((size_t)b * D + d) * 8];
+            cf[0] = (real)a[0];
+            cf[1] = (real)a[1];
+            cf[2] = (real)a[2];
+            cf[3] = (real)p->w[d];
+            for (int ax = 0; ax < 3; ++ax) cf[4 + ax] = (ax < p->dim) ? (real)(p->w[d] * std::fabs(p->s[3 * d + ax])) : (real)0;
+            cf[7] = 0;
+            for (int r = 0; r < R; ++r) {
+                const double trb = tau[b] * p->tau_scale[r];
+                invd[((size_t)r * B + b) * D + d] = (real)(1.0 / (1.0 / trb + a[0] + a[1] + a[2]));
+            }
+            for (int ax = 0; ax < 3; ++ax) vws[((size_t)b * D + d) * 3 + ax] = p->v[b] * p->w[d] * p->s[3 * d + ax];
+        }
+        qb[b] = (real)(p->C[b] * p->cur_Q / (kFourPi * Csum));
+        cb[b] = (real)(p->C[b] / kFourPi);
+        qc[b] = p->C[b] / (kFourPi * Csum);
+        esh[b] = p->C[b] * p->T_ref / kFourPi;
+        for (int ax = 0; ax < 3; ++ax) {
+            double sws = 0.0;
+            for (int d = 0; d < D; ++d) sws += p->w[d] * p->s[3 * d + ax];
+            qsh[ax] += p->v[b] * esh[b] * sws;
+        }
+    }
+    for (int r = 0; r < R; ++r) {
+        double K = 0.0;
+        for (int b = 0; b < B; ++b) {
+            const double trb = tau[b] * p->tau_scale[r];
+            srf[(size_t)r * B + b] = (real)(p->C[b] / (kFourPi * trb));
+            sra[(size_t)r * B + b] = (real)(1.0 / trb);
+            wf[(size_t)r * B + b] = 1.0 / trb;
+            wa[(size_t)r * B + b] = p->C[b] / (kFourPi * trb);
+            itt[(size_t)r * B + b] = 1.0 / (trb * tau[b]);
+            K += p->C[b] / trb;
+        }
+        Kinv[r] = 1.0 / K;
+    }
+    for (int side = 0; side < 6; ++side)
+        for (int b = 0; b < B; ++b) {
+            const double nrm = p->side_norm[side];
+            scf[side * B + b] = nrm > 0 ? 1.0 / nrm : 0.0;
+            sca[side * B + b] = nrm > 0 ? p->h[side / 2] / (p->v[b] * nrm) : 0.0;
+        }
+    // isothermal inflow C_b (T_w - T_ref) / (4 pi)
+    std::vector<real> efix((size_t)B * std::max(p->F, 1), (real)0);
+    for (int f = 0; f < p->F; ++f)
+        if (p->face_kind[f] == 0)
+            for (int b = 0; b < B; ++b)
+                efix[(size_t)b * p->F + f] = (real)(p->C[b] * (p->cur_Tw[p->face_side[f]] - p->T_ref) / kFourPi);
+    CK(p, upload(ws.coef, coef));
+    CK(p, upload(ws.invdiag, invd));
+    CK(p, upload(ws.srck_f, srf));
+    CK(p, upload(ws.srck_a, sra));
+    CK(p, upload(ws.qb, qb));
+    CK(p, upload(ws.cb4pi, cb));
+    CK(p, upload(ws.wgt_f, wf));
+    CK(p, upload(ws.wgt_a, wa));
+    CK(p, upload(ws.Kinv, Kinv));
+    CK(p, upload(ws.scale_f, scf));
+    CK(p, upload(ws.scale_a, sca));
+    CK(p, upload(ws.inv_tt, itt));
+    CK(p, upload(ws.qcoef, qc));
+    CK(p, upload(ws.vws, vws));
+    CK(p, upload(ws.qshift, qsh));
+    CK(p, upload(ws.eshift, esh));
+    CK(p, upload(ws.ein_fixed, efix));
+    return BTE_OK;
+}
+
+template <typename real>
+int ensure_workspace(bte_plan *p, Workspace<real> &ws) {
+    if (ws.init) return BTE_OK;
+    const size_t N = (size_t)p->N, B = p->B, F = std::max(p->F, 1);
+    const size_t S = max_subsets(p);
+    for (int i = 0; i < 2; ++i) {
+        CK(p, ws.tdev[i].ensure(sizeof(real) * N));
+        CK(p, ws.ein[i].ensure(sizeof(real) * B * F));
+        CK(p, ws.T[i].ensure(sizeof(double) * N));
+    }
+    CK(p, ws.part.ensure(sizeof(real) * S * B * N));
+    CK(p, ws.fsum.ensure(sizeof(real) * S * B * F));
+    std::vector<real> ph(N, (real)0);
+    for (size_t c = 0; c < N && !p->phi.empty(); ++c) ph[c] = (real)p->phi[c];
+    CK(p, upload(ws.phi, ph));
+    ws.init = true;
+    return BTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launches of one iteration
+// ---------------------------------------------------------------------------
+template <typename real>
+SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int dw, bool adj) {
+    SweepParams<real> sp{};
+    sp.nx = p->nx;
+    sp.ny = p->ny;
+    sp.nz = p->nz;
+    sp.B = p->B;
+    sp.D = p->D;
+    sp.F = std::max(p->F, 1);
+    sp.R = p->R;
+    const int lz = tile_layers(p);
+    sp.WY = (p->ny + 31) / 32;
+    sp.WZ = (p->dim == 3) ? (p->nz + lz - 1) / lz : 1;
+    sp.N = p->N;
+    sp.cell = p->d_cell.as<int2>();
+    sp.part = ws.part.template as<real>();
+    sp.fsum = ws.fsum.template as<real>();
+    sp.coef = ws.coef.template as<real>();
+    sp.invdiag = ws.invdiag.template as<real>();
+    sp.srck = adj ? ws.srck_a.template as<real>() : ws.srck_f.template as<real>();
+    sp.qb = ws.qb.template as<real>();
+    sp.phi = p->phi.empty() ? nullptr : ws.phi.template as<real>();
+    sp.cb4pi = ws.cb4pi.template as<real>();
+    auto pr = ws.dsub.at(dw);
+    sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
+    sp.S = (int)ws.subsets.at(dw).first.size();
+    sp.done = p->d_status.as<int>();
+    // stage the band's boundary values in shared memory when they fit next to
+    // the exchange buffers (<= 200 KB of the 227 KB per CTA)
+    const size_t ein_bytes = sizeof(real) * (size_t)sp.F;
+    const size_t xchg = sizeof(real) * (size_t)sp.WY * sp.WZ * (2 * lz * 16 + (p->dim == 3 ? 2 * 32 * 16 : 0));
+    sp.ein_smem = (ein_bytes + xchg <= 200 * 1024) ? 1 : 0;
+    return sp;
+}
+
+template <typename real>
+UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int dw, bool adj, double tol) {
+    UpdateParams<real> u{};
+    u.N = p->N;
+    u.B = p->B;
+    u.S = (int)ws.subsets.at(dw).first.size();
+    u.F = p->F;
+    u.R = p->R;
+    u.adjoint = adj ? 1 : 0;
+    u.T_ref = p->T_ref;
+    u.cell = p->d_cell.as<int2>();
+    auto pr = ws.dsub.at(dw);
+    u.sub = (adj ? pr.second : pr.first)->template as<Subset>();
+    u.part = ws.part.template as<real>();
+    u.fsum = ws.fsum.template as<real>();
+    u.g = ws.g.template as<double>();
+    u.wgt = adj ? ws.wgt_a.template as<double>() : ws.wgt_f.template as<double>();
+    u.Kinv = ws.Kinv.template as<double>();
+    u.face_cell = p->d_face_cell.as<int>();
+    u.face_side = p->d_face_side.as<int>();
+    u.face_kind = p->d_face_kind.as<int>();
+    u.ein_fixed = ws.ein_fixed.template as<real>();
+    u.side_scale = adj ? ws.scale_a.template as<double>() : ws.scale_f.template as<double>();
+    u.blockpart = p->d_blockpart.as<double>();
+    u.counter = p->d_counter.as<unsigned int>();
+    Status *st = p->d_status.as<Status>();
+    u.done = &st->done;
+    u.iter = &st->iter;
+    u.status = &st->status;
+    u.last = st->last;
+    u.eps_hist = p->d_hist.as<double>();
+    u.max_hist = p->hist_cap;
+    u.tol = tol;
+    u.n_active = p->n_active;
+    return u;
+}
+
+template <typename real>
+cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int dw, int parity, double tol, bool store_e,
+                            bool replay, cudaStream_t stream) {
+    SweepParams<real> sp = sweep_params(p, ws, dw, false);
+    sp.tsrc = ws.tdev[parity].template as<real>();
+    sp.ein = ws.ein[parity].template as<real>();
+    sp.store_e = store_e ? 1 : 0;
+    sp.e = ws.e.template as<real>();
+    if (replay) sp.done = nullptr;
+    cudaError_t e = launch_sweep<real>(sp, dw, tile_layers(p), p->dim == 3, false, stream);
+    if (e != cudaSuccess || replay) return e;
+    UpdateParams<real> u = update_params(p, ws, dw, false, tol);
+    u.x_in = ws.T[parity].template as<double>();
+    u.x_out = ws.T[parity ^ 1].template as<double>();
+    u.xdev_out = ws.tdev[parity ^ 1].template as<real>();
+    u.ein_out = ws.ein[parity ^ 1].template as<real>();
+    return launch_update<real>(u, stream);
+}
+
+template <typename real>
+int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaStream_t stream) {
+    const long long N = p->N;
+    std::vector<double> T0(N);
+    if (o->T_init) {
+        if (is_device_ptr(o->T_init)) {
+            CK(p, cudaMemcpy(T0.data(), o->T_init, sizeof(double) * N, cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(T0.data(), o->T_init, sizeof(double) * N);
+        }
+    } else {
+        std::fill(T0.begin(), T0.end(), o->T_init_uniform);
+    }
+    double sum = 0.0;
+    for (long long c = 0; c < N; ++c) {
+        if (!p->mask[c]) {
+            T0[c] = 0.0;
+            continue;
+        }
+        if (!(T0[c] > 0.0) || !std::isfinite(T0[c])) return fail(p, BTE_EINVAL, "T_init must be finite and > 0 in solid cells");
+        sum += T0[c];
+    }
+    p->T_ref = sum / (double)p->n_active;
+    std::vector<real> td(N);
+    for (long long c = 0; c < N; ++c) td[c] = p->mask[c] ? (real)(T0[c] - p->T_ref) : (real)0;
+    const int B = p->B, F = std::max(p->F, 1);
+    std::vector<real> e0((size_t)B * F, (real)0);
+    for (int f = 0; f < p->F; ++f) {
+        const long long c = p->face_cell[f];
+        const int side = p->face_side[f];
+        for (int b = 0; b < B; ++b) {
+            double val;
+            if (p->face_kind[f] == 0)
+                val = p->C[b] * (p->cur_Tw[side] - p->T_ref) / kFourPi;
+            else  // diffuse reflection of the initial equilibrium e0(T_init)
+                val = p->C[b] * (T0[c] - p->T_ref) / kFourPi * p->side_out[side] / p->side_norm[side];
+            e0[(size_t)b * F + f] = (real)val;
+        }
+    }
+    CK(p, cudaMemcpyAsync(ws.T[0].p, T0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
+    CK(p, cudaMemcpyAsync(ws.tdev[0].p, td.data(), sizeof(real) * N, cudaMemcpyHostToDevice, stream));
+    CK(p, cudaMemcpyAsync(ws.ein[0].p, e0.data(), sizeof(real) * e0.size(), cudaMemcpyHostToDevice, stream));
+    CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
+    CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
+    CK(p, cudaStreamSynchronize(stream));
+    return BTE_OK;
+}
+
+template <typename real>
+int autotune(bte_plan *p, Workspace<real> &ws, cudaStream_t stream) {
+    std::vector<int> cand = tile_candidates(p);
+    if (cand.empty()) return 0;
+    if (cand.size() == 1) return cand[0];
+    float best = 1e30f;
+    int best_dw = cand[0];
+    for (int dw : cand) {
+        if (ensure_subsets(p, ws, dw) != BTE_OK) return 0;
+        // two warm-up sweeps, then the median-free minimum of three
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 5; ++rep) {
+            cudaEventRecord(p->ev0, stream);
+            SweepParams<real> sp = sweep_params(p, ws, dw, false);
+            sp.tsrc = ws.tdev[0].template as<real>();
+            sp.ein = ws.ein[0].template as<real>();
+            sp.done = nullptr;
+            if (launch_sweep<real>(sp, dw, tile_layers(p), p->dim == 3, false, stream) != cudaSuccess) {
+                cudaGetLastError();
+                tmin = 1e30f;
+                break;
+            }
+            cudaEventRecord(p->ev1, stream);
+            cudaEventSynchronize(p->ev1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+            if (rep >= 2) tmin = std::min(tmin, ms);
+        }
+        if (tmin < best) {
+            best = tmin;
+            best_dw = dw;
+        }
+    }
+    return best_dw;
+}
+
+template <typename real>
+int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, void *e_out, bte_stats *st) {
+    cudaStream_t stream = (cudaStream_t)o->stream;
+    Workspace<real> &ws = ws_of<real>(p);
+    int rc = ensure_workspace(p, ws);
+    if (rc) return rc;
+    // per-solve parameters
+    p->cur_tau = p->tau;
+    if (o->tau) {
+        for (int b = 0; b < p->B; ++b)
+            if (!(o->tau[b] > 0.0) || !std::isfinite(o->tau[b])) return fail(p, BTE_EINVAL, "tau override must be > 0");
+        p->cur_tau.assign(o->tau, o->tau + p->B);
+    }
+    p->cur_Tw.assign(p->bc_T, p->bc_T + 6);
+    if (o->T_wall) p->cur_Tw.assign(o->T_wall, o->T_wall + 6);
+    p->cur_Q = o->Q_amp;
+    if ((rc = begin_state(p, o, ws, stream))) return rc;
+    if ((rc = upload_tables(p, ws))) return rc;
+    // tile
+    std::vector<int> cand = tile_candidates(p);
+    if (cand.empty()) return fail(p, BTE_EINVAL, "grid too large for the sweep tiles (ny/nz)");
+    int dw = o->dirs_per_lane;
+    if (dw) {
+        if (std::find(cand.begin(), cand.end(), dw) == cand.end())
+            return fail(p, BTE_EINVAL, "dirs_per_lane not supported for this grid");
+    } else {
+        if (!ws.tuned_dw) ws.tuned_dw = autotune(p, ws, stream);
+        dw = ws.tuned_dw ? ws.tuned_dw : cand[0];
+    }
+    if ((rc = ensure_subsets(p, ws, dw))) return rc;
+    const bool need_e = e_out || q_out || true;  // the adjoint needs e; kept on device
+    if (need_e || o->store_e_every_iter) CK(p, ws.e.ensure(sizeof(real) * (size_t)p->N * p->B * p->D));
+    // re-initialise after autotuning touched the work buffers
+    if ((rc = begin_state(p, o, ws, stream))) return rc;
+
+    // one launch outside any capture sets the kernel's shared-memory attribute
+    CK(p, enqueue_forward(p, ws, dw, 0, tol, false, true, stream));
+    int poll = o->poll_every > 0 ? o->poll_every : 32;
+    poll = std::max(2, poll + (poll & 1));
+    const double tol = o->tol;
+    const bool store_every = o->store_e_every_iter != 0;
+    // graph of `poll` iterations (even, so every replay starts at parity 0)
+    auto key = std::make_tuple(dw, poll, tol, store_every ? 1 : 0);
+    if (!ws.graph || ws.graph_key != key) {
+        if (ws.graph) {
+            cudaGraphExecDestroy(ws.graph);
+            ws.graph = nullptr;
+        }
+        cudaStream_t cs;
+        CK(p, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int i = 0; i < poll && ce == cudaSuccess; ++i)
+            ce = enqueue_forward(p, ws, dw, i & 1, tol, store_every, false, cs);
+        cudaError_t ce2 = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess) return fail(p, BTE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        if (ce2 != cudaSuccess) return fail(p, BTE_ECUDA, std::string("graph capture end: ") + cudaGetErrorString(ce2));
+        ce = cudaGraphInstantiate(&ws.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            ws.graph = nullptr;
+            return fail(p, BTE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        ws.graph_key = key;
+    }
+    const int max_iter = o->max_iter;
+    int enq = 0;
+    long long launches = 0;
+    CK(p, cudaEventRecord(p->ev0, stream));
+    while (enq < max_iter) {
+        const int k = std::min(poll, max_iter - enq);
+        if (k == poll) {
+            CK(p, cudaGraphLaunch(ws.graph, stream));
+        } else {
+            for (int i = 0; i < k; ++i) CK(p, enqueue_forward(p, ws, dw, (enq + i) & 1, tol, store_every, false, stream));
+        }
+        enq += k;
+        launches += 2LL * k;
+        CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
+        CK(p, cudaStreamSynchronize(stream));
+        if (p->h_status->done) break;
+    }
+    CK(p, cudaEventRecord(p->ev1, stream));
+    CK(p, cudaEventSynchronize(p->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+    const int n = p->h_status->iter;
+    const bool bad = p->h_status->status != 0;
+    const bool converged = tol > 0.0 && p->h_status->done && !bad;
+    // regenerate e^n from the inputs of the last iteration
+    if (n > 0) CK(p, enqueue_forward(p, ws, dw, (n - 1) & 1, tol, true, true, stream));
+    if (n > 0) launches += 1;
+    p->e_current = n > 0;
+    const int par = n & 1;
+    CK(p, cudaMemcpyAsync(T_out, ws.T[par].p, sizeof(double) * p->N, cudaMemcpyDefault, stream));
+    if (q_out && n > 0) {
+        CK(p, ws.q.ensure(sizeof(double) * 3 * p->N));
+        CK(p, launch_flux<real>(p->N, p->B, p->D, p->d_cell.as<int2>(), ws.e.template as<real>(), ws.vws.template as<double>(),
+                                ws.qshift.template as<double>(), ws.q.template as<double>(), stream));
+        launches += 1;
+        CK(p, cudaMemcpyAsync(q_out, ws.q.p, sizeof(double) * 3 * p->N, cudaMemcpyDefault, stream));
+    }
+    if (e_out && n > 0) {
+        const size_t ne = (size_t)p->N * p->B * p->D;
+        if (is_device_ptr(e_out)) {
+            CK(p, launch_permute_e<real>(p->N, p->B, p->D, ws.e.template as<real>(), p->d_perm.as<int>(),
+                                         ws.eshift.template as<double>(), (real *)e_out, stream));
+            launches += 1;
+        } else {
+            CK(p, cudaMemcpyAsync(e_out, ws.e.p, sizeof(real) * ne, cudaMemcpyDeviceToHost, stream));
+            CK(p, cudaStreamSynchronize(stream));
+            real *eo = (real *)e_out;
+            std::vector<real> tmp(p->D);
+            for (size_t cb = 0; cb < (size_t)p->N * p->B; ++cb) {
+                const int b = (int)(cb % p->B);
+                const double sh = p->C[b] * p->T_ref / kFourPi;
+                for (int d = 0; d < p->D; ++d) tmp[p->perm[d]] = (real)((double)eo[cb * p->D + d] + sh);
+                std::memcpy(eo + cb * p->D, tmp.data(), sizeof(real) * p->D);
+            }
+        }
+    }
+    CK(p, cudaStreamSynchronize(stream));
+    p->solved = true;
+    p->stream = stream;
+    p->solved_precision = (sizeof(real) == 4) ? BTE_FP32 : BTE_FP64;
+    p->solved_iters = n;
+    p->solved_dw = dw;
+    if (st) {
+        st->iterations = n;
+        st->converged = converged ? 1 : 0;
+        st->eps_T = p->h_status->last[0];
+        st->T_max = p->h_status->last[1];
+        st->seconds = ms * 1e-3;
+        st->updates_per_s = st->seconds > 0 ? (double)n * p->n_active * p->B * p->D / st->seconds : 0.0;
+        st->dirs_per_lane = dw;
+        st->kernel_launches = launches;
+    }
+    if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the temperature update");
+    if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "max_iter reached before eps_T < tol");
+    return BTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+template <typename real>
+cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity, double tol, bool final_pass,
+                            cudaStream_t stream) {
+    SweepParams<real> sp = sweep_params(p, ws, dw, true);
+    sp.tsrc = ws.thdev[parity].template as<real>();
+    sp.ein = ws.mein[parity].template as<real>();
+    sp.e = ws.e.template as<real>();
+    sp.gpart = ws.gpart.template as<real>();
+    sp.read_e = final_pass ? 1 : 0;
+    sp.tfwd = ws.tdev[p->solved_iters & 1].template as<real>();
+    if (final_pass) sp.done = nullptr;
+    cudaError_t e = launch_sweep<real>(sp, dw, tile_layers(p), p->dim == 3, true, stream);
+    if (e != cudaSuccess) return e;
+    UpdateParams<real> u = update_params(p, ws, dw, true, tol);
+    u.eps_hist = nullptr;  // the history belongs to the forward solve
+    u.x_in = ws.theta[parity].template as<double>();
+    u.x_out = ws.theta[parity ^ 1].template as<double>();
+    u.xdev_out = ws.thdev[parity ^ 1].template as<real>();
+    u.ein_out = ws.mein[parity ^ 1].template as<real>();
+    if (final_pass) {
+        u.ignore_done = 1;
+        u.fsum_total = ws.msum.template as<double>();
+    }
+    return launch_update<real>(u, stream);
+}
+
+template <typename real>
+int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Tw, double *g_Q,
+              bte_stats *st) {
+    cudaStream_t stream = p->stream;
+    Workspace<real> &ws = ws_of<real>(p);
+    const int dw = p->solved_dw;
+    const long long N = p->N;
+    const int B = p->B, F = std::max(p->F, 1);
+    const size_t S = max_subsets(p);
+    for (int i = 0; i < 2; ++i) {
+        CK(p, ws.thdev[i].ensure(sizeof(real) * N));
+        CK(p, ws.mein[i].ensure(sizeof(real) * (size_t)B * F));
+        CK(p, ws.theta[i].ensure(sizeof(double) * N));
+    }
+    CK(p, ws.gpart.ensure(sizeof(real) * S * B * N));
+    CK(p, ws.msum.ensure(sizeof(double) * (size_t)B * F));
+    CK(p, ws.g.ensure(sizeof(double) * N));
+    CK(p, ws.grad_out.ensure(sizeof(double) * (B + 7)));
+    std::vector<double> g(N);
+    if (is_device_ptr(dJ_dT)) {
+        CK(p, cudaMemcpyAsync(g.data(), dJ_dT, sizeof(double) * N, cudaMemcpyDeviceToHost, stream));
+        CK(p, cudaStreamSynchronize(stream));
+    } else {
+        std::memcpy(g.data(), dJ_dT, sizeof(double) * N);
+    }
+    // Theta^0 = g / K (mu^0 = 0), M^0 = 0
+    std::vector<double> K(p->R);
+    for (int r = 0; r < p->R; ++r) {
+        double k = 0.0;
+        for (int b = 0; b < B; ++b) k += p->C[b] / (p->cur_tau[b] * p->tau_scale[r]);
+        K[r] = k;
+    }
+    std::vector<double> th(N, 0.0);
+    std::vector<real> thr(N, (real)0);
+    for (long long c = 0; c < N; ++c) {
+        if (!p->mask[c]) {
+            g[c] = 0.0;
+            continue;
+        }
+        if (!std::isfinite(g[c])) return fail(p, BTE_EINVAL, "dJ_dT must be finite");
+        th[c] = g[c] / K[p->mask[c] - 1];
+        thr[c] = (real)th[c];
+    }
+    CK(p, cudaMemcpyAsync(ws.g.p, g.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
+    CK(p, cudaMemcpyAsync(ws.theta[0].p, th.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
+    CK(p, cudaMemcpyAsync(ws.thdev[0].p, thr.data(), sizeof(real) * N, cudaMemcpyHostToDevice, stream));
+    CK(p, cudaMemsetAsync(ws.mein[0].p, 0, sizeof(real) * (size_t)B * F, stream));
+    CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
+    CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
+    if (!p->e_current) {
+        // regenerate the forward e^n from the stored state of the last solve
+        CK(p, enqueue_forward(p, ws, dw, (p->solved_iters - 1) & 1, 0.0, true, true, stream));
+        p->e_current = true;
+    }
+    CK(p, enqueue_adjoint(p, ws, dw, 0, tol, false, stream));   // attribute set outside capture
+    CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
+    CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
+    const int poll = 32;
+    auto key = std::make_tuple(dw, poll, tol, 0);
+    if (!ws.agraph || ws.agraph_key != key) {
+        if (ws.agraph) {
+            cudaGraphExecDestroy(ws.agraph);
+            ws.agraph = nullptr;
+        }
+        cudaStream_t cs;
+        CK(p, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int i = 0; i < poll && ce == cudaSuccess; ++i) ce = enqueue_adjoint(p, ws, dw, i & 1, tol, false, cs);
+        cudaError_t ce2 = cudaStreamEndCapture(cs, &gr);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess || ce2 != cudaSuccess)
+            return fail(p, BTE_ECUDA, std::string("adjoint graph capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+        ce = cudaGraphInstantiate(&ws.agraph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ce != cudaSuccess) {
+            ws.agraph = nullptr;
+            return fail(p, BTE_ECUDA, std::string("adjoint graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        ws.agraph_key = key;
+    }
+    int enq = 0;
+    long long launches = p->e_current ? 0 : 1;
+    CK(p, cudaEventRecord(p->ev0, stream));
+    while (enq < max_iter) {
+        const int k = std::min(poll, max_iter - enq);
+        launches += 2LL * k;
+        if (k == poll) {
+            CK(p, cudaGraphLaunch(ws.agraph, stream));
+        } else {
+            for (int i = 0; i < k; ++i) CK(p, enqueue_adjoint(p, ws, dw, (enq + i) & 1, tol, false, stream));
+        }
+        enq += k;
+        CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
+        CK(p, cudaStreamSynchronize(stream));
+        if (p->h_status->done) break;
+    }
+    const int n = p->h_status->iter;
+    const bool bad = p->h_status->status != 0;
+    const bool converged = tol > 0.0 && p->h_status->done && !bad;
+    // final pass: one more transposed sweep from Theta^n that also forms the
+    // gradient partials against the forward state, then the face sums
+    CK(p, enqueue_adjoint(p, ws, dw, n & 1, tol, true, stream));
+    GradParams<real> gp{};
+    gp.N = N;
+    gp.B = B;
+    gp.S = (int)ws.subsets.at(dw).first.size();
+    gp.F = p->F;
+    gp.cell = p->d_cell.as<int2>();
+    gp.apart = ws.part.template as<real>();
+    gp.gpart = ws.gpart.template as<real>();
+    if (!p->phi.empty()) {
+        CK(p, upload(ws.phi64, p->phi));
+        gp.phi = ws.phi64.template as<double>();
+    }
+    gp.inv_tt = ws.inv_tt.template as<double>();
+    gp.qcoef = ws.qcoef.template as<double>();
+    std::vector<double> cb(B);
+    for (int b = 0; b < B; ++b) cb[b] = p->C[b] / kFourPi;
+    CK(p, upload(ws.tfwd_dummy, cb));
+    gp.cb4pi = ws.tfwd_dummy.template as<double>();
+    gp.face_side = p->d_face_side.as<int>();
+    gp.face_kind = p->d_face_kind.as<int>();
+    gp.msum = ws.msum.template as<double>();
+    const int nblk = (int)((N + 255) / 256) + (p->F + 255) / 256;
+    DevBuf bp;
+    CK(p, bp.ensure(sizeof(double) * (size_t)nblk * (B + 7)));
+    gp.blockpart = bp.as<double>();
+    gp.counter = p->d_counter.as<unsigned int>();
+    gp.out = ws.grad_out.template as<double>();
+    CK(p, launch_grad<real>(gp, stream));
+    std::vector<double> out(B + 7);
+    CK(p, cudaMemcpyAsync(out.data(), ws.grad_out.p, sizeof(double) * (B + 7), cudaMemcpyDeviceToHost, stream));
+    CK(p, cudaEventRecord(p->ev1, stream));
+    CK(p, cudaEventSynchronize(p->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+    if (g_tau) std::memcpy(g_tau, out.data(), sizeof(double) * B);
+    if (g_Tw) {
+        for (int f = 0; f < 6; ++f) g_Tw[f] = (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL) ? out[B + f] : 0.0;
+    }
+    if (g_Q) *g_Q = out[B + 6];
+    if (st) {
+        st->iterations = n;
+        st->converged = converged;
+        st->eps_T = p->h_status->last[0];
+        st->T_max = p->h_status->last[1];
+        st->seconds = ms * 1e-3;
+        st->updates_per_s = st->seconds > 0 ? (double)(n + 1) * p->n_active * p->B * p->D / st->seconds : 0.0;
+        st->dirs_per_lane = dw;
+        st->kernel_launches = launches + 3;  // final sweep + update + gradient reduction
+    }
+    if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the adjoint update");
+    if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "adjoint: max_iter reached before tol");
+    return BTE_OK;
+}
+
+template <typename real>
+int profile_t(bte_plan *p, int reps, double *ms_per_sweep) {
+    Workspace<real> &ws = ws_of<real>(p);
+    cudaStream_t stream = p->stream;
+    const int par = (p->solved_iters - 1) & 1;
+    for (int i = 0; i < 2; ++i) CK(p, enqueue_forward(p, ws, p->solved_dw, par, 0.0, false, true, stream));
+    CK(p, cudaEventRecord(p->ev0, stream));
+    for (int i = 0; i < reps; ++i) CK(p, enqueue_forward(p, ws, p->solved_dw, par, 0.0, false, true, stream));
+    CK(p, cudaEventRecord(p->ev1, stream));
+    CK(p, cudaEventSynchronize(p->ev1));
+    float ms = 0.f;
+    CK(p, cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    *ms_per_sweep = ms / reps;
+    return BTE_OK;
+}
+
+int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_bands *bands, const bte_quad *quad,
+               const bte_bcs *bcs, const double *q_profile) {
+    if (!g || !mask || !bands || !quad || !bcs) return fail(nullptr, BTE_EINVAL, "null argument");
+    if (g->dim < 1 || g->dim > 3) return fail(nullptr, BTE_EINVAL, "dim must be 1, 2 or 3");
+    for (int a = 0; a < 3; ++a) {
+        if (g->n[a] < 1) return fail(nullptr, BTE_EINVAL, "n[a] must be >= 1");
+        if (a >= g->dim && g->n[a] != 1) return fail(nullptr, BTE_EINVAL, "n[a] must be 1 for axes >= dim");
+        if (!(g->length[a] > 0.0) || !std::isfinite(g->length[a])) return fail(nullptr, BTE_EINVAL, "length must be > 0");
+    }
+    p->dim = g->dim;
+    p->nx = g->n[0];
+    p->ny = g->n[1];
+    p->nz = g->n[2];
+    p->N = (long long)p->nx * p->ny * p->nz;
+    if (p->N > (1LL << 31) - 1) return fail(nullptr, BTE_EINVAL, "too many cells");
+    for (int a = 0; a < 3; ++a) p->h[a] = g->length[a] / g->n[a];
+    if (bands->B < 1 || bands->R < 1 || bands->R > kMaxRegions || !bands->C || !bands->v || !bands->tau || !bands->tau_scale)
+        return fail(nullptr, BTE_EINVAL, "bands: need B >= 1, 1 <= R <= 15 and all arrays");
+    p->B = bands->B;
+    p->R = bands->R;
+    p->C.assign(bands->C, bands->C + p->B);
+    p->v.assign(bands->v, bands->v + p->B);
+    p->tau.assign(bands->tau, bands->tau + p->B);
+    p->tau_scale.assign(bands->tau_scale, bands->tau_scale + p->R);
+    for (int b = 0; b < p->B; ++b)
+        if (!(p->C[b] > 0) || !(p->v[b] > 0) || !(p->tau[b] > 0) || !std::isfinite(p->C[b] * p->v[b] * p->tau[b]))
+            return fail(nullptr, BTE_EINVAL, "bands: C, v, tau must be finite and > 0");
+    for (int r = 0; r < p->R; ++r)
+        if (!(p->tau_scale[r] > 0) || !std::isfinite(p->tau_scale[r]))
+            return fail(nullptr, BTE_EINVAL, "bands: tau_scale must be finite and > 0");
+    if (quad->D < 1 || !quad->s || !quad->w) return fail(nullptr, BTE_EINVAL, "quad: need D >= 1");
+    p->D = quad->D;
+    double wsum = 0.0;
+    for (int d = 0; d < p->D; ++d) {
+        if (!(quad->w[d] > 0) || !std::isfinite(quad->w[d])) return fail(nullptr, BTE_EINVAL, "quad: weights must be > 0");
+        wsum += quad->w[d];
+        const double n2 = quad->s[3 * d] * quad->s[3 * d] + quad->s[3 * d + 1] * quad->s[3 * d + 1] +
+                          quad->s[3 * d + 2] * quad->s[3 * d + 2];
+        if (!(std::fabs(n2 - 1.0) < 1e-8)) return fail(nullptr, BTE_EINVAL, "quad: directions must be unit vectors");
+    }
+    if (std::fabs(wsum - kFourPi) > 1e-10 * kFourPi) return fail(nullptr, BTE_EINVAL, "quad: sum of weights must be 4 pi");
+    // internal order: stable sort by orientation key over the resolved axes
+    std::vector<int> order(p->D);
+    std::vector<int> key(p->D);
+    for (int d = 0; d < p->D; ++d) {
+        order[d] = d;
+        int k = 0;
+        for (int a = 0; a < p->dim; ++a) k = k * 2 + (quad->s[3 * d + a] < 0.0 ? 1 : 0);
+        key[d] = k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
+    p->s.resize(3 * p->D);
+    p->w.resize(p->D);
+    p->perm.resize(p->D);
+    for (int d = 0; d < p->D; ++d) {
+        for (int a = 0; a < 3; ++a) p->s[3 * d + a] = quad->s[3 * order[d] + a];
+        p->w[d] = quad->w[order[d]];
+        p->perm[d] = order[d];
+    }
+    for (int d = 0; d < p->D;) {
+        int e = d;
+        while (e < p->D && key[order[e]] == key[order[d]]) ++e;
+        int neg = 0;
+        for (int a = 0; a < p->dim; ++a)
+            if (p->s[3 * d + a] < 0.0) neg |= 1 << a;
+        p->groups_d0.push_back(d);
+        p->groups_cnt.push_back(e - d);
+        p->groups_neg.push_back(neg);
+        d = e;
+    }
+    for (int side = 0; side < 6; ++side) {
+        const int a = side / 2;
+        const double sg = (side & 1) ? 1.0 : -1.0;
+        double nin = 0.0, nout = 0.0;
+        for (int d = 0; d < p->D; ++d) {
+            const double sn = p->s[3 * d + a] * sg;
+            if (sn < 0.0) nin += p->w[d] * std::fabs(sn);
+            if (sn > 0.0) nout += p->w[d] * sn;
+        }
+        p->side_norm[side] = nin;
+        p->side_out[side] = nout;
+    }
+    for (int f = 0; f < 6; ++f) {
+        if (bcs->type[f] != BTE_BC_ISOTHERMAL && bcs->type[f] != BTE_BC_DIFFUSE)
+            return fail(nullptr, BTE_EINVAL, "bcs: unknown face type");
+        if (bcs->type[f] == BTE_BC_ISOTHERMAL && f / 2 < p->dim && (!(bcs->T[f] > 0) || !std::isfinite(bcs->T[f])))
+            return fail(nullptr, BTE_EINVAL, "bcs: wall temperature must be > 0");
+        p->bc_type[f] = bcs->type[f];
+        p->bc_T[f] = bcs->T[f];
+    }
+    // cells and faces
+    p->mask.assign(mask, mask + p->N);
+    p->cellinfo.resize(p->N);
+    bool anchored = false;
+    for (int k = 0; k < p->nz; ++k)
+        for (int j = 0; j < p->ny; ++j)
+            for (int i = 0; i < p->nx; ++i) {
+                const long long c = cell_index(p, i, j, k);
+                const int r = p->mask[c];
+                if (r > p->R) return fail(nullptr, BTE_EINVAL, "mask value exceeds the number of regions");
+                int flags = r, base = p->F;
+                if (r) {
+                    ++p->n_active;
+                    const int idx[3] = {i, j, k};
+                    for (int side = 0; side < 2 * p->dim; ++side) {
+                        const int a = side / 2;
+                        int jdx[3] = {i, j, k};
+                        jdx[a] += (side & 1) ? 1 : -1;
+                        const bool outside = jdx[a] < 0 || jdx[a] >= g->n[a];
+                        const bool voidn = !outside && p->mask[cell_index(p, jdx[0], jdx[1], jdx[2])] == 0;
+                        (void)idx;
+                        if (outside || voidn) {
+                            flags |= 1 << (kSideShift + side);
+                            p->face_cell.push_back((int)c);
+                            p->face_side.push_back(side);
+                            const bool iso = outside && p->bc_type[side] == BTE_BC_ISOTHERMAL;
+                            p->face_kind.push_back(iso ? 0 : 1);
+                            if (iso) anchored = true;
+                            ++p->F;
+                        }
+                    }
+                }
+                p->cellinfo[c] = make_int2(base, flags);
+            }
+    if (p->n_active == 0) return fail(nullptr, BTE_EINVAL, "mask has no solid cell");
+    if (!anchored) return fail(nullptr, BTE_EINVAL, "no isothermal face touches the solid (temperature undetermined)");
+    if (q_profile) {
+        p->phi.assign(q_profile, q_profile + p->N);
+        for (long long c = 0; c < p->N; ++c)
+            if (!std::isfinite(p->phi[c])) return fail(nullptr, BTE_EINVAL, "q_profile must be finite");
+    }
+    return BTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bte_version(void) { return "libbte 0.1 (sm_103a)"; }
+
+void bte_default_opts(bte_solve_opts *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->precision = BTE_FP32;
+    o->tol = 1e-6;
+    o->max_iter = 100000;
+    o->T_init = nullptr;
+    o->T_init_uniform = 300.0;
+    o->Q_amp = 1.0;
+    o->poll_every = 32;
+}
+
+int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands, const bte_quad *quad,
+               const bte_bcs *bcs, const double *q_profile, bte_plan **out) {
+    if (!out) return fail(nullptr, BTE_EINVAL, "out is null");
+    *out = nullptr;
+    std::unique_ptr<bte_plan> p(new (std::nothrow) bte_plan());
+    if (!p) return fail(nullptr, BTE_ENOMEM, "host allocation failed");
+    int rc = build_plan(p.get(), g, mask, bands, quad, bcs, q_profile);
+    if (rc) return rc;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) return fail(nullptr, BTE_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(ce));
+#define CKC(expr)                                                                                               \
+    do {                                                                                                        \
+        cudaError_t _e = (expr);                                                                                \
+        if (_e != cudaSuccess)                                                                                  \
+            return fail(nullptr, _e == cudaErrorMemoryAllocation ? BTE_ENOMEM : BTE_ECUDA,                      \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));                                    \
+    } while (0)
+    CKC(upload(p->d_cell, p->cellinfo));
+    CKC(upload(p->d_face_cell, p->face_cell));
+    CKC(upload(p->d_face_side, p->face_side));
+    CKC(upload(p->d_face_kind, p->face_kind));
+    CKC(upload(p->d_perm, p->perm));
+    CKC(p->d_status.ensure(sizeof(Status)));
+    CKC(p->d_counter.ensure(sizeof(unsigned int)));
+    CKC(cudaMemset(p->d_counter.p, 0, sizeof(unsigned int)));
+    const long long nblk = (p->N + 255) / 256 + ((long long)std::max(p->F, 1) * p->B + 255) / 256 + 16;
+    CKC(p->d_blockpart.ensure(sizeof(double) * 2 * nblk));
+    p->hist_cap = 1 << 16;
+    CKC(p->d_hist.ensure(sizeof(double) * p->hist_cap));
+    CKC(cudaMallocHost(&p->h_status, sizeof(Status)));
+    CKC(cudaEventCreate(&p->ev0));
+    CKC(cudaEventCreate(&p->ev1));
+#undef CKC
+    *out = p.release();
+    return BTE_OK;
+}
+
+int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, void *e_out, bte_stats *st) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (!o || !T_out) return fail(p, BTE_EINVAL, "opts and T_out are required");
+    if (o->max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
+    if (!o->T_init && !(o->T_init_uniform > 0.0)) return fail(p, BTE_EINVAL, "T_init_uniform must be > 0");
+    if (!std::isfinite(o->Q_amp)) return fail(p, BTE_EINVAL, "Q_amp must be finite");
+    if (o->T_wall)
+        for (int f = 0; f < 6; ++f)
+            if (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL && (!(o->T_wall[f] > 0) || !std::isfinite(o->T_wall[f])))
+                return fail(p, BTE_EINVAL, "T_wall override must be > 0");
+    p->solved = false;
+    if (o->precision == BTE_FP32) return solve_t<float>(p, o, T_out, q_out, e_out, st);
+    if (o->precision == BTE_FP64) return solve_t<double>(p, o, T_out, q_out, e_out, st);
+    return fail(p, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+}
+
+int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Twall,
+                double *g_Qamp, bte_stats *st) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (!dJ_dT) return fail(p, BTE_EINVAL, "dJ_dT is required");
+    if (max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
+    if (!p->solved || p->solved_iters < 1) return fail(p, BTE_ESTATE, "bte_adjoint needs a preceding bte_solve");
+    if (p->solved_precision == BTE_FP32) return adjoint_t<float>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, st);
+    return adjoint_t<double>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, st);
+}
+
+int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (reps < 1 || !ms_per_sweep) return fail(p, BTE_EINVAL, "reps >= 1 and ms_per_sweep required");
+    if (!p->solved || p->solved_iters < 1) return fail(p, BTE_ESTATE, "bte_profile_sweep needs a preceding bte_solve");
+    if (p->solved_precision == BTE_FP32) return profile_t<float>(p, reps, ms_per_sweep);
+    return profile_t<double>(p, reps, ms_per_sweep);
+}
+
+int bte_eps_history(const bte_plan *p, double *out, int n) {
+    if (!p || !out || n < 0) return BTE_EINVAL;
+    const int m = std::min(n, std::min(p->solved_iters, p->hist_cap));
+    if (m > 0 && cudaMemcpy(out, p->d_hist.p, sizeof(double) * m, cudaMemcpyDeviceToHost) != cudaSuccess) return BTE_ECUDA;
+    return m;
+}
+
+void bte_destroy(bte_plan *p) { delete p; }
+
+const char *bte_last_error(const bte_plan *p) { return p ? p->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,316 @@
+// FP64 reductions between sweeps.
+//
+// Forward (Eq. updatee0_t): T_c = T_ref + sum_b (1/tau_cb) sum_s part[s][b][c] / K_c,
+// K_c = sum_b C_b/tau_cb, where part[s][b][c] = sum over the subset's
+// directions of w_d (e_cbd - C_b T_ref/(4 pi)) from the sweep (FP32 inside a
+// subset, FP64 from here on).  Diffuse faces get the next inflow
+// e_in = sum_{s.n>0} w |s.n| e / sum_{s.n<0} w |s.n| (diffusely reflecting
+// boundary, quadrature-consistent normaliser).  The convergence measure is
+// eps_T = sqrt(mean (T_new - T_old)^2) / max T_new (Methods, step 4).
+//
+// Adjoint: Theta_c = (dJ/dT_c + sum_b C_b/(4 pi tau_cb) sum_d mu_cbd) / K_c and
+// the diffuse-face adjoint value M' = (sum over entering directions of
+// a_d mu_d) h / (v_b N_side); the stop measure is the relative RMS change of
+// Theta.
+//
+// Reductions over blocks are deterministic: every block writes its partial,
+// the last block to finish (ticket counter) combines them in block order.
+#include <math.h>
+
+#include "bte_internal.cuh"
+
+namespace bte {
+
+constexpr int kUpdThreads = 256;
+
+__device__ __forceinline__ void block_reduce2(double &a, double &m, double *sh) {
+    // sum of a, max of m over the block (kUpdThreads threads)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[2 * warp] = a;
+        sh[2 * warp + 1] = m;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sh[2 * lane] : 0.0;
+        m = lane < nw ? sh[2 * lane + 1] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        }
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_constant__ UpdateParams<real> P,
+                                                             int cell_blocks) {
+    if (!P.ignore_done && *((volatile int *)P.done) != 0) return;
+    __shared__ double sh[2 * (kUpdThreads / 32)];
+    __shared__ int is_last;
+    double ss = 0.0, mx = -INFINITY;
+    if ((int)blockIdx.x < cell_blocks) {
+        const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (c < P.N) {
+            const int2 ci = P.cell[c];
+            const int r = ci.y & kRegionMask;
+            if (r != 0) {
+                double acc = 0.0;
+                for (int b = 0; b < P.B; ++b) {
+                    double sb = 0.0;
+                    for (int s = 0; s < P.S; ++s) sb += (double)P.part[((long long)s * P.B + b) * P.N + c];
+                    acc += sb * P.wgt[(r - 1) * P.B + b];
+                }
+                double xn;
+                if (!P.adjoint) {
+                    const double dev = acc * P.Kinv[r - 1];
+                    xn = P.T_ref + dev;
+                    P.xdev_out[c] = (real)dev;
+                    mx = xn;
+                } else {
+                    xn = (P.g[c] + acc) * P.Kinv[r - 1];
+                    P.xdev_out[c] = (real)xn;
+                    mx = fabs(xn);
+                }
+                const double d = xn - P.x_in[c];
+                ss = d * d;
+                if (!isfinite(xn)) ss = NAN;
+                P.x_out[c] = xn;
+            } else {
+                P.x_out[c] = 0.0;
+                P.xdev_out[c] = (real)0;
+            }
+        }
+    } else {
+        const long long fb = (long long)(blockIdx.x - cell_blocks) * blockDim.x + threadIdx.x;
+        if (fb < (long long)P.F * P.B) {
+            const int b = (int)(fb / P.F);
+            const int f = (int)(fb % P.F);
+            const int side = P.face_side[f];
+            const int a = side >> 1;
+            const bool plus = side & 1;
+            if (P.face_kind[f] == 0 && !P.adjoint) {
+                P.ein_out[fb] = P.ein_fixed[fb];
+            } else {
+                double sum = 0.0;
+                for (int s = 0; s < P.S; ++s) {
+                    const bool neg = (P.sub[s].neg >> a) & 1;
+                    // the subset leaves a cell by the plus side iff it runs upward on axis a
+                    if (neg != plus) sum += (double)P.fsum[((long long)s * P.B + b) * P.F + f];
+                }
+                if (P.fsum_total) P.fsum_total[fb] = sum;
+                P.ein_out[fb] = (P.face_kind[f] == 0) ? (real)0 : (real)(sum * P.side_scale[side * P.B + b]);
+            }
+        }
+    }
+    block_reduce2(ss, mx, sh);
+    if (threadIdx.x == 0) {
+        P.blockpart[2 * blockIdx.x] = ss;
+        P.blockpart[2 * blockIdx.x + 1] = mx;
+        __threadfence();
+        const unsigned ticket = atomicAdd(P.counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // last block: combine in block order (deterministic)
+    double tss = 0.0, tmx = -INFINITY;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < cell_blocks; ++i) {
+            tss += ((volatile double *)P.blockpart)[2 * i];
+            tmx = fmax(tmx, ((volatile double *)P.blockpart)[2 * i + 1]);
+        }
+        *P.counter = 0u;
+        const double eps = (tmx > 0.0) ? sqrt(tss / (double)P.n_active) / tmx : 0.0;
+        const int it = *P.iter;
+        if (P.eps_hist && it < P.max_hist) P.eps_hist[it] = eps;
+        P.last[0] = eps;
+        P.last[1] = tmx;
+        P.last[2] = tss;
+        if (!P.ignore_done) {
+            *P.iter = it + 1;
+            if (!isfinite(eps)) {
+                *P.status = 1;
+                *P.done = 1;
+            } else if (P.tol > 0.0 && eps < P.tol) {
+                *P.done = 1;
+            }
+        }
+    }
+}
+
+template <typename real>
+cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st) {
+    const int cell_blocks = (int)((p.N + kUpdThreads - 1) / kUpdThreads);
+    const long long fb = (long long)p.F * p.B;
+    const int face_blocks = (int)((fb + kUpdThreads - 1) / kUpdThreads);
+    update_kernel<real><<<cell_blocks + face_blocks, kUpdThreads, 0, st>>>(p, cell_blocks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// heat flux q_c = sum_b v_b sum_d w_d s_d e_cbd (one warp per cell)
+// ---------------------------------------------------------------------------
+template <typename real>
+__global__ void flux_kernel(long long N, int B, int D, const int2 *__restrict__ cell,
+                            const real *__restrict__ e, const double *__restrict__ vws,
+                            const double *__restrict__ qshift, double *__restrict__ q) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= N) return;
+    const bool act = (cell[c].y & kRegionMask) != 0;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    if (act) {
+        const real *ec = e + c * (long long)B * D;
+        for (int i = lane; i < B * D; i += 32) {
+            const double ev = (double)ec[i];
+            q0 += vws[3 * i] * ev;
+            q1 += vws[3 * i + 1] * ev;
+            q2 += vws[3 * i + 2] * ev;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        q0 += __shfl_down_sync(0xffffffffu, q0, o);
+        q1 += __shfl_down_sync(0xffffffffu, q1, o);
+        q2 += __shfl_down_sync(0xffffffffu, q2, o);
+    }
+    if (lane == 0) {
+        // e is stored relative to C_b T_ref/(4 pi); add that part's flux back
+        q[3 * c] = act ? q0 + qshift[0] : 0.0;
+        q[3 * c + 1] = act ? q1 + qshift[1] : 0.0;
+        q[3 * c + 2] = act ? q2 + qshift[2] : 0.0;
+    }
+}
+
+template <typename real>
+cudaError_t launch_flux(long long N, int B, int D, const int2 *cell, const real *e, const double *vws,
+                        const double *qshift, double *q, cudaStream_t st) {
+    const long long threads = N * 32;
+    flux_kernel<real><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, B, D, cell, e, vws, qshift, q);
+    return cudaGetLastError();
+}
+
+// e_user[c][b][perm[d]] = e_int[c][b][d] + shift_b (absolute energy)
+template <typename real>
+__global__ void permute_e_kernel(long long total, int D, int B, const real *__restrict__ e_int,
+                                 const int *__restrict__ perm, const double *__restrict__ shift,
+                                 real *__restrict__ e_user) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int d = (int)(i % D);
+    const long long cb = i / D;
+    const int b = (int)(cb % B);
+    e_user[cb * D + perm[d]] = (real)((double)e_int[i] + shift[b]);
+}
+
+template <typename real>
+cudaError_t launch_permute_e(long long N, int B, int D, const real *e_int, const int *perm,
+                             const double *shift, real *e_user, cudaStream_t st) {
+    const long long total = N * B * D;
+    permute_e_kernel<real><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(total, D, B, e_int, perm, shift, e_user);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// gradients: dJ/dtau_b = sum_c (1/(tau_cb tau_b)) sum_d (mu - w Theta)(e - e0)
+//            dJ/dT_f   = sum over isothermal faces of side f of sum_b C_b/(4 pi) sum_d a_d mu_d
+//            dJ/dQ_amp = sum_c phi_c sum_b C_b/(4 pi sum C) sum_d mu_cbd
+// ---------------------------------------------------------------------------
+constexpr int kGradThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    return r;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constant__ GradParams<real> G,
+                                                            int cell_blocks) {
+    __shared__ double sh[kGradThreads / 32];
+    __shared__ int is_last;
+    const int NO = G.B + 7;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool is_cell = (int)blockIdx.x < cell_blocks;
+    const long long fi = (long long)(blockIdx.x - cell_blocks) * blockDim.x + threadIdx.x;
+    int r = 0;
+    if (is_cell && i < G.N) r = G.cell[i].y & kRegionMask;
+    double gq = 0.0;
+    for (int b = 0; b < G.B; ++b) {
+        double v = 0.0;
+        if (is_cell && r != 0) {
+            double gs = 0.0, ms = 0.0;
+            for (int s = 0; s < G.S; ++s) {
+                const long long o = ((long long)s * G.B + b) * G.N + i;
+                gs += (double)G.gpart[o];
+                ms += (double)G.apart[o];
+            }
+            v = gs * G.inv_tt[(r - 1) * G.B + b];
+            if (G.phi) gq += G.phi[i] * G.qcoef[b] * ms;
+        }
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) G.blockpart[(long long)blockIdx.x * NO + b] = v;
+    }
+    for (int f6 = 0; f6 < 6; ++f6) {
+        double v = 0.0;
+        if (!is_cell && fi < G.F && G.face_kind[fi] == 0 && G.face_side[fi] == f6) {
+            for (int b = 0; b < G.B; ++b) v += G.cb4pi[b] * G.msum[(long long)b * G.F + fi];
+        }
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) G.blockpart[(long long)blockIdx.x * NO + G.B + f6] = v;
+    }
+    gq = block_sum(gq, sh);
+    if (threadIdx.x == 0) {
+        G.blockpart[(long long)blockIdx.x * NO + G.B + 6] = gq;
+        __threadfence();
+        const unsigned ticket = atomicAdd(G.counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+        double acc = 0.0;
+        for (int blk = 0; blk < (int)gridDim.x; ++blk) acc += ((volatile double *)G.blockpart)[(long long)blk * NO + o];
+        G.out[o] = acc;
+    }
+    if (threadIdx.x == 0) *G.counter = 0u;
+}
+
+template <typename real>
+cudaError_t launch_grad(const GradParams<real> &g, cudaStream_t st) {
+    const int cell_blocks = (int)((g.N + kGradThreads - 1) / kGradThreads);
+    const int face_blocks = (g.F + kGradThreads - 1) / kGradThreads;
+    grad_kernel<real><<<cell_blocks + face_blocks, kGradThreads, 0, st>>>(g, cell_blocks);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_update<float>(const UpdateParams<float> &, cudaStream_t);
+template cudaError_t launch_update<double>(const UpdateParams<double> &, cudaStream_t);
+template cudaError_t launch_flux<float>(long long, int, int, const int2 *, const float *, const double *,
+                                        const double *, double *, cudaStream_t);
+template cudaError_t launch_flux<double>(long long, int, int, const int2 *, const double *, const double *,
+                                         const double *, double *, cudaStream_t);
+template cudaError_t launch_permute_e<float>(long long, int, int, const float *, const int *, const double *,
+                                             float *, cudaStream_t);
+template cudaError_t launch_permute_e<double>(long long, int, int, const double *, const int *,
+                                              const double *, double *, cudaStream_t);
+template cudaError_t launch_grad<float>(const GradParams<float> &, cudaStream_t);
+template cudaError_t launch_grad<double>(const GradParams<double> &, cudaStream_t);
+
+}  // namespace bte
