@@ -554,16 +554,16 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         dw = ws.tuned_dw ? ws.tuned_dw : cand[0];
     }
     if ((rc = ensure_subsets(p, ws, dw))) return rc;
-    const bool need_e = e_out || q_out || true;  // the adjoint needs e; kept on device
-    if (need_e || o->store_e_every_iter) CK(p, ws.e.ensure(sizeof(real) * (size_t)p->N * p->B * p->D));
-    // re-initialise after autotuning touched the work buffers
-    if ((rc = begin_state(p, o, ws, stream))) return rc;
-
+    // e of the final iterate is always regenerated on the device (outputs and
+    // the adjoint read it)
+    CK(p, ws.e.ensure(sizeof(real) * (size_t)p->N * p->B * p->D));
+    const double tol = o->tol;
     // one launch outside any capture sets the kernel's shared-memory attribute
     CK(p, enqueue_forward(p, ws, dw, 0, tol, false, true, stream));
+    // re-initialise after autotuning / the warm launch touched the work buffers
+    if ((rc = begin_state(p, o, ws, stream))) return rc;
     int poll = o->poll_every > 0 ? o->poll_every : 32;
     poll = std::max(2, poll + (poll & 1));
-    const double tol = o->tol;
     const bool store_every = o->store_e_every_iter != 0;
     // graph of `poll` iterations (even, so every replay starts at parity 0)
     auto key = std::make_tuple(dw, poll, tol, store_every ? 1 : 0);
