@@ -130,8 +130,10 @@ typedef struct {
     const double *T_wall;   /* 6 overrides of bcs->T (host), or NULL */
     void *stream;           /* cudaStream_t to run on (NULL = legacy default) */
     int poll_every;         /* iterations per device->host convergence poll (0 = auto) */
-    int dirs_per_lane;      /* sweep tile: directions held per lane (0 = autotuned) */
+    int dirs_per_lane;      /* sweep tile: directions per lane/warp (0 = autotuned) */
     int store_e_every_iter; /* 1: write e to HBM on every sweep; 0: only the final one */
+    int tile_kind;          /* 0 = autotuned; 1 = general wavefront kernel (any grid);
+                               2 = row-block kernel (unmasked 1D/2D, one region) */
 } bte_solve_opts;
 
 typedef struct {
@@ -141,8 +143,10 @@ typedef struct {
     double T_max;           /* max T of the last iterate (K) */
     double seconds;         /* device time of the iteration loop */
     double updates_per_s;   /* iterations * solid cells * B * D / seconds */
-    int dirs_per_lane;      /* tile used */
+    int dirs_per_lane;      /* tile used: directions per lane/warp */
     long long kernel_launches; /* kernels launched by the call (incl. early-exit ones) */
+    int tile_kind;          /* tile used: 1 general, 2 row-block (see bte_solve_opts) */
+    int dirs_per_cta;       /* tile used: directions per CTA */
 } bte_stats;
 
 /* Fill opts with defaults: FP32, tol 1e-6, max_iter 100000, T_init 300 K,

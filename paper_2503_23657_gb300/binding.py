@@ -58,14 +58,16 @@ class SolveOpts(ctypes.Structure):
                 ("T_init", ctypes.c_void_p), ("T_init_uniform", ctypes.c_double),
                 ("Q_amp", ctypes.c_double), ("tau", ctypes.c_void_p), ("T_wall", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("poll_every", ctypes.c_int),
-                ("dirs_per_lane", ctypes.c_int), ("store_e_every_iter", ctypes.c_int)]
+                ("dirs_per_lane", ctypes.c_int), ("store_e_every_iter", ctypes.c_int),
+                ("tile_kind", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("eps_T", ctypes.c_double),
                 ("T_max", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("updates_per_s", ctypes.c_double), ("dirs_per_lane", ctypes.c_int),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("tile_kind", ctypes.c_int),
+                ("dirs_per_cta", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -177,7 +179,7 @@ class Plan:
 
     def solve(self, T_out, q_out=None, e_out=None, precision=BTE_FP32, tol=1e-6, max_iter=100000,
               T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None,
-              poll_every=32, dirs_per_lane=0, store_e_every_iter=False, check=True):
+              poll_every=32, dirs_per_lane=0, store_e_every_iter=False, tile_kind=0, check=True):
         """Run bte_solve.  Buffers are numpy arrays (host) or torch tensors
         (host or CUDA) of the documented sizes.  Returns (rc, stats dict)."""
         p = self.problem
@@ -197,6 +199,7 @@ class Plan:
         o.poll_every = poll_every
         o.dirs_per_lane = dirs_per_lane
         o.store_e_every_iter = 1 if store_e_every_iter else 0
+        o.tile_kind = tile_kind
         st = Stats()
         rc = self._lib.bte_solve(self._h, ctypes.byref(o), _addr(T_out), _addr(q_out), _addr(e_out),
                                  ctypes.byref(st))

@@ -60,6 +60,38 @@ struct SweepParams {
     int ein_smem;                     // stage this band's boundary values in shared memory
 };
 
+// Parameters of the row-block sweep for unmasked 1D/2D grids with one region
+// (sweep2d.cuh).  One CTA per (direction chunk, band), warps_per_cta warps of
+// DW directions each.
+template <typename real>
+struct Sweep2DParams {
+    int nx, ny;
+    int B, D, F, S;                   // S = number of chunks
+    int warps_per_cta;
+    const real *__restrict__ tsrc;    // fwd: T - T_ref; adj: Theta [N]
+    const real *__restrict__ phi;     // fwd source profile [N] or null
+    const real *__restrict__ ein;     // [B][F] boundary values
+    real *__restrict__ part;          // [S][B][N]
+    real *__restrict__ fsum;          // [S][B][F]
+    real *__restrict__ e;             // [N][B][D] (store_e)
+    const Subset *__restrict__ sub;   // [S] chunks
+    const real *__restrict__ coef;    // [B][D][8]
+    const real *__restrict__ invdiag; // [B][D] (region 1)
+    const real *__restrict__ srck;    // [B] fwd C_b/(4 pi tau_b); adj 1/tau_b
+    const real *__restrict__ qb;      // [B]
+    const real *__restrict__ taub;    // [B] tau_b (region 1), for the fixed-point bound
+    const int *__restrict__ wall_face;  // [6][wall_stride] face index or -1
+    int wall_stride;
+    const int *__restrict__ done;
+    int store_e;
+    int acc_smem;                     // accumulate per-cell sums of the CTA in shared memory
+};
+
+template <typename real>
+cudaError_t launch_sweep2d(const Sweep2DParams<real> &p, int dirs_per_warp, int row_blocks, bool adjoint,
+                           cudaStream_t st);
+size_t sweep2d_smem(int nx, int ny, int acc_smem, int real_bytes);
+
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.
 template <typename real>
 struct UpdateParams {
@@ -117,7 +149,7 @@ cudaError_t launch_flux(long long N, int B, int D, const int2 *cell, const real 
                         double *q, cudaStream_t st);
 
 template <typename real>
-cudaError_t launch_permute_e(long long N, int B, int D, const real *e_int, const int *perm,
+cudaError_t launch_permute_e(long long N, int B, int D, const int2 *cell, const real *e_int, const int *perm,
                              const double *shift /*[B]*/, real *e_user, cudaStream_t st);
 
 // Gradient reduction after the final adjoint sweep (all FP64 accumulation).

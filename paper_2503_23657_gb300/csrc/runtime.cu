@@ -71,14 +71,15 @@ struct Workspace {
     bool init = false;
     DevBuf tdev[2], ein[2], T[2];      // forward state sets
     DevBuf thdev[2], mein[2], theta[2];  // adjoint state sets
-    DevBuf ein_fixed, part, fsum, e, gpart, phi, coef, invdiag, srck_f, srck_a, qb, cb4pi;
+    DevBuf ein_fixed, part, fsum, e, gpart, phi, coef, invdiag, srck_f, srck_a, qb, cb4pi, taub;
     DevBuf wgt_f, wgt_a, Kinv, scale_f, scale_a, msum, g, grad_out, inv_tt, qcoef, phi64, vws, qshift, q,
         eshift, tfwd_dummy;
     // direction subsets per tile width
-    std::map<int, std::pair<std::vector<Subset>, std::vector<Subset>>> subsets;  // dw -> (fwd, adj)
+    std::map<int, std::pair<std::vector<Subset>, std::vector<Subset>>> subsets;  // tile -> (fwd, adj)
     std::map<int, std::pair<DevBuf *, DevBuf *>> dsub;
     std::vector<std::unique_ptr<DevBuf>> subbufs;
-    int tuned_dw = 0;
+    std::map<int, int> tuned;  // tile request -> chosen tile
+    DevBuf wall;  // [6][wall_stride] face index of each wall position (-1: none)
     // graph cache
     cudaGraphExec_t graph = nullptr;
     std::tuple<int, int, double, int> graph_key{-1, -1, 0.0, -1};
@@ -122,7 +123,9 @@ struct bte_plan {
     bool solved = false;
     int solved_precision = -1;
     int solved_iters = 0;
-    int solved_dw = 0;
+    int solved_tile = 0;
+    int wall_stride = 1;
+    std::vector<int> wall_face;
     bool e_current = false;
     cudaStream_t stream = nullptr;  // stream of the last solve (used by the adjoint)
     double T_ref = 300.0;
@@ -175,6 +178,14 @@ bool is_device_ptr(const void *ptr) {
 
 long long cell_index(const bte_plan *p, int i, int j, int k) { return i + (long long)p->nx * (j + (long long)p->ny * k); }
 
+// A sweep tile: kernel kind (0 = general wavefront kernel, 1 = row-block 2D
+// kernel), directions per lane/warp (dw) and directions per CTA chunk (cw).
+struct Tile {
+    int kind, dw, cw;
+};
+inline int tile_id(int kind, int dw, int cw) { return kind * 100000 + cw * 100 + dw; }
+inline Tile tile_of(int id) { return Tile{id / 100000, id % 100, (id / 100) % 1000}; }
+
 // Directions of one orientation group split into subsets of at most dw.
 std::vector<Subset> make_subsets(const bte_plan *p, int dw, bool flip) {
     std::vector<Subset> out;
@@ -201,16 +212,61 @@ int tile_layers(const bte_plan *p) {
     return 0;
 }
 
-std::vector<int> tile_candidates(const bte_plan *p) {
+// Row-block 2D kernel: unmasked 1D/2D grid, one region, ny <= 256, the
+// per-cell source (and for FP32 the per-cell accumulator) fits in shared memory.
+bool rowblock_ok(const bte_plan *p, int real_bytes, int *acc_smem) {
+    if (p->dim > 2 || p->ny > 256 || p->n_active != p->N) return false;
+    for (long long c = 0; c < p->N; ++c)
+        if (p->mask[c] != 1) return false;
+    const size_t lim = 200 * 1024;
+    if (real_bytes == 4 && sweep2d_smem(p->nx, p->ny, 1, 4) <= lim) {
+        *acc_smem = 1;
+        return true;
+    }
+    *acc_smem = 0;
+    return sweep2d_smem(p->nx, p->ny, 0, real_bytes) <= lim;
+}
+
+int rowblock_rb(const bte_plan *p) {
+    for (int rb : {1, 2, 4, 8})
+        if (32 * rb >= p->ny) return rb;
+    return 0;
+}
+
+int max_group(const bte_plan *p) {
+    int m = 0;
+    for (int c : p->groups_cnt) m = std::max(m, c);
+    return m;
+}
+
+// Candidate tiles for a precision; kind_req 0 = any, 1 = general only, 2 = row-block only.
+std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req = 0, int dw_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
-    if (lz == 0) return out;
-    const bool z = p->dim == 3;
-    const int WY = (p->ny + 31) / 32;
-    const int WZ = z ? (p->nz + lz - 1) / lz : 1;
-    for (int dw : {4, 8, 16}) {
-        const int mt = sweep_max_threads(dw, lz, z);
-        if (mt > 0 && WY * WZ * 32 <= mt) out.push_back(dw);
+    if (lz != 0 && kind_req != 2) {
+        const bool z = p->dim == 3;
+        const int WY = (p->ny + 31) / 32;
+        const int WZ = z ? (p->nz + lz - 1) / lz : 1;
+        for (int dw : {4, 8, 16}) {
+            const int mt = sweep_max_threads(dw, lz, z);
+            if (mt > 0 && WY * WZ * 32 <= mt && (!dw_req || dw == dw_req)) out.push_back(tile_id(0, dw, dw));
+        }
+    }
+    int acc = 0;
+    if (kind_req != 1 && rowblock_ok(p, real_bytes, &acc)) {
+        const int gmax = max_group(p);
+        for (int dw : {1, 2, 4, 8}) {
+            if (dw_req && dw != dw_req) continue;
+            if (!acc) {
+                out.push_back(tile_id(1, dw, dw));
+                continue;
+            }
+            for (int warps : {1, 2, 4, 8, 16}) {
+                const int cw = dw * warps;
+                if (cw > gmax * 2 && warps > 1) break;
+                out.push_back(tile_id(1, dw, cw));
+            }
+        }
     }
     return out;
 }
@@ -223,24 +279,29 @@ template <>
 Workspace<double> &ws_of<double>(bte_plan *p) { return p->ws64; }
 
 template <typename real>
-int ensure_subsets(bte_plan *p, Workspace<real> &ws, int dw) {
-    if (ws.dsub.count(dw)) return BTE_OK;
-    auto f = make_subsets(p, dw, false);
-    auto a = make_subsets(p, dw, true);
-    ws.subsets[dw] = {f, a};
+int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
+    if (ws.dsub.count(tid)) return BTE_OK;
+    const int cw = tile_of(tid).cw;
+    auto f = make_subsets(p, cw, false);
+    auto a = make_subsets(p, cw, true);
+    ws.subsets[tid] = {f, a};
     ws.subbufs.emplace_back(new DevBuf());
     DevBuf *bf = ws.subbufs.back().get();
     ws.subbufs.emplace_back(new DevBuf());
     DevBuf *ba = ws.subbufs.back().get();
     CK(p, upload(*bf, f));
     CK(p, upload(*ba, a));
-    ws.dsub[dw] = {bf, ba};
+    ws.dsub[tid] = {bf, ba};
     return BTE_OK;
 }
 
+// Partial sets a tile can produce at most (general tiles >= 4 directions per
+// set; the row-block kernel down to 1 direction per set).
 int max_subsets(const bte_plan *p) {
+    int dummy = 0;
+    const int per = (rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy)) ? 1 : 4;
     int s = 0;
-    for (size_t g = 0; g < p->groups_cnt.size(); ++g) s += (p->groups_cnt[g] + 3) / 4;
+    for (size_t g = 0; g < p->groups_cnt.size(); ++g) s += (p->groups_cnt[g] + per - 1) / per;
     return s;
 }
 
@@ -250,7 +311,7 @@ int upload_tables(bte_plan *p, Workspace<real> &ws) {
     const int B = p->B, D = p->D, R = p->R;
     const std::vector<double> &tau = p->cur_tau;
     std::vector<real> coef((size_t)B * D * 8), invd((size_t)R * B * D), srf((size_t)R * B), sra((size_t)R * B),
-        qb(B), cb(B);
+        qb(B), cb(B), tb(B);
     std::vector<double> wf((size_t)R * B), wa((size_t)R * B), Kinv(R), scf(6 * B), sca(6 * B), itt((size_t)R * B),
         qc(B), vws((size_t)B * D * 3), qsh(3, 0.0), esh(B);
     double Csum = 0.0;
@@ -273,6 +334,7 @@ int upload_tables(bte_plan *p, Workspace<real> &ws) {
             for (int ax = 0; ax < 3; ++ax) vws[((size_t)b * D + d) * 3 + ax] = p->v[b] * p->w[d] * p->s[3 * d + ax];
         }
         qb[b] = (real)(p->C[b] * p->cur_Q / (kFourPi * Csum));
+        tb[b] = (real)(tau[b] * p->tau_scale[0]);
         cb[b] = (real)(p->C[b] / kFourPi);
         qc[b] = p->C[b] / (kFourPi * Csum);
         esh[b] = p->C[b] * p->T_ref / kFourPi;
@@ -313,6 +375,7 @@ int upload_tables(bte_plan *p, Workspace<real> &ws) {
     CK(p, upload(ws.srck_a, sra));
     CK(p, upload(ws.qb, qb));
     CK(p, upload(ws.cb4pi, cb));
+    CK(p, upload(ws.taub, tb));
     CK(p, upload(ws.wgt_f, wf));
     CK(p, upload(ws.wgt_a, wa));
     CK(p, upload(ws.Kinv, Kinv));
@@ -350,7 +413,7 @@ int ensure_workspace(bte_plan *p, Workspace<real> &ws) {
 // launches of one iteration
 // ---------------------------------------------------------------------------
 template <typename real>
-SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int dw, bool adj) {
+SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int tid, bool adj) {
     SweepParams<real> sp{};
     sp.nx = p->nx;
     sp.ny = p->ny;
@@ -372,9 +435,9 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int dw, bool ad
     sp.qb = ws.qb.template as<real>();
     sp.phi = p->phi.empty() ? nullptr : ws.phi.template as<real>();
     sp.cb4pi = ws.cb4pi.template as<real>();
-    auto pr = ws.dsub.at(dw);
+    auto pr = ws.dsub.at(tid);
     sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
-    sp.S = (int)ws.subsets.at(dw).first.size();
+    sp.S = (int)ws.subsets.at(tid).first.size();
     sp.done = p->d_status.as<int>();
     // stage the band's boundary values in shared memory when they fit next to
     // the exchange buffers (<= 200 KB of the 227 KB per CTA)
@@ -385,17 +448,17 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int dw, bool ad
 }
 
 template <typename real>
-UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int dw, bool adj, double tol) {
+UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool adj, double tol) {
     UpdateParams<real> u{};
     u.N = p->N;
     u.B = p->B;
-    u.S = (int)ws.subsets.at(dw).first.size();
+    u.S = (int)ws.subsets.at(tid).first.size();
     u.F = p->F;
     u.R = p->R;
     u.adjoint = adj ? 1 : 0;
     u.T_ref = p->T_ref;
     u.cell = p->d_cell.as<int2>();
-    auto pr = ws.dsub.at(dw);
+    auto pr = ws.dsub.at(tid);
     u.sub = (adj ? pr.second : pr.first)->template as<Subset>();
     u.part = ws.part.template as<real>();
     u.fsum = ws.fsum.template as<real>();
@@ -422,17 +485,65 @@ UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int dw, bool 
 }
 
 template <typename real>
-cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int dw, int parity, double tol, bool store_e,
-                            bool replay, cudaStream_t stream) {
-    SweepParams<real> sp = sweep_params(p, ws, dw, false);
-    sp.tsrc = ws.tdev[parity].template as<real>();
-    sp.ein = ws.ein[parity].template as<real>();
+Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bool adj) {
+    const Tile tl = tile_of(tid);
+    Sweep2DParams<real> sp{};
+    sp.nx = p->nx;
+    sp.ny = p->ny;
+    sp.B = p->B;
+    sp.D = p->D;
+    sp.F = std::max(p->F, 1);
+    sp.warps_per_cta = tl.cw / tl.dw;
+    sp.part = ws.part.template as<real>();
+    sp.fsum = ws.fsum.template as<real>();
+    sp.coef = ws.coef.template as<real>();
+    sp.invdiag = ws.invdiag.template as<real>();
+    sp.srck = adj ? ws.srck_a.template as<real>() : ws.srck_f.template as<real>();
+    sp.qb = ws.qb.template as<real>();
+    sp.taub = ws.taub.template as<real>();
+    sp.phi = p->phi.empty() ? nullptr : ws.phi.template as<real>();
+    auto pr = ws.dsub.at(tid);
+    sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
+    sp.S = (int)ws.subsets.at(tid).first.size();
+    sp.wall_face = ws.wall.template as<int>();
+    sp.wall_stride = p->wall_stride;
+    sp.done = p->d_status.as<int>();
+    int acc = 0;
+    rowblock_ok(p, (int)sizeof(real), &acc);
+    sp.acc_smem = acc;
+    return sp;
+}
+
+// One sweep (all bands x directions x cells) with the given tile.
+template <typename real>
+cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool adj, const real *tsrc,
+                              const real *ein, bool store_e, bool use_done, cudaStream_t stream) {
+    const Tile tl = tile_of(tid);
+    if (tl.kind == 1) {
+        Sweep2DParams<real> sp = sweep2d_params(p, ws, tid, adj);
+        sp.tsrc = tsrc;
+        sp.ein = ein;
+        sp.store_e = store_e ? 1 : 0;
+        sp.e = ws.e.template as<real>();
+        if (!use_done) sp.done = nullptr;
+        return launch_sweep2d<real>(sp, tl.dw, rowblock_rb(p), adj, stream);
+    }
+    SweepParams<real> sp = sweep_params(p, ws, tid, adj);
+    sp.tsrc = tsrc;
+    sp.ein = ein;
     sp.store_e = store_e ? 1 : 0;
     sp.e = ws.e.template as<real>();
-    if (replay) sp.done = nullptr;
-    cudaError_t e = launch_sweep<real>(sp, dw, tile_layers(p), p->dim == 3, false, stream);
+    if (!use_done) sp.done = nullptr;
+    return launch_sweep<real>(sp, tl.dw, tile_layers(p), p->dim == 3, adj, stream);
+}
+
+template <typename real>
+cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int tid, int parity, double tol, bool store_e,
+                            bool replay, cudaStream_t stream) {
+    cudaError_t e = launch_tile_sweep(p, ws, tid, false, ws.tdev[parity].template as<real>(),
+                                      ws.ein[parity].template as<real>(), store_e, !replay, stream);
     if (e != cudaSuccess || replay) return e;
-    UpdateParams<real> u = update_params(p, ws, dw, false, tol);
+    UpdateParams<real> u = update_params(p, ws, tid, false, tol);
     u.x_in = ws.T[parity].template as<double>();
     u.x_out = ws.T[parity ^ 1].template as<double>();
     u.xdev_out = ws.tdev[parity ^ 1].template as<real>();
@@ -488,24 +599,20 @@ int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaS
     return BTE_OK;
 }
 
+// Pick the fastest candidate tile by timing whole iterations (sweep +
+// update) on the current state; the caller re-initialises the state after.
 template <typename real>
-int autotune(bte_plan *p, Workspace<real> &ws, cudaStream_t stream) {
-    std::vector<int> cand = tile_candidates(p);
+int autotune(bte_plan *p, Workspace<real> &ws, const std::vector<int> &cand, cudaStream_t stream) {
     if (cand.empty()) return 0;
     if (cand.size() == 1) return cand[0];
     float best = 1e30f;
-    int best_dw = cand[0];
-    for (int dw : cand) {
-        if (ensure_subsets(p, ws, dw) != BTE_OK) return 0;
-        // two warm-up sweeps, then the median-free minimum of three
+    int best_tid = cand[0];
+    for (int tid : cand) {
+        if (ensure_subsets(p, ws, tid) != BTE_OK) return 0;
         float tmin = 1e30f;
-        for (int rep = 0; rep < 5; ++rep) {
+        for (int rep = 0; rep < 6; ++rep) {
             cudaEventRecord(p->ev0, stream);
-            SweepParams<real> sp = sweep_params(p, ws, dw, false);
-            sp.tsrc = ws.tdev[0].template as<real>();
-            sp.ein = ws.ein[0].template as<real>();
-            sp.done = nullptr;
-            if (launch_sweep<real>(sp, dw, tile_layers(p), p->dim == 3, false, stream) != cudaSuccess) {
+            if (enqueue_forward(p, ws, tid, rep & 1, 0.0, false, false, stream) != cudaSuccess) {
                 cudaGetLastError();
                 tmin = 1e30f;
                 break;
@@ -518,10 +625,10 @@ int autotune(bte_plan *p, Workspace<real> &ws, cudaStream_t stream) {
         }
         if (tmin < best) {
             best = tmin;
-            best_dw = dw;
+            best_tid = tid;
         }
     }
-    return best_dw;
+    return best_tid;
 }
 
 template <typename real>
@@ -542,17 +649,20 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     p->cur_Q = o->Q_amp;
     if ((rc = begin_state(p, o, ws, stream))) return rc;
     if ((rc = upload_tables(p, ws))) return rc;
-    // tile
-    std::vector<int> cand = tile_candidates(p);
-    if (cand.empty()) return fail(p, BTE_EINVAL, "grid too large for the sweep tiles (ny/nz)");
-    int dw = o->dirs_per_lane;
-    if (dw) {
-        if (std::find(cand.begin(), cand.end(), dw) == cand.end())
-            return fail(p, BTE_EINVAL, "dirs_per_lane not supported for this grid");
+    // tile: the caller's restriction, then the autotuned choice (cached)
+    if (o->tile_kind < 0 || o->tile_kind > 2) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1 or 2");
+    std::vector<int> cand = tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane);
+    if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
+    const int tkey = o->tile_kind * 100 + o->dirs_per_lane;
+    int tid;
+    if (ws.tuned.count(tkey)) {
+        tid = ws.tuned[tkey];
     } else {
-        if (!ws.tuned_dw) ws.tuned_dw = autotune(p, ws, stream);
-        dw = ws.tuned_dw ? ws.tuned_dw : cand[0];
+        tid = autotune(p, ws, cand, stream);
+        if (!tid) return fail(p, BTE_ECUDA, "tile autotuning failed");
+        ws.tuned[tkey] = tid;
     }
+    const int dw = tid;
     if ((rc = ensure_subsets(p, ws, dw))) return rc;
     // e of the final iterate is always regenerated on the device (outputs and
     // the adjoint read it)
@@ -630,7 +740,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     if (e_out && n > 0) {
         const size_t ne = (size_t)p->N * p->B * p->D;
         if (is_device_ptr(e_out)) {
-            CK(p, launch_permute_e<real>(p->N, p->B, p->D, ws.e.template as<real>(), p->d_perm.as<int>(),
+            CK(p, launch_permute_e<real>(p->N, p->B, p->D, p->d_cell.as<int2>(), ws.e.template as<real>(), p->d_perm.as<int>(),
                                          ws.eshift.template as<double>(), (real *)e_out, stream));
             launches += 1;
         } else {
@@ -640,8 +750,9 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
             std::vector<real> tmp(p->D);
             for (size_t cb = 0; cb < (size_t)p->N * p->B; ++cb) {
                 const int b = (int)(cb % p->B);
-                const double sh = p->C[b] * p->T_ref / kFourPi;
-                for (int d = 0; d < p->D; ++d) tmp[p->perm[d]] = (real)((double)eo[cb * p->D + d] + sh);
+                const double sh = p->mask[cb / p->B] ? p->C[b] * p->T_ref / kFourPi : 0.0;
+                for (int d = 0; d < p->D; ++d)
+                    tmp[p->perm[d]] = p->mask[cb / p->B] ? (real)((double)eo[cb * p->D + d] + sh) : (real)0;
                 std::memcpy(eo + cb * p->D, tmp.data(), sizeof(real) * p->D);
             }
         }
@@ -651,7 +762,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     p->stream = stream;
     p->solved_precision = (sizeof(real) == 4) ? BTE_FP32 : BTE_FP64;
     p->solved_iters = n;
-    p->solved_dw = dw;
+    p->solved_tile = tid;
     if (st) {
         st->iterations = n;
         st->converged = converged ? 1 : 0;
@@ -659,7 +770,9 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         st->T_max = p->h_status->last[1];
         st->seconds = ms * 1e-3;
         st->updates_per_s = st->seconds > 0 ? (double)n * p->n_active * p->B * p->D / st->seconds : 0.0;
-        st->dirs_per_lane = dw;
+        st->dirs_per_lane = tile_of(tid).dw;
+        st->tile_kind = tile_of(tid).kind + 1;
+        st->dirs_per_cta = tile_of(tid).cw;
         st->kernel_launches = launches;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the temperature update");
@@ -673,6 +786,18 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
 template <typename real>
 cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity, double tol, bool final_pass,
                             cudaStream_t stream) {
+    if (!final_pass && tile_of(dw).kind == 1) {
+        cudaError_t e = launch_tile_sweep(p, ws, dw, true, ws.thdev[parity].template as<real>(),
+                                          ws.mein[parity].template as<real>(), false, true, stream);
+        if (e != cudaSuccess) return e;
+        UpdateParams<real> u = update_params(p, ws, dw, true, tol);
+        u.eps_hist = nullptr;
+        u.x_in = ws.theta[parity].template as<double>();
+        u.x_out = ws.theta[parity ^ 1].template as<double>();
+        u.xdev_out = ws.thdev[parity ^ 1].template as<real>();
+        u.ein_out = ws.mein[parity ^ 1].template as<real>();
+        return launch_update<real>(u, stream);
+    }
     SweepParams<real> sp = sweep_params(p, ws, dw, true);
     sp.tsrc = ws.thdev[parity].template as<real>();
     sp.ein = ws.mein[parity].template as<real>();
@@ -701,7 +826,12 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
               bte_stats *st) {
     cudaStream_t stream = p->stream;
     Workspace<real> &ws = ws_of<real>(p);
-    const int dw = p->solved_dw;
+    const int dw = p->solved_tile;
+    // the final gradient pass reads e and runs on a general tile
+    std::vector<int> gen = tile_candidates(p, (int)sizeof(real), 1, 0);
+    if (gen.empty()) return fail(p, BTE_EINVAL, "no general sweep tile for the gradient pass");
+    const int gtile = gen[0];
+    if (int rc2 = ensure_subsets(p, ws, gtile)) return rc2;
     const long long N = p->N;
     const int B = p->B, F = std::max(p->F, 1);
     const size_t S = max_subsets(p);
@@ -798,11 +928,11 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     const bool converged = tol > 0.0 && p->h_status->done && !bad;
     // final pass: one more transposed sweep from Theta^n that also forms the
     // gradient partials against the forward state, then the face sums
-    CK(p, enqueue_adjoint(p, ws, dw, n & 1, tol, true, stream));
+    CK(p, enqueue_adjoint(p, ws, gtile, n & 1, tol, true, stream));
     GradParams<real> gp{};
     gp.N = N;
     gp.B = B;
-    gp.S = (int)ws.subsets.at(dw).first.size();
+    gp.S = (int)ws.subsets.at(gtile).first.size();
     gp.F = p->F;
     gp.cell = p->d_cell.as<int2>();
     gp.apart = ws.part.template as<real>();
@@ -845,7 +975,9 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         st->T_max = p->h_status->last[1];
         st->seconds = ms * 1e-3;
         st->updates_per_s = st->seconds > 0 ? (double)(n + 1) * p->n_active * p->B * p->D / st->seconds : 0.0;
-        st->dirs_per_lane = dw;
+        st->dirs_per_lane = tile_of(dw).dw;
+        st->tile_kind = tile_of(dw).kind + 1;
+        st->dirs_per_cta = tile_of(dw).cw;
         st->kernel_launches = launches + 3;  // final sweep + update + gradient reduction
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the adjoint update");
@@ -858,9 +990,9 @@ int profile_t(bte_plan *p, int reps, double *ms_per_sweep) {
     Workspace<real> &ws = ws_of<real>(p);
     cudaStream_t stream = p->stream;
     const int par = (p->solved_iters - 1) & 1;
-    for (int i = 0; i < 2; ++i) CK(p, enqueue_forward(p, ws, p->solved_dw, par, 0.0, false, true, stream));
+    for (int i = 0; i < 2; ++i) CK(p, enqueue_forward(p, ws, p->solved_tile, par, 0.0, false, true, stream));
     CK(p, cudaEventRecord(p->ev0, stream));
-    for (int i = 0; i < reps; ++i) CK(p, enqueue_forward(p, ws, p->solved_dw, par, 0.0, false, true, stream));
+    for (int i = 0; i < reps; ++i) CK(p, enqueue_forward(p, ws, p->solved_tile, par, 0.0, false, true, stream));
     CK(p, cudaEventRecord(p->ev1, stream));
     CK(p, cudaEventSynchronize(p->ev1));
     float ms = 0.f;
@@ -994,6 +1126,20 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
                 p->cellinfo[c] = make_int2(base, flags);
             }
     if (p->n_active == 0) return fail(nullptr, BTE_EINVAL, "mask has no solid cell");
+    // domain-wall position -> face index (used by the row-block 2D kernel)
+    p->wall_stride = std::max((long long)p->ny * p->nz, std::max((long long)p->nx * p->nz, (long long)p->nx * p->ny));
+    p->wall_face.assign((size_t)6 * p->wall_stride, -1);
+    for (int f = 0; f < p->F; ++f) {
+        const long long c = p->face_cell[f];
+        const int side = p->face_side[f];
+        const int i = (int)(c % p->nx), j = (int)((c / p->nx) % p->ny), k = (int)(c / ((long long)p->nx * p->ny));
+        const int a = side / 2;
+        const int idx[3] = {i, j, k};
+        const bool on_wall = (side & 1) ? idx[a] == g->n[a] - 1 : idx[a] == 0;
+        if (!on_wall) continue;
+        long long pos = a == 0 ? j + (long long)p->ny * k : (a == 1 ? i + (long long)p->nx * k : i + (long long)p->nx * j);
+        p->wall_face[(size_t)side * p->wall_stride + pos] = f;
+    }
     if (!anchored) return fail(nullptr, BTE_EINVAL, "no isothermal face touches the solid (temperature undetermined)");
     if (q_profile) {
         p->phi.assign(q_profile, q_profile + p->N);
@@ -1044,10 +1190,12 @@ int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands, c
     CKC(upload(p->d_face_side, p->face_side));
     CKC(upload(p->d_face_kind, p->face_kind));
     CKC(upload(p->d_perm, p->perm));
+    CKC(upload(p->ws32.wall, p->wall_face));
+    CKC(upload(p->ws64.wall, p->wall_face));
     CKC(p->d_status.ensure(sizeof(Status)));
     CKC(p->d_counter.ensure(sizeof(unsigned int)));
     CKC(cudaMemset(p->d_counter.p, 0, sizeof(unsigned int)));
-    const long long nblk = (p->N + 255) / 256 + ((long long)std::max(p->F, 1) * p->B + 255) / 256 + 16;
+    const long long nblk = (p->N + 31) / 32 + ((long long)std::max(p->F, 1) * p->B + 255) / 256 + 16;
     CKC(p->d_blockpart.ensure(sizeof(double) * 2 * nblk));
     p->hist_cap = 1 << 16;
     CKC(p->d_hist.ensure(sizeof(double) * p->hist_cap));

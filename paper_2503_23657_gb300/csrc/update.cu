@@ -48,33 +48,59 @@ __device__ __forceinline__ void block_reduce2(double &a, double &m, double *sh) 
     }
 }
 
+// Threads of a cell block are laid out [band slot y][cell x] (32 cells x 8
+// band slots): each thread sums the partial sets of its bands (within a band
+// in the sweep precision, i.e. over directions), the weighted band sums are
+// combined in FP64 in a fixed order.
+constexpr int kCellsPerBlock = 32;
+constexpr int kBandSlots = kUpdThreads / kCellsPerBlock;
+
 template <typename real>
 __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_constant__ UpdateParams<real> P,
                                                              int cell_blocks) {
     if (!P.ignore_done && *((volatile int *)P.done) != 0) return;
     __shared__ double sh[2 * (kUpdThreads / 32)];
+    __shared__ double sband[kBandSlots][kCellsPerBlock];
     __shared__ int is_last;
     double ss = 0.0, mx = -INFINITY;
     if ((int)blockIdx.x < cell_blocks) {
-        const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        if (c < P.N) {
-            const int2 ci = P.cell[c];
-            const int r = ci.y & kRegionMask;
-            if (r != 0) {
-                double acc = 0.0;
-                for (int b = 0; b < P.B; ++b) {
-                    double sb = 0.0;
-                    for (int s = 0; s < P.S; ++s) sb += (double)P.part[((long long)s * P.B + b) * P.N + c];
-                    acc += sb * P.wgt[(r - 1) * P.B + b];
+        const int tx = threadIdx.x % kCellsPerBlock;
+        const int ty = threadIdx.x / kCellsPerBlock;
+        const long long c = (long long)blockIdx.x * kCellsPerBlock + tx;
+        int r = 0;
+        if (c < P.N) r = P.cell[c].y & kRegionMask;
+        double acc = 0.0;
+        if (r != 0) {
+            for (int b = ty; b < P.B; b += kBandSlots) {
+                const real *pp = P.part + (long long)b * P.N + c;
+                const long long stride = (long long)P.B * P.N;
+                real s0 = real(0), s1 = real(0), s2 = real(0), s3 = real(0);
+                int s = 0;
+                for (; s + 4 <= P.S; s += 4) {
+                    s0 += pp[(s + 0) * stride];
+                    s1 += pp[(s + 1) * stride];
+                    s2 += pp[(s + 2) * stride];
+                    s3 += pp[(s + 3) * stride];
                 }
+                for (; s < P.S; ++s) s0 += pp[s * stride];
+                acc += (double)((s0 + s1) + (s2 + s3)) * P.wgt[(r - 1) * P.B + b];
+            }
+        }
+        sband[ty][tx] = acc;
+        __syncthreads();
+        if (ty == 0 && c < P.N) {
+            if (r != 0) {
+                double tot = 0.0;
+#pragma unroll
+                for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
                 double xn;
                 if (!P.adjoint) {
-                    const double dev = acc * P.Kinv[r - 1];
+                    const double dev = tot * P.Kinv[r - 1];
                     xn = P.T_ref + dev;
                     P.xdev_out[c] = (real)dev;
                     mx = xn;
                 } else {
-                    xn = (P.g[c] + acc) * P.Kinv[r - 1];
+                    xn = (P.g[c] + tot) * P.Kinv[r - 1];
                     P.xdev_out[c] = (real)xn;
                     mx = fabs(xn);
                 }
@@ -121,8 +147,8 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_consta
     if (!is_last) return;
     __threadfence();
     // last block: combine in block order (deterministic)
-    double tss = 0.0, tmx = -INFINITY;
     if (threadIdx.x == 0) {
+        double tss = 0.0, tmx = -INFINITY;
         for (int i = 0; i < cell_blocks; ++i) {
             tss += ((volatile double *)P.blockpart)[2 * i];
             tmx = fmax(tmx, ((volatile double *)P.blockpart)[2 * i + 1]);
@@ -148,7 +174,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_consta
 
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st) {
-    const int cell_blocks = (int)((p.N + kUpdThreads - 1) / kUpdThreads);
+    const int cell_blocks = (int)((p.N + kCellsPerBlock - 1) / kCellsPerBlock);
     const long long fb = (long long)p.F * p.B;
     const int face_blocks = (int)((fb + kUpdThreads - 1) / kUpdThreads);
     update_kernel<real><<<cell_blocks + face_blocks, kUpdThreads, 0, st>>>(p, cell_blocks);
@@ -198,24 +224,26 @@ cudaError_t launch_flux(long long N, int B, int D, const int2 *cell, const real 
     return cudaGetLastError();
 }
 
-// e_user[c][b][perm[d]] = e_int[c][b][d] + shift_b (absolute energy)
+// e_user[c][b][perm[d]] = e_int[c][b][d] + shift_b (absolute energy); 0 in void cells
 template <typename real>
-__global__ void permute_e_kernel(long long total, int D, int B, const real *__restrict__ e_int,
-                                 const int *__restrict__ perm, const double *__restrict__ shift,
-                                 real *__restrict__ e_user) {
+__global__ void permute_e_kernel(long long total, int D, int B, const int2 *__restrict__ cell,
+                                 const real *__restrict__ e_int, const int *__restrict__ perm,
+                                 const double *__restrict__ shift, real *__restrict__ e_user) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int d = (int)(i % D);
     const long long cb = i / D;
     const int b = (int)(cb % B);
-    e_user[cb * D + perm[d]] = (real)((double)e_int[i] + shift[b]);
+    const bool act = (cell[cb / B].y & kRegionMask) != 0;
+    e_user[cb * D + perm[d]] = act ? (real)((double)e_int[i] + shift[b]) : (real)0;
 }
 
 template <typename real>
-cudaError_t launch_permute_e(long long N, int B, int D, const real *e_int, const int *perm,
+cudaError_t launch_permute_e(long long N, int B, int D, const int2 *cell, const real *e_int, const int *perm,
                              const double *shift, real *e_user, cudaStream_t st) {
     const long long total = N * B * D;
-    permute_e_kernel<real><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(total, D, B, e_int, perm, shift, e_user);
+    permute_e_kernel<real><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(total, D, B, cell, e_int, perm, shift,
+                                                                            e_user);
     return cudaGetLastError();
 }
 
@@ -306,9 +334,9 @@ template cudaError_t launch_flux<float>(long long, int, int, const int2 *, const
                                         const double *, double *, cudaStream_t);
 template cudaError_t launch_flux<double>(long long, int, int, const int2 *, const double *, const double *,
                                          const double *, double *, cudaStream_t);
-template cudaError_t launch_permute_e<float>(long long, int, int, const float *, const int *, const double *,
-                                             float *, cudaStream_t);
-template cudaError_t launch_permute_e<double>(long long, int, int, const double *, const int *,
+template cudaError_t launch_permute_e<float>(long long, int, int, const int2 *, const float *, const int *,
+                                             const double *, float *, cudaStream_t);
+template cudaError_t launch_permute_e<double>(long long, int, int, const int2 *, const double *, const int *,
                                               const double *, double *, cudaStream_t);
 template cudaError_t launch_grad<float>(const GradParams<float> &, cudaStream_t);
 template cudaError_t launch_grad<double>(const GradParams<double> &, cudaStream_t);

@@ -57,6 +57,24 @@ def test_fp64_adjoint_matches_oracle_and_fd(bte, name, dim, kw):
     assert g_Q == pytest.approx(fd["g_Q"], rel=1e-3)
 
 
+def test_adjoint_rowblock_matches_general(bte):
+    """2D unmasked square: the row-block kernel's adjoint equals the general
+    kernel's (FP64)."""
+    p = bi.square_2d(n=20, L=0.3e-6)
+    p = p.copy(C=p.C[:4], v=p.v[:4], tau=p.tau[:4])
+    plan = bte.Plan(p)
+    g = np.zeros(p.n_cells)
+    g[[5, 77, 230, 399]] = [1.0, -0.5, 0.25, 2.0]
+    out = []
+    for kind in (1, 2):
+        T = np.zeros(p.n_cells)
+        plan.solve(T, precision=bte.BTE_FP64, tol=1e-13, tile_kind=kind)
+        rc, g_tau, g_Tw, g_Q, st = plan.adjoint(g, tol=1e-13)
+        out.append((g_tau, g_Tw))
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-9)
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-9, atol=1e-15)
+
+
 @pytest.mark.parametrize("name,dim,kw", CASES, ids=[c[0] for c in CASES])
 def test_fp32_adjoint_within_fd_tolerance(bte, name, dim, kw):
     p, ref, probes, T_obs = _setup(dim, kw)

@@ -28,6 +28,11 @@ def bte():
     return m
 
 
+def rowblock_eligible(p):
+    """The row-block kernel handles unmasked 1D/2D grids with one region."""
+    return p.dim <= 2 and bool(np.all(p.mask == 1)) and p.n[1] <= 256
+
+
 def rel(a, b, mask=None):
     if mask is not None:
         a, b = a[mask], b[mask]
@@ -47,14 +52,18 @@ TINY = [
 
 @pytest.mark.parametrize("name,dim,kw", TINY, ids=[t[0] for t in TINY])
 @pytest.mark.parametrize("k", [1, 7])
-def test_fp64_fixed_iterations(bte, name, dim, kw, k):
+@pytest.mark.parametrize("kind", [1, 2])
+def test_fp64_fixed_iterations(bte, name, dim, kw, k, kind):
     p = bi.tiny(dim, **kw)
+    if kind == 2 and not rowblock_eligible(p):
+        pytest.skip("row-block kernel needs an unmasked 1D/2D grid")
     ref = oracle.solve(p, max_iter=k, tol=0.0)
     plan = bte.Plan(p)
     T = np.zeros(p.n_cells)
     q = np.zeros((p.n_cells, 3))
     e = np.zeros((p.n_cells, p.B, p.D))
-    rc, st = plan.solve(T, q_out=q, e_out=e, precision=bte.BTE_FP64, tol=0.0, max_iter=k)
+    rc, st = plan.solve(T, q_out=q, e_out=e, precision=bte.BTE_FP64, tol=0.0, max_iter=k, tile_kind=kind)
+    assert st["tile_kind"] == kind
     act = p.mask > 0
     assert st["iterations"] == k
     assert rel(T, ref["T"], act) < 1e-12
@@ -63,15 +72,20 @@ def test_fp64_fixed_iterations(bte, name, dim, kw, k):
     np.testing.assert_allclose(plan.eps_history(k), ref["eps"], rtol=1e-9, atol=1e-300)
 
 
+TILES = [(0, 0), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4), (2, 8)]
+
+
 @pytest.mark.parametrize("name,dim,kw", TINY, ids=[t[0] for t in TINY])
-@pytest.mark.parametrize("dw", [0, 4, 8])
-def test_fp32_fixed_iterations(bte, name, dim, kw, dw):
+@pytest.mark.parametrize("kind,dw", TILES, ids=[f"k{a}dw{b}" for a, b in TILES])
+def test_fp32_fixed_iterations(bte, name, dim, kw, kind, dw):
     p = bi.tiny(dim, **kw)
+    if kind == 2 and not rowblock_eligible(p):
+        pytest.skip("row-block kernel needs an unmasked 1D/2D grid")
     k = 12
     ref = oracle.solve(p, max_iter=k, tol=0.0)
     plan = bte.Plan(p)
     T = np.zeros(p.n_cells)
-    rc, st = plan.solve(T, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw)
+    rc, st = plan.solve(T, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=kind)
     act = p.mask > 0
     assert rel(T, ref["T"], act) < 1e-5
     # and relative to the temperature variation itself
@@ -110,11 +124,12 @@ def test_square2d_full_size_fixed_iterations(bte):
     ref = oracle.solve(p, max_iter=k, tol=0.0)
     plan = bte.Plan(p)
     T = np.zeros(p.n_cells)
-    plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=k)
-    assert rel(T, ref["T"]) < 1e-12
-    for dw in (4, 8, 16):
+    for kind in (1, 2):
+        plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=k, tile_kind=kind)
+        assert rel(T, ref["T"]) < 1e-12
+    for kind, dw in [(1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (2, 8), (0, 0)]:
         T32 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
-        plan.solve(T32, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw)
+        plan.solve(T32, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=kind)
         assert rel(T32.cpu().numpy(), ref["T"]) < 1e-5
 
 
@@ -167,6 +182,14 @@ def test_device_and_host_outputs_agree(bte):
     plan.solve(Td, e_out=ed, precision=bte.BTE_FP32, tol=0.0, max_iter=5)
     np.testing.assert_array_equal(Td.cpu().numpy(), Th)
     np.testing.assert_array_equal(ed.cpu().numpy(), eh)
+
+
+def test_rowblock_rejected_for_masked_grid(bte):
+    p = bi.tiny(2, n=(7, 6, 1), B=2, masked=True, diffuse=(2,))
+    plan = bte.Plan(p)
+    T = np.zeros(p.n_cells)
+    rc, st = plan.solve(T, tol=0.0, max_iter=2, tile_kind=2, check=False)
+    assert rc == -1
 
 
 def test_store_every_iteration_same_result(bte):
