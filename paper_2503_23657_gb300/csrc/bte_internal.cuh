@@ -37,16 +37,17 @@ template <typename real>
 struct SweepParams {
     int nx, ny, nz;
     int B, D, F, S, R;
+    int Spad;                         // S rounded up to a multiple of 4
     int WY, WZ;                       // warps along y, warp groups along z
     long long N;                      // nx*ny*nz
     const int2 *__restrict__ cell;    // {face base, flags}
     const real *__restrict__ tsrc;    // fwd: T - T_ref; adj: Theta   [N]
     const real *__restrict__ phi;     // fwd source profile [N] or null
     const real *__restrict__ ein;     // [B][F] boundary values
-    real *__restrict__ part;          // [S][B][N] per-subset reduction
+    real *__restrict__ part;          // [B][N][Spad] per-subset reduction
     real *__restrict__ fsum;          // [S][B][F] per-subset face sums
     real *__restrict__ e;             // [N][B][D] store (fwd) / read (adj)
-    real *__restrict__ gpart;         // [S][B][N] adj: sum_d mu_d e_d
+    real *__restrict__ gpart;         // [B][N][Spad] adj: sum_d (mu_d - w_d Theta)(e_d - e0)
     const Subset *__restrict__ sub;   // [S]
     const real *__restrict__ coef;    // [B][D][8]: a_x a_y a_z w ws_x ws_y ws_z pad
     const real *__restrict__ invdiag; // [R][B][D]
@@ -61,17 +62,18 @@ struct SweepParams {
 };
 
 // Parameters of the row-block sweep for unmasked 1D/2D grids with one region
-// (sweep2d.cuh).  One CTA per (direction chunk, band), warps_per_cta warps of
-// DW directions each.
+// (sweep2d.cuh).  One CTA per (direction chunk, band); a chunk holds up to
+// warps_per_cta * DW directions of one quadrant, DW per warp.
 template <typename real>
 struct Sweep2DParams {
     int nx, ny;
     int B, D, F, S;                   // S = number of chunks
+    int Spad;                         // S rounded up to a multiple of 4
     int warps_per_cta;
-    const real *__restrict__ tsrc;    // fwd: T - T_ref; adj: Theta [N]
-    const real *__restrict__ phi;     // fwd source profile [N] or null
+    const real *__restrict__ tsrc;    // fwd: T - T_ref; adj: Theta [N, padded to 16 elements]
+    const real *__restrict__ phi;     // fwd source profile [N, padded] or null
     const real *__restrict__ ein;     // [B][F] boundary values
-    real *__restrict__ part;          // [S][B][N]
+    real *__restrict__ part;          // [B][N][Spad]
     real *__restrict__ fsum;          // [S][B][F]
     real *__restrict__ e;             // [N][B][D] (store_e)
     const Subset *__restrict__ sub;   // [S] chunks
@@ -79,29 +81,30 @@ struct Sweep2DParams {
     const real *__restrict__ invdiag; // [B][D] (region 1)
     const real *__restrict__ srck;    // [B] fwd C_b/(4 pi tau_b); adj 1/tau_b
     const real *__restrict__ qb;      // [B]
-    const real *__restrict__ taub;    // [B] tau_b (region 1), for the fixed-point bound
     const int *__restrict__ wall_face;  // [6][wall_stride] face index or -1
     int wall_stride;
     const int *__restrict__ done;
+    int *__restrict__ status;         // set to 2 if a bounded wait expires
     int store_e;
-    int acc_smem;                     // accumulate per-cell sums of the CTA in shared memory
+    int stage;                        // stage per-cell inputs in shared memory (TMA bulk copy)
 };
 
 template <typename real>
 cudaError_t launch_sweep2d(const Sweep2DParams<real> &p, int dirs_per_warp, int row_blocks, bool adjoint,
                            cudaStream_t st);
-size_t sweep2d_smem(int nx, int ny, int acc_smem, int real_bytes);
+size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, int real_bytes);
 
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.
 template <typename real>
 struct UpdateParams {
     long long N;
     int B, S, F, R;
+    int Spad;
     int adjoint;
     double T_ref;
     const int2 *__restrict__ cell;
     const Subset *__restrict__ sub;
-    const real *__restrict__ part;    // [S][B][N]
+    const real *__restrict__ part;    // [B][N][Spad]
     const real *__restrict__ fsum;    // [S][B][F]
     const double *__restrict__ x_in;  // fwd T_old / adj Theta_old [N]
     double *__restrict__ x_out;       // [N]
@@ -157,9 +160,10 @@ template <typename real>
 struct GradParams {
     long long N;
     int B, S, F;
+    int Spad;
     const int2 *__restrict__ cell;
-    const real *__restrict__ apart;     // [S][B][N] sum_d mu_d
-    const real *__restrict__ gpart;     // [S][B][N] sum_d (mu_d - w_d Theta)(e_d - e0)
+    const real *__restrict__ apart;     // [B][N][Spad] sum_d mu_d
+    const real *__restrict__ gpart;     // [B][N][Spad] sum_d (mu_d - w_d Theta)(e_d - e0)
     const double *__restrict__ phi;     // [N] source profile or null
     const double *__restrict__ inv_tt;  // [R][B] 1/(tau_rb tau_b)
     const double *__restrict__ qcoef;   // [B] Q_amp derivative weight C_b/(4 pi sum C)

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -71,7 +72,7 @@ struct Workspace {
     bool init = false;
     DevBuf tdev[2], ein[2], T[2];      // forward state sets
     DevBuf thdev[2], mein[2], theta[2];  // adjoint state sets
-    DevBuf ein_fixed, part, fsum, e, gpart, phi, coef, invdiag, srck_f, srck_a, qb, cb4pi, taub;
+    DevBuf ein_fixed, part, fsum, e, gpart, phi, coef, invdiag, srck_f, srck_a, qb, cb4pi;
     DevBuf wgt_f, wgt_a, Kinv, scale_f, scale_a, msum, g, grad_out, inv_tt, qcoef, phi64, vws, qshift, q,
         eshift, tfwd_dummy;
     // direction subsets per tile width
@@ -212,31 +213,24 @@ int tile_layers(const bte_plan *p) {
     return 0;
 }
 
-// Row-block 2D kernel: unmasked 1D/2D grid, one region, ny <= 256, the
-// per-cell source (and for FP32 the per-cell accumulator) fits in shared memory.
-bool rowblock_ok(const bte_plan *p, int real_bytes, int *acc_smem) {
-    if (p->dim > 2 || p->ny > 256 || p->n_active != p->N) return false;
-    for (long long c = 0; c < p->N; ++c)
-        if (p->mask[c] != 1) return false;
-    const size_t lim = 200 * 1024;
-    if (real_bytes == 4 && sweep2d_smem(p->nx, p->ny, 1, 4) <= lim) {
-        *acc_smem = 1;
-        return true;
-    }
-    *acc_smem = 0;
-    return sweep2d_smem(p->nx, p->ny, 0, real_bytes) <= lim;
-}
-
 int rowblock_rb(const bte_plan *p) {
-    for (int rb : {1, 2, 4, 8})
+    for (int rb : {1, 2, 3, 4, 5})
         if (32 * rb >= p->ny) return rb;
     return 0;
 }
 
-int max_group(const bte_plan *p) {
-    int m = 0;
-    for (int c : p->groups_cnt) m = std::max(m, c);
-    return m;
+// Row-block 2D kernel: unmasked 1D/2D grid, one region, ny <= 160, and the
+// CTA's shared memory (reduction ring for `warps` warps, wall values) fits.
+// *stage tells whether the per-cell inputs also fit (else they are read
+// from global memory).
+bool rowblock_ok(const bte_plan *p, int real_bytes, int *stage, int warps = 1) {
+    const int rb = rowblock_rb(p);
+    if (p->dim > 2 || rb == 0 || p->n_active != p->N) return false;
+    for (long long c = 0; c < p->N; ++c)
+        if (p->mask[c] != 1) return false;
+    const size_t lim = 200 * 1024;
+    *stage = sweep2d_smem(p->nx, p->ny, 1, p->phi.empty() ? 0 : 1, warps, rb, real_bytes) <= lim ? 1 : 0;
+    return sweep2d_smem(p->nx, p->ny, 0, 0, warps, rb, real_bytes) <= lim;
 }
 
 // Candidate tiles for a precision; kind_req 0 = any, 1 = general only, 2 = row-block only.
@@ -252,19 +246,16 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
             if (mt > 0 && WY * WZ * 32 <= mt && (!dw_req || dw == dw_req)) out.push_back(tile_id(0, dw, dw));
         }
     }
-    int acc = 0;
-    if (kind_req != 1 && rowblock_ok(p, real_bytes, &acc)) {
-        const int gmax = max_group(p);
-        for (int dw : {1, 2, 4, 8}) {
+    int stage = 0;
+    if (kind_req != 1 && rowblock_ok(p, real_bytes, &stage)) {
+        int gmax = 0;
+        for (int c : p->groups_cnt) gmax = std::max(gmax, c);
+        for (int dw : {1, 2, 4}) {
             if (dw_req && dw != dw_req) continue;
-            if (!acc) {
-                out.push_back(tile_id(1, dw, dw));
-                continue;
-            }
             for (int warps : {1, 2, 4, 8, 16}) {
-                const int cw = dw * warps;
-                if (cw > gmax * 2 && warps > 1) break;
-                out.push_back(tile_id(1, dw, cw));
+                if (warps > 1 && dw * warps > gmax) break;
+                if (!rowblock_ok(p, real_bytes, &stage, warps)) break;
+                out.push_back(tile_id(1, dw, dw * warps));  // cw = directions per CTA chunk
             }
         }
     }
@@ -281,7 +272,7 @@ Workspace<double> &ws_of<double>(bte_plan *p) { return p->ws64; }
 template <typename real>
 int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
     if (ws.dsub.count(tid)) return BTE_OK;
-    const int cw = tile_of(tid).cw;
+    const int cw = tile_of(tid).cw;  // directions per CTA (general kernel: cw == dw)
     auto f = make_subsets(p, cw, false);
     auto a = make_subsets(p, cw, true);
     ws.subsets[tid] = {f, a};
@@ -299,7 +290,7 @@ int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
 // set; the row-block kernel down to 1 direction per set).
 int max_subsets(const bte_plan *p) {
     int dummy = 0;
-    const int per = (rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy)) ? 1 : 4;
+    const int per = (rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy)) ? 1 : 4;  // row-block: dw >= 1
     int s = 0;
     for (size_t g = 0; g < p->groups_cnt.size(); ++g) s += (p->groups_cnt[g] + per - 1) / per;
     return s;
@@ -311,7 +302,7 @@ int upload_tables(bte_plan *p, Workspace<real> &ws) {
     const int B = p->B, D = p->D, R = p->R;
     const std::vector<double> &tau = p->cur_tau;
     std::vector<real> coef((size_t)B * D * 8), invd((size_t)R * B * D), srf((size_t)R * B), sra((size_t)R * B),
-        qb(B), cb(B), tb(B);
+        qb(B), cb(B);
     std::vector<double> wf((size_t)R * B), wa((size_t)R * B), Kinv(R), scf(6 * B), sca(6 * B), itt((size_t)R * B),
         qc(B), vws((size_t)B * D * 3), qsh(3, 0.0), esh(B);
     double Csum = 0.0;
@@ -334,7 +325,6 @@ int upload_tables(bte_plan *p, Workspace<real> &ws) {
             for (int ax = 0; ax < 3; ++ax) vws[((size_t)b * D + d) * 3 + ax] = p->v[b] * p->w[d] * p->s[3 * d + ax];
         }
         qb[b] = (real)(p->C[b] * p->cur_Q / (kFourPi * Csum));
-        tb[b] = (real)(tau[b] * p->tau_scale[0]);
         cb[b] = (real)(p->C[b] / kFourPi);
         qc[b] = p->C[b] / (kFourPi * Csum);
         esh[b] = p->C[b] * p->T_ref / kFourPi;
@@ -375,7 +365,6 @@ int upload_tables(bte_plan *p, Workspace<real> &ws) {
     CK(p, upload(ws.srck_a, sra));
     CK(p, upload(ws.qb, qb));
     CK(p, upload(ws.cb4pi, cb));
-    CK(p, upload(ws.taub, tb));
     CK(p, upload(ws.wgt_f, wf));
     CK(p, upload(ws.wgt_a, wa));
     CK(p, upload(ws.Kinv, Kinv));
@@ -396,13 +385,14 @@ int ensure_workspace(bte_plan *p, Workspace<real> &ws) {
     const size_t N = (size_t)p->N, B = p->B, F = std::max(p->F, 1);
     const size_t S = max_subsets(p);
     for (int i = 0; i < 2; ++i) {
-        CK(p, ws.tdev[i].ensure(sizeof(real) * N));
+        CK(p, ws.tdev[i].ensure(sizeof(real) * (N + 16)));
         CK(p, ws.ein[i].ensure(sizeof(real) * B * F));
         CK(p, ws.T[i].ensure(sizeof(double) * N));
     }
-    CK(p, ws.part.ensure(sizeof(real) * S * B * N));
+    const size_t Spad = (S + 3) & ~(size_t)3;
+    CK(p, ws.part.ensure(sizeof(real) * Spad * B * N));
     CK(p, ws.fsum.ensure(sizeof(real) * S * B * F));
-    std::vector<real> ph(N, (real)0);
+    std::vector<real> ph(N + 16, (real)0);
     for (size_t c = 0; c < N && !p->phi.empty(); ++c) ph[c] = (real)p->phi[c];
     CK(p, upload(ws.phi, ph));
     ws.init = true;
@@ -438,6 +428,7 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int tid, bool a
     auto pr = ws.dsub.at(tid);
     sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
     sp.S = (int)ws.subsets.at(tid).first.size();
+    sp.Spad = (sp.S + 3) & ~3;
     sp.done = p->d_status.as<int>();
     // stage the band's boundary values in shared memory when they fit next to
     // the exchange buffers (<= 200 KB of the 227 KB per CTA)
@@ -453,6 +444,7 @@ UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool
     u.N = p->N;
     u.B = p->B;
     u.S = (int)ws.subsets.at(tid).first.size();
+    u.Spad = (u.S + 3) & ~3;
     u.F = p->F;
     u.R = p->R;
     u.adjoint = adj ? 1 : 0;
@@ -500,17 +492,18 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     sp.invdiag = ws.invdiag.template as<real>();
     sp.srck = adj ? ws.srck_a.template as<real>() : ws.srck_f.template as<real>();
     sp.qb = ws.qb.template as<real>();
-    sp.taub = ws.taub.template as<real>();
     sp.phi = p->phi.empty() ? nullptr : ws.phi.template as<real>();
     auto pr = ws.dsub.at(tid);
     sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
     sp.S = (int)ws.subsets.at(tid).first.size();
+    sp.Spad = (sp.S + 3) & ~3;
     sp.wall_face = ws.wall.template as<int>();
     sp.wall_stride = p->wall_stride;
     sp.done = p->d_status.as<int>();
-    int acc = 0;
-    rowblock_ok(p, (int)sizeof(real), &acc);
-    sp.acc_smem = acc;
+    sp.status = &p->d_status.as<Status>()->status;
+    int stage = 0;
+    rowblock_ok(p, (int)sizeof(real), &stage, sp.warps_per_cta);
+    sp.stage = stage;
     return sp;
 }
 
@@ -623,6 +616,9 @@ int autotune(bte_plan *p, Workspace<real> &ws, const std::vector<int> &cand, cud
             cudaEventElapsedTime(&ms, p->ev0, p->ev1);
             if (rep >= 2) tmin = std::min(tmin, ms);
         }
+        if (std::getenv("BTE_TUNE_VERBOSE"))
+            std::fprintf(stderr, "bte tune: kind %d dw %d cw %d: %.4f ms/iteration\n", tile_of(tid).kind + 1,
+                         tile_of(tid).dw, tile_of(tid).cw, tmin);
         if (tmin < best) {
             best = tmin;
             best_tid = tid;
@@ -715,15 +711,17 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         launches += 2LL * k;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
         CK(p, cudaStreamSynchronize(stream));
-        if (p->h_status->done) break;
+        if (p->h_status->done || p->h_status->status) break;
     }
     CK(p, cudaEventRecord(p->ev1, stream));
     CK(p, cudaEventSynchronize(p->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->ev0, p->ev1);
     const int n = p->h_status->iter;
-    const bool bad = p->h_status->status != 0;
+    const int sflag = p->h_status->status;
+    const bool bad = sflag != 0;
     const bool converged = tol > 0.0 && p->h_status->done && !bad;
+    if (sflag == 2) return fail(p, BTE_ETIMEOUT, "a bounded device wait (bulk copy) expired");
     // regenerate e^n from the inputs of the last iteration
     if (n > 0) CK(p, enqueue_forward(p, ws, dw, (n - 1) & 1, tol, true, true, stream));
     if (n > 0) launches += 1;
@@ -786,7 +784,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
 template <typename real>
 cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity, double tol, bool final_pass,
                             cudaStream_t stream) {
-    if (!final_pass && tile_of(dw).kind == 1) {
+    if (!final_pass) {
         cudaError_t e = launch_tile_sweep(p, ws, dw, true, ws.thdev[parity].template as<real>(),
                                           ws.mein[parity].template as<real>(), false, true, stream);
         if (e != cudaSuccess) return e;
@@ -806,7 +804,7 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
     sp.read_e = final_pass ? 1 : 0;
     sp.tfwd = ws.tdev[p->solved_iters & 1].template as<real>();
     if (final_pass) sp.done = nullptr;
-    cudaError_t e = launch_sweep<real>(sp, dw, tile_layers(p), p->dim == 3, true, stream);
+    cudaError_t e = launch_sweep<real>(sp, tile_of(dw).dw, tile_layers(p), p->dim == 3, true, stream);
     if (e != cudaSuccess) return e;
     UpdateParams<real> u = update_params(p, ws, dw, true, tol);
     u.eps_hist = nullptr;  // the history belongs to the forward solve
@@ -836,11 +834,11 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     const int B = p->B, F = std::max(p->F, 1);
     const size_t S = max_subsets(p);
     for (int i = 0; i < 2; ++i) {
-        CK(p, ws.thdev[i].ensure(sizeof(real) * N));
+        CK(p, ws.thdev[i].ensure(sizeof(real) * (N + 16)));
         CK(p, ws.mein[i].ensure(sizeof(real) * (size_t)B * F));
         CK(p, ws.theta[i].ensure(sizeof(double) * N));
     }
-    CK(p, ws.gpart.ensure(sizeof(real) * S * B * N));
+    CK(p, ws.gpart.ensure(sizeof(real) * ((S + 3) & ~(size_t)3) * B * N));
     CK(p, ws.msum.ensure(sizeof(double) * (size_t)B * F));
     CK(p, ws.g.ensure(sizeof(double) * N));
     CK(p, ws.grad_out.ensure(sizeof(double) * (B + 7)));
@@ -921,9 +919,10 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         enq += k;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
         CK(p, cudaStreamSynchronize(stream));
-        if (p->h_status->done) break;
+        if (p->h_status->done || p->h_status->status) break;
     }
     const int n = p->h_status->iter;
+    if (p->h_status->status == 2) return fail(p, BTE_ETIMEOUT, "a bounded device wait (bulk copy) expired");
     const bool bad = p->h_status->status != 0;
     const bool converged = tol > 0.0 && p->h_status->done && !bad;
     // final pass: one more transposed sweep from Theta^n that also forms the
@@ -933,6 +932,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     gp.N = N;
     gp.B = B;
     gp.S = (int)ws.subsets.at(gtile).first.size();
+    gp.Spad = (gp.S + 3) & ~3;
     gp.F = p->F;
     gp.cell = p->d_cell.as<int2>();
     gp.apart = ws.part.template as<real>();

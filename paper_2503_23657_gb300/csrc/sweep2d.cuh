@@ -3,245 +3,372 @@
 // Same discrete equations as sweep.cuh (Eq. fvm-1 with step upwind faces,
 // the triangular matrix A of Eq. A_matrix), organised for small 2D grids:
 //
-//   * one CTA per (direction chunk, band); a chunk is up to W*DW directions
-//     of one quadrant, so they share the traversal order;
-//   * each warp owns DW directions over ALL ny rows: lane l of row block r
-//     holds row j = 32 r + l in registers (RB blocks), so the y-upwind value
-//     of every row comes from lane-1 of the same block (lane 0: lane 31 of
-//     block r-1) by one warp shuffle -- no shared-memory exchange and no
-//     barrier inside the wavefront loop; warps never wait on each other;
-//   * at step t row j updates x = t - j; whole row blocks outside the
-//     wavefront are skipped (warp-uniform);
-//   * the per-cell source C_b (T - T_ref)/(4 pi tau_b) + Q_b phi (forward) or
-//     Theta/tau_b (adjoint) is staged once per CTA in shared memory, as are
-//     the upwind wall values; the per-cell weighted direction sum of the
-//     CTA's warps is accumulated in shared memory and written once per cell
-//     at the end, so a band has only (#chunks) partials per cell.
-//
-// The shared-memory accumulation uses 64-bit fixed-point integer atomics so
-// the result does not depend on the order in which warps arrive (bitwise
-// reproducible runs).  The fixed-point scale comes from the discrete maximum
-// principle of the upwind update: e_c is a weighted mean of tau*src_c and
-// its upwind values, so |e| <= max(tau_b max|src|, max|wall value|) and a
-// CTA's per-cell sum is bounded by that times the sum of its weights.
+//   * one CTA per (direction chunk, band): a chunk is up to W*DW directions
+//     of one quadrant (one traversal order); warp w owns DW of them over ALL
+//     ny rows.  Lane l of row block r holds row j = 32 r + l in registers
+//     (RB blocks), so the y-upwind value of a row comes from lane-1 of the
+//     same block (lane 0: lane 31 of block r-1) by one warp shuffle and the
+//     x-upwind value is the lane's own register from the previous step;
+//   * at step t row j updates x = t - j.  The set of row blocks inside the
+//     wavefront changes only a few times per sweep, so each such phase runs
+//     straight-line code over exactly its active blocks (a template per
+//     (first, last) active block): the RB*DW independent recurrences of a
+//     step interleave freely, with no per-block branch;
+//   * the per-cell temperature deviation (and source profile) is brought
+//     into shared memory once per CTA by a TMA bulk copy (cp.async.bulk on
+//     an mbarrier, bounded wait), the band's upwind wall values are staged;
+//   * the warps of a CTA visit the same cells at the same step, so their
+//     per-cell weighted direction sums go to a shared-memory ring of
+//     kRing diagonals; every kRing steps the CTA sums the ring over its
+//     warps in a fixed order and writes one partial per cell (no atomics,
+//     bitwise reproducible), and the wall face sums are combined the same
+//     way at the end.
 #pragma once
+
+#include <stdint.h>
 
 #include "bte_internal.cuh"
 
 namespace bte {
 
-__device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v); }
-__device__ __forceinline__ long long to_fixed(double v) { return __double2ll_rn(v); }
+// ---- TMA bulk copy + mbarrier helpers (sm_90+ PTX) ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the barrier phase did not complete within `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+constexpr long long kWaitPolls = 1LL << 22;
+
+constexpr int kRing = 16;  // diagonals per CTA reduction round
 
 template <int DW, int RB>
 struct Sweep2DTile {
     static constexpr int kMaxThreads = 512;
 };
 
+// Per-warp sweep state; everything lives in registers after inlining.
+template <typename real, int DW, int RB, bool ADJ>
+struct RowSweep {
+    real old[RB][DW];  // value of this lane's row at its last x (the x-upwind value)
+    int yrow[RB];      // Y (grid row) of this lane's row in block r
+    int t_lo[RB];      // step at which the row enters the grid (x = 0)
+    int c_base[RB];    // cell index at step t is c_base + cstep * t
+    real ax[DW], ay[DW], w[DW], invd[DW], wsy[DW];
+    int cstep, lane, nx, last_row, set;
+    real srck, qb;
+    bool with_phi, store_e, direct;
+    const real *src_t, *src_phi, *wy;
+    real *ring;        // this warp's ring [kRing][RB][32] (direct == false)
+    real *part_b;      // band b's partials, set `set` (direct == true)
+    int spad;
+    real *fsy;         // this warp's downwind y-wall sums, by X
+    real *e;
+    long long eoff;    // b * D + d0
+    int BD, ndir;
+
+    template <int R>
+    __device__ __forceinline__ void block(int t, int slot) {
+        const int dx = t - t_lo[R];
+        const bool valid = (unsigned)dx < (unsigned)nx;
+        const int c = c_base[R] + cstep * t;
+        real base = valid ? src_t[c] : real(0);
+        base *= srck;
+        if (with_phi) base = fma(valid ? src_phi[c] : real(0), qb, base);
+        real Ey = real(0);
+        if (R == 0) Ey = (lane == 0 && valid) ? wy[c - nx * yrow[0]] : real(0);
+        real acc = real(0);
+#pragma unroll
+        for (int dd = 0; dd < DW; ++dd) {
+            real vy;
+            if (R > 0) {
+                // lane 31 hands row 32R-1 (block R-1) to lane 0 of block R
+                const real prov = (lane == 31) ? old[R > 0 ? R - 1 : 0][dd] : old[R][dd];
+                vy = __shfl_sync(0xffffffffu, prov, (lane + 31) & 31);
+            } else {
+                vy = __shfl_sync(0xffffffffu, old[0][dd], (lane + 31) & 31);
+                vy = (lane == 0) ? (ADJ ? Ey * w[dd] : Ey) : vy;  // row 0: upwind y-wall
+            }
+            real r0 = ADJ ? base * w[dd] : base;
+            r0 = fma(ax[dd], old[R][dd], r0);  // x-upwind (the wall value before x = 0)
+            r0 = fma(ay[dd], vy, r0);
+            const real en = r0 * invd[dd];
+            old[R][dd] = valid ? en : old[R][dd];
+            acc = ADJ ? acc + en : fma(w[dd], en, acc);
+        }
+        if (direct) {
+            if (valid) part_b[(long long)c * spad] = acc;
+        } else {
+            ring[(slot * RB + R) * 32 + lane] = acc;
+        }
+        if (store_e && valid) {
+            real *ep = e + (long long)c * BD + eoff;
+#pragma unroll
+            for (int dd = 0; dd < DW; ++dd)
+                if (dd < ndir) ep[dd] = old[R][dd];
+        }
+        if (32 * R + lane == last_row && valid) {
+            real fs = real(0);
+#pragma unroll
+            for (int dd = 0; dd < DW; ++dd) fs = fma(wsy[dd], old[R][dd], fs);
+            fsy[c - nx * yrow[R]] = fs;
+        }
+    }
+
+    // the active blocks R = HI..LO of one step, highest first, so block R
+    // reads block R-1's previous-step values before they change
+    template <int R, int LO>
+    __device__ __forceinline__ void blocks_desc(int t, int slot) {
+        if constexpr (R >= LO) {
+            block<R>(t, slot);
+            blocks_desc<R - 1, LO>(t, slot);
+        }
+    }
+    template <int LO, int HI>
+    __device__ __forceinline__ void steps(int t_begin, int t_end, int t0) {
+        for (int t = t_begin; t < t_end; ++t) blocks_desc<HI, LO>(t, t - t0);
+    }
+};
+
 template <typename real, int DW, int RB, bool ADJ>
 __global__ void __launch_bounds__(Sweep2DTile<DW, RB>::kMaxThreads)
 sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     if (P.done != nullptr && *((volatile const int *)P.done) != 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
     const int N = P.nx * P.ny;
-    unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(smem_raw);  // [N] if acc_smem
-    unsigned long long *s_fx = s_acc + (P.acc_smem ? N : 0);  // [ny] downwind x-wall sums
-    unsigned long long *s_fy = s_fx + P.ny;                  // [nx] downwind y-wall sums
-    real *s_base = reinterpret_cast<real *>(s_fy + P.nx);    // [N]
-    real *s_wx = s_base + ((N + 3) & ~3);                    // [ny] upwind x-wall values
-    real *s_wy = s_wx + ((P.ny + 3) & ~3);                   // [nx] upwind y-wall values
-    __shared__ double s_red[32];
-    __shared__ double s_scale[2];
+    const int Npad = (N + 15) & ~15;
+    const int W = P.warps_per_cta;
+    const bool direct = (W == 1);
+    const bool with_phi = (!ADJ && P.phi != nullptr);
+    real *s_t = reinterpret_cast<real *>(smem_raw);                  // [Npad] T - T_ref or Theta
+    real *s_phi = s_t + (P.stage ? Npad : 0);                        // [Npad] source profile (fwd)
+    real *s_ring = s_phi + ((P.stage && with_phi) ? Npad : 0);       // [W][kRing][RB][32] (W > 1)
+    real *s_fs = s_ring + (direct ? 0 : W * kRing * RB * 32);        // [W][nx + ny] wall sums
+    real *s_wx = s_fs + W * (P.ny + P.nx);                           // [ny] upwind x-wall values
+    real *s_wy = s_wx + P.ny;                                        // [nx] upwind y-wall values
 
-    const int s = blockIdx.x;
+    const int s = blockIdx.x;  // chunk = partial set
     const int b = blockIdx.y;
-    const Subset ch = P.sub[s];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nthr = blockDim.x;
     const int B = P.B, D = P.D;
+    const Subset ch = P.sub[s];
     const bool negx = ch.neg & 1, negy = (ch.neg >> 1) & 1;
     const int up_x = negx ? 1 : 0, up_y = negy ? 3 : 2;
-    const int dn_x = up_x ^ 1, dn_y = up_y ^ 1;
-    const int *wf = P.wall_face;
-    const real *einb = P.ein + (long long)b * P.F;
 
-    // ---- prologue: per-cell source, wall values, accumulators ----
-    const real srck = P.srck[b];
-    const real qb = (!ADJ && P.phi != nullptr) ? P.qb[b] : real(0);
-    double mb = 0.0, mw = 0.0;
-    for (int c = threadIdx.x; c < N; c += nthr) {
-        real v = P.tsrc[c] * srck;
-        if (!ADJ && P.phi != nullptr) v += P.phi[c] * qb;
-        s_base[c] = v;
-        mb = fmax(mb, fabs((double)v));
-        if (P.acc_smem) s_acc[c] = 0ull;
-    }
-    for (int y = threadIdx.x; y < P.ny; y += nthr) {
-        const int f = wf[up_x * P.wall_stride + y];
-        s_wx[y] = f >= 0 ? einb[f] : real(0);
-        mw = fmax(mw, fabs((double)s_wx[y]));
-        s_fx[y] = 0ull;
-    }
-    for (int x = threadIdx.x; x < P.nx; x += nthr) {
-        const int f = wf[up_y * P.wall_stride + x];
-        s_wy[x] = f >= 0 ? einb[f] : real(0);
-        mw = fmax(mw, fabs((double)s_wy[x]));
-        s_fy[x] = 0ull;
-    }
-    // bound of |e| over the CTA's problems, then the fixed-point scales
-    mb = fmax(mb * (double)P.taub[b], mw);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-    if (lane == 0) s_red[warp] = mb;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double bound = 0.0;
-        for (int i = 0; i < (nthr >> 5); ++i) bound = fmax(bound, s_red[i]);
-        double wsum = 0.0, wmax = 0.0, fsum = 0.0;
-        for (int dd = 0; dd < ch.cnt; ++dd) {
-            const real *cf = P.coef + ((long long)b * D + ch.d0 + dd) * 8;
-            wsum += (double)cf[3];
-            wmax = fmax(wmax, (double)cf[3]);
-            fsum += ADJ ? fmax((double)cf[0], (double)cf[1]) : fmax((double)cf[4], (double)cf[5]);
+    // ---- prologue: TMA bulk copy of the per-cell inputs, wall values ----
+    if (P.stage) {
+        if (threadIdx.x == 0) {
+            mbar_init(&s_bar, 1);
+            mbar_fence_init();
         }
-        if (ADJ) bound *= wmax;                      // adjoint sources and walls carry w_d
-        // floor keeps the scale finite in the sweep precision (values below it
-        // are far below the solver's resolution)
-        const double floor_b = sizeof(real) == 4 ? 1e-18 : 1e-280;
-        const double acc_bound = fmax(bound * (ADJ ? (double)ch.cnt : wsum) * 1.0001, floor_b);
-        const double face_bound = fmax(bound * fsum * 1.0001, floor_b);
-        s_scale[0] = 4611686018427387904.0 / acc_bound;   // 2^62
-        s_scale[1] = 4611686018427387904.0 / face_bound;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = (uint32_t)(Npad * sizeof(real));
+            mbar_arrive_expect_tx(&s_bar, with_phi ? 2 * bytes : bytes);
+            bulk_copy_g2s(s_t, P.tsrc, bytes, &s_bar);
+            if (with_phi) bulk_copy_g2s(s_phi, P.phi, bytes, &s_bar);
+        }
     }
+    {
+        const real *einb = P.ein + (long long)b * P.F;
+        for (int y = threadIdx.x; y < P.ny; y += nthr) {
+            const int f = P.wall_face[up_x * P.wall_stride + y];
+            s_wx[y] = f >= 0 ? einb[f] : real(0);
+        }
+        for (int x = threadIdx.x; x < P.nx; x += nthr) {
+            const int f = P.wall_face[up_y * P.wall_stride + x];
+            s_wy[x] = f >= 0 ? einb[f] : real(0);
+        }
+        for (int i = threadIdx.x; i < W * (P.ny + P.nx); i += nthr) s_fs[i] = real(0);
+    }
+    bool ok = true;
+    if (P.stage) ok = mbar_wait_bounded(&s_bar, 0, kWaitPolls);
     __syncthreads();
-    const real sc_acc = (real)s_scale[0];
-    const real sc_face = (real)s_scale[1];
+    if (!ok) {
+        // the bulk copy did not complete: report, wait once more for it, stop
+        if (threadIdx.x == 0) {
+            atomicExch(P.status, 2);
+            mbar_wait_bounded(&s_bar, 0, kWaitPolls);
+        }
+        return;
+    }
 
+    // ---- this warp's directions ----
+    RowSweep<real, DW, RB, ADJ> S;
+    S.lane = lane;
+    S.nx = P.nx;
+    S.last_row = P.ny - 1;
+    S.cstep = negx ? -1 : 1;
+    S.with_phi = with_phi;
+    S.store_e = P.store_e != 0;
+    S.direct = direct;
+    S.set = s;
+    S.src_t = P.stage ? s_t : P.tsrc;
+    S.src_phi = P.stage ? s_phi : P.phi;
+    S.wy = s_wy;
+    S.ring = s_ring + warp * kRing * RB * 32;
+    S.part_b = P.part + (long long)b * N * P.Spad + s;
+    S.spad = P.Spad;
+    S.fsy = s_fs + warp * (P.ny + P.nx);
+    real *fsx = S.fsy + P.nx;
+    S.e = P.e;
+    S.BD = B * D;
+    S.srck = P.srck[b];
+    S.qb = with_phi ? P.qb[b] : real(0);
     const int d0 = ch.d0 + warp * DW;
-    const int ndir = min(DW, ch.cnt - warp * DW);
-    if (ndir > 0) {
-        real ax[DW], ay[DW], w[DW], invd[DW], wsx[DW], wsy[DW];
+    S.ndir = max(0, min(DW, ch.cnt - warp * DW));
+    S.eoff = (long long)b * D + d0;
+    real wsx[DW];
 #pragma unroll
-        for (int dd = 0; dd < DW; ++dd) {
-            if (dd < ndir) {
-                const real *cf = P.coef + ((long long)b * D + d0 + dd) * 8;
-                ax[dd] = cf[0];
-                ay[dd] = cf[1];
-                w[dd] = cf[3];
-                // face-sum weights: forward w|s_a| (energy leaving), adjoint a_a
-                wsx[dd] = ADJ ? cf[0] : cf[4];
-                wsy[dd] = ADJ ? cf[1] : cf[5];
-                invd[dd] = P.invdiag[(long long)b * D + d0 + dd];
-            } else {
-                ax[dd] = ay[dd] = w[dd] = invd[dd] = wsx[dd] = wsy[dd] = real(0);
-            }
+    for (int dd = 0; dd < DW; ++dd) {
+        if (dd < S.ndir) {
+            const real *cf = P.coef + ((long long)b * D + d0 + dd) * 8;
+            S.ax[dd] = cf[0];
+            S.ay[dd] = cf[1];
+            S.w[dd] = cf[3];
+            // face-sum weights: forward w|s_a| (energy leaving), adjoint a_a
+            wsx[dd] = ADJ ? cf[0] : cf[4];
+            S.wsy[dd] = ADJ ? cf[1] : cf[5];
+            S.invd[dd] = P.invdiag[(long long)b * D + d0 + dd];
+        } else {
+            S.ax[dd] = S.ay[dd] = S.w[dd] = S.invd[dd] = wsx[dd] = S.wsy[dd] = real(0);
         }
-        real old[RB][DW];
+    }
+    const int X0 = negx ? P.nx - 1 : 0;
 #pragma unroll
-        for (int r = 0; r < RB; ++r)
+    for (int r = 0; r < RB; ++r) {
+        const int j = 32 * r + lane;
+        const bool in = j < P.ny;
+        const int Y = negy ? P.ny - 1 - j : j;
+        S.yrow[r] = in ? Y : 0;
+        S.t_lo[r] = in ? j : (1 << 29);  // rows beyond the grid are never valid
+        S.c_base[r] = X0 + P.nx * Y - S.cstep * j;
+        // before the row enters the grid its x-upwind value is the wall value
+        const real ex = in ? s_wx[Y] : real(0);
 #pragma unroll
-            for (int dd = 0; dd < DW; ++dd) old[r][dd] = real(0);
-        real *part_sb = P.part + ((long long)s * B + b) * N;
-        const int n_steps = P.nx + P.ny - 1;
-        const int src_lane = (lane + 31) & 31;
-        for (int t = 0; t < n_steps; ++t) {
-#pragma unroll
-            for (int r = RB - 1; r >= 0; --r) {
-                const int j0 = 32 * r;
-                if (j0 >= P.ny || t < j0 || t - j0 - 31 >= P.nx) continue;  // block outside the wavefront
-                const int j = j0 + lane;
-                const int x = t - j;
-                const bool valid = (j < P.ny) && (x >= 0) && (x < P.nx);
-                const int X = negx ? P.nx - 1 - x : x;
-                const int Y = negy ? P.ny - 1 - j : j;
-                const int c = X + P.nx * Y;
-                const real base = valid ? s_base[c] : real(0);
-                const bool bx = (x == 0);
-                const bool by = (j == 0);
-                const real Ex = (valid && bx) ? s_wx[Y] : real(0);
-                const real Ey = (valid && by) ? s_wy[X] : real(0);
-                real acc = real(0);
-#pragma unroll
-                for (int dd = 0; dd < DW; ++dd) {
-                    // lane 31 hands row 32r-1 (block r-1) to lane 0 of block r
-                    const real prov = (r > 0 && lane == 31) ? old[r > 0 ? r - 1 : 0][dd] : old[r][dd];
-                    real vy = __shfl_sync(0xffffffffu, prov, src_lane);
-                    real vx = old[r][dd];
-                    if (ADJ) {
-                        vx = bx ? Ex * w[dd] : vx;
-                        vy = by ? Ey * w[dd] : vy;
-                    } else {
-                        vx = bx ? Ex : vx;
-                        vy = by ? Ey : vy;
-                    }
-                    real r0 = ADJ ? base * w[dd] : base;
-                    r0 = fma(ax[dd], vx, r0);
-                    r0 = fma(ay[dd], vy, r0);
-                    const real en = r0 * invd[dd];
-                    if (valid) {
-                        old[r][dd] = en;
-                        acc = ADJ ? acc + en : fma(w[dd], en, acc);
-                    }
-                }
-                if (valid) {
-                    if (P.acc_smem)
-                        atomicAdd(&s_acc[c], (unsigned long long)to_fixed(acc * sc_acc));
-                    else
-                        part_sb[c] = acc;
-                    if (P.store_e) {
-                        real *ep = P.e + ((long long)c * B + b) * D + d0;
-#pragma unroll
-                        for (int dd = 0; dd < DW; ++dd)
-                            if (dd < ndir) ep[dd] = old[r][dd];
-                    }
-                    if (x == P.nx - 1) {
-                        real fs = real(0);
-#pragma unroll
-                        for (int dd = 0; dd < DW; ++dd) fs = fma(wsx[dd], old[r][dd], fs);
-                        atomicAdd(&s_fx[Y], (unsigned long long)to_fixed(fs * sc_face));
-                    }
-                    if (j == P.ny - 1) {
-                        real fs = real(0);
-#pragma unroll
-                        for (int dd = 0; dd < DW; ++dd) fs = fma(wsy[dd], old[r][dd], fs);
-                        atomicAdd(&s_fy[X], (unsigned long long)to_fixed(fs * sc_face));
+        for (int dd = 0; dd < DW; ++dd) S.old[r][dd] = ADJ ? ex * S.w[dd] : ex;
+    }
+
+    // ---- wavefront: phases of constant active blocks (ring flush every kRing steps) ----
+    const int n_steps = P.nx + P.ny - 1;
+    const int nblk = (P.ny + 31) / 32;
+    const int round = direct ? n_steps : kRing;
+    for (int t0 = 0; t0 < n_steps; t0 += round) {
+        const int t1 = min(t0 + round, n_steps);
+        int tt = t0;
+        while (tt < t1) {
+            const int lo = (tt - 31 - P.nx < 0) ? 0 : (tt - 31 - P.nx) / 32 + 1;
+            const int hi = min(nblk - 1, tt / 32);
+            int tn = t1;
+            if (hi + 1 < nblk) tn = min(tn, 32 * (hi + 1));
+            tn = min(tn, 32 * lo + 31 + P.nx);
+#define BTE_PHASE(L, H)                                                 \
+    case (L) * 8 + (H):                                                 \
+        if constexpr ((H) < RB) S.template steps<(L), (H)>(tt, tn, t0); \
+        break;
+            switch (lo * 8 + hi) {
+                BTE_PHASE(0, 0) BTE_PHASE(0, 1) BTE_PHASE(0, 2) BTE_PHASE(0, 3) BTE_PHASE(0, 4)
+                BTE_PHASE(1, 1) BTE_PHASE(1, 2) BTE_PHASE(1, 3) BTE_PHASE(1, 4)
+                BTE_PHASE(2, 2) BTE_PHASE(2, 3) BTE_PHASE(2, 4)
+                BTE_PHASE(3, 3) BTE_PHASE(3, 4)
+                BTE_PHASE(4, 4)
+                default: break;
+            }
+#undef BTE_PHASE
+            tt = tn;
+        }
+        if (!direct) {
+            __syncthreads();
+            // sum the ring over the warps (fixed order): warp q takes ring rows
+            // (slot, block) q, q+W, ...; lane = row within the block
+            for (int slot = 0; slot < t1 - t0; ++slot) {
+                const int t = t0 + slot;
+                for (int rr = warp; rr < nblk; rr += W) {
+                    const int j = 32 * rr + lane;
+                    const int x = t - j;
+                    real sum = real(0);
+                    for (int q = 0; q < W; ++q) sum += s_ring[((q * kRing + slot) * RB + rr) * 32 + lane];
+                    if (j < P.ny && x >= 0 && x < P.nx) {
+                        const int X = negx ? P.nx - 1 - x : x;
+                        const int Y = negy ? P.ny - 1 - j : j;
+                        P.part[((long long)b * N + X + P.nx * Y) * P.Spad + s] = sum;
                     }
                 }
             }
+            __syncthreads();
+        }
+    }
+    // downwind x-wall sums: after its last column every row keeps that value
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        if (32 * r + lane < P.ny) {
+            real fs = real(0);
+#pragma unroll
+            for (int dd = 0; dd < DW; ++dd) fs = fma(wsx[dd], S.old[r][dd], fs);
+            fsx[S.yrow[r]] = fs;
         }
     }
     __syncthreads();
-    // ---- epilogue: one partial per cell and per wall face for the CTA ----
-    const double inv_acc = 1.0 / s_scale[0], inv_face = 1.0 / s_scale[1];
-    if (P.acc_smem) {
-        real *part_sb = P.part + ((long long)s * B + b) * N;
-        for (int c = threadIdx.x; c < N; c += nthr) part_sb[c] = (real)((double)(long long)s_acc[c] * inv_acc);
-    }
+    // wall face sums of the chunk: downwind y wall (by X), downwind x wall (by Y)
     real *fs_sb = P.fsum + ((long long)s * B + b) * P.F;
-    for (int y = threadIdx.x; y < P.ny; y += nthr) {
-        const int f = wf[dn_x * P.wall_stride + y];
-        if (f >= 0) fs_sb[f] = (real)((double)(long long)s_fx[y] * inv_face);
-    }
-    for (int x = threadIdx.x; x < P.nx; x += nthr) {
-        const int f = wf[dn_y * P.wall_stride + x];
-        if (f >= 0) fs_sb[f] = (real)((double)(long long)s_fy[x] * inv_face);
+    for (int i = threadIdx.x; i < P.ny + P.nx; i += nthr) {
+        real sum = real(0);
+        for (int q = 0; q < W; ++q) sum += s_fs[q * (P.ny + P.nx) + i];
+        int f;
+        if (i < P.nx)
+            f = P.wall_face[(up_y ^ 1) * P.wall_stride + i];
+        else
+            f = P.wall_face[(up_x ^ 1) * P.wall_stride + (i - P.nx)];
+        if (f >= 0) fs_sb[f] = sum;
     }
 }
 
 template <typename real>
-size_t sweep2d_smem_bytes(int nx, int ny, int acc_smem) {
+size_t sweep2d_smem_bytes(int nx, int ny, int stage, int with_phi, int warps, int rb) {
     const size_t N = (size_t)nx * ny;
-    const size_t fixed = 8 * ((acc_smem ? N : 0) + (size_t)nx + (size_t)ny);
-    const size_t n = ((N + 3) & ~(size_t)3) + (((size_t)ny + 3) & ~(size_t)3) + (((size_t)nx + 3) & ~(size_t)3);
-    return fixed + n * sizeof(real);
+    const size_t Npad = (N + 15) & ~(size_t)15;
+    size_t n = (warps > 1 ? (size_t)warps * kRing * rb * 32 : 0) + (size_t)warps * (nx + ny) + nx + ny;
+    if (stage) n += Npad * (with_phi ? 2 : 1);
+    return n * sizeof(real);
 }
 
 template <typename real, int DW, int RB, bool ADJ>
 cudaError_t launch_sweep2d_t(const Sweep2DParams<real> &p, cudaStream_t st) {
     const int threads = p.warps_per_cta * 32;
     if (threads > Sweep2DTile<DW, RB>::kMaxThreads || p.ny > 32 * RB) return cudaErrorInvalidConfiguration;
-    const size_t smem = sweep2d_smem_bytes<real>(p.nx, p.ny, p.acc_smem);
+    const size_t smem =
+        sweep2d_smem_bytes<real>(p.nx, p.ny, p.stage, (!ADJ && p.phi != nullptr) ? 1 : 0, p.warps_per_cta, RB);
     auto kern = sweep2d_kernel<real, DW, RB, ADJ>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -5,20 +5,19 @@ namespace bte {
 cudaError_t launch_sweep2d_float(const Sweep2DParams<float> &p, int dw, int rb, bool adj, cudaStream_t st) {
     if (dw == 1 && rb == 1) return adj ? launch_sweep2d_t<float, 1, 1, true>(p, st) : launch_sweep2d_t<float, 1, 1, false>(p, st);
     if (dw == 1 && rb == 2) return adj ? launch_sweep2d_t<float, 1, 2, true>(p, st) : launch_sweep2d_t<float, 1, 2, false>(p, st);
+    if (dw == 1 && rb == 3) return adj ? launch_sweep2d_t<float, 1, 3, true>(p, st) : launch_sweep2d_t<float, 1, 3, false>(p, st);
     if (dw == 1 && rb == 4) return adj ? launch_sweep2d_t<float, 1, 4, true>(p, st) : launch_sweep2d_t<float, 1, 4, false>(p, st);
-    if (dw == 1 && rb == 8) return adj ? launch_sweep2d_t<float, 1, 8, true>(p, st) : launch_sweep2d_t<float, 1, 8, false>(p, st);
+    if (dw == 1 && rb == 5) return adj ? launch_sweep2d_t<float, 1, 5, true>(p, st) : launch_sweep2d_t<float, 1, 5, false>(p, st);
     if (dw == 2 && rb == 1) return adj ? launch_sweep2d_t<float, 2, 1, true>(p, st) : launch_sweep2d_t<float, 2, 1, false>(p, st);
     if (dw == 2 && rb == 2) return adj ? launch_sweep2d_t<float, 2, 2, true>(p, st) : launch_sweep2d_t<float, 2, 2, false>(p, st);
+    if (dw == 2 && rb == 3) return adj ? launch_sweep2d_t<float, 2, 3, true>(p, st) : launch_sweep2d_t<float, 2, 3, false>(p, st);
     if (dw == 2 && rb == 4) return adj ? launch_sweep2d_t<float, 2, 4, true>(p, st) : launch_sweep2d_t<float, 2, 4, false>(p, st);
-    if (dw == 2 && rb == 8) return adj ? launch_sweep2d_t<float, 2, 8, true>(p, st) : launch_sweep2d_t<float, 2, 8, false>(p, st);
+    if (dw == 2 && rb == 5) return adj ? launch_sweep2d_t<float, 2, 5, true>(p, st) : launch_sweep2d_t<float, 2, 5, false>(p, st);
     if (dw == 4 && rb == 1) return adj ? launch_sweep2d_t<float, 4, 1, true>(p, st) : launch_sweep2d_t<float, 4, 1, false>(p, st);
     if (dw == 4 && rb == 2) return adj ? launch_sweep2d_t<float, 4, 2, true>(p, st) : launch_sweep2d_t<float, 4, 2, false>(p, st);
+    if (dw == 4 && rb == 3) return adj ? launch_sweep2d_t<float, 4, 3, true>(p, st) : launch_sweep2d_t<float, 4, 3, false>(p, st);
     if (dw == 4 && rb == 4) return adj ? launch_sweep2d_t<float, 4, 4, true>(p, st) : launch_sweep2d_t<float, 4, 4, false>(p, st);
-    if (dw == 4 && rb == 8) return adj ? launch_sweep2d_t<float, 4, 8, true>(p, st) : launch_sweep2d_t<float, 4, 8, false>(p, st);
-    if (dw == 8 && rb == 1) return adj ? launch_sweep2d_t<float, 8, 1, true>(p, st) : launch_sweep2d_t<float, 8, 1, false>(p, st);
-    if (dw == 8 && rb == 2) return adj ? launch_sweep2d_t<float, 8, 2, true>(p, st) : launch_sweep2d_t<float, 8, 2, false>(p, st);
-    if (dw == 8 && rb == 4) return adj ? launch_sweep2d_t<float, 8, 4, true>(p, st) : launch_sweep2d_t<float, 8, 4, false>(p, st);
-    if (dw == 8 && rb == 8) return adj ? launch_sweep2d_t<float, 8, 8, true>(p, st) : launch_sweep2d_t<float, 8, 8, false>(p, st);
+    if (dw == 4 && rb == 5) return adj ? launch_sweep2d_t<float, 4, 5, true>(p, st) : launch_sweep2d_t<float, 4, 5, false>(p, st);
     return cudaErrorInvalidConfiguration;
 }
 
@@ -27,7 +26,8 @@ cudaError_t launch_sweep2d<float>(const Sweep2DParams<float> &p, int dw, int rb,
     return launch_sweep2d_float(p, dw, rb, adj, st);
 }
 
-size_t sweep2d_smem(int nx, int ny, int acc_smem, int real_bytes) {
-    return real_bytes == 4 ? sweep2d_smem_bytes<float>(nx, ny, acc_smem) : sweep2d_smem_bytes<double>(nx, ny, acc_smem);
+size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, int real_bytes) {
+    return real_bytes == 4 ? sweep2d_smem_bytes<float>(nx, ny, stage, with_phi, warps, rb)
+                           : sweep2d_smem_bytes<double>(nx, ny, stage, with_phi, warps, rb);
 }
 }  // namespace bte

@@ -5,20 +5,19 @@ namespace bte {
 cudaError_t launch_sweep2d_double(const Sweep2DParams<double> &p, int dw, int rb, bool adj, cudaStream_t st) {
     if (dw == 1 && rb == 1) return adj ? launch_sweep2d_t<double, 1, 1, true>(p, st) : launch_sweep2d_t<double, 1, 1, false>(p, st);
     if (dw == 1 && rb == 2) return adj ? launch_sweep2d_t<double, 1, 2, true>(p, st) : launch_sweep2d_t<double, 1, 2, false>(p, st);
+    if (dw == 1 && rb == 3) return adj ? launch_sweep2d_t<double, 1, 3, true>(p, st) : launch_sweep2d_t<double, 1, 3, false>(p, st);
     if (dw == 1 && rb == 4) return adj ? launch_sweep2d_t<double, 1, 4, true>(p, st) : launch_sweep2d_t<double, 1, 4, false>(p, st);
-    if (dw == 1 && rb == 8) return adj ? launch_sweep2d_t<double, 1, 8, true>(p, st) : launch_sweep2d_t<double, 1, 8, false>(p, st);
+    if (dw == 1 && rb == 5) return adj ? launch_sweep2d_t<double, 1, 5, true>(p, st) : launch_sweep2d_t<double, 1, 5, false>(p, st);
     if (dw == 2 && rb == 1) return adj ? launch_sweep2d_t<double, 2, 1, true>(p, st) : launch_sweep2d_t<double, 2, 1, false>(p, st);
     if (dw == 2 && rb == 2) return adj ? launch_sweep2d_t<double, 2, 2, true>(p, st) : launch_sweep2d_t<double, 2, 2, false>(p, st);
+    if (dw == 2 && rb == 3) return adj ? launch_sweep2d_t<double, 2, 3, true>(p, st) : launch_sweep2d_t<double, 2, 3, false>(p, st);
     if (dw == 2 && rb == 4) return adj ? launch_sweep2d_t<double, 2, 4, true>(p, st) : launch_sweep2d_t<double, 2, 4, false>(p, st);
-    if (dw == 2 && rb == 8) return adj ? launch_sweep2d_t<double, 2, 8, true>(p, st) : launch_sweep2d_t<double, 2, 8, false>(p, st);
+    if (dw == 2 && rb == 5) return adj ? launch_sweep2d_t<double, 2, 5, true>(p, st) : launch_sweep2d_t<double, 2, 5, false>(p, st);
     if (dw == 4 && rb == 1) return adj ? launch_sweep2d_t<double, 4, 1, true>(p, st) : launch_sweep2d_t<double, 4, 1, false>(p, st);
     if (dw == 4 && rb == 2) return adj ? launch_sweep2d_t<double, 4, 2, true>(p, st) : launch_sweep2d_t<double, 4, 2, false>(p, st);
+    if (dw == 4 && rb == 3) return adj ? launch_sweep2d_t<double, 4, 3, true>(p, st) : launch_sweep2d_t<double, 4, 3, false>(p, st);
     if (dw == 4 && rb == 4) return adj ? launch_sweep2d_t<double, 4, 4, true>(p, st) : launch_sweep2d_t<double, 4, 4, false>(p, st);
-    if (dw == 4 && rb == 8) return adj ? launch_sweep2d_t<double, 4, 8, true>(p, st) : launch_sweep2d_t<double, 4, 8, false>(p, st);
-    if (dw == 8 && rb == 1) return adj ? launch_sweep2d_t<double, 8, 1, true>(p, st) : launch_sweep2d_t<double, 8, 1, false>(p, st);
-    if (dw == 8 && rb == 2) return adj ? launch_sweep2d_t<double, 8, 2, true>(p, st) : launch_sweep2d_t<double, 8, 2, false>(p, st);
-    if (dw == 8 && rb == 4) return adj ? launch_sweep2d_t<double, 8, 4, true>(p, st) : launch_sweep2d_t<double, 8, 4, false>(p, st);
-    if (dw == 8 && rb == 8) return adj ? launch_sweep2d_t<double, 8, 8, true>(p, st) : launch_sweep2d_t<double, 8, 8, false>(p, st);
+    if (dw == 4 && rb == 5) return adj ? launch_sweep2d_t<double, 4, 5, true>(p, st) : launch_sweep2d_t<double, 4, 5, false>(p, st);
     return cudaErrorInvalidConfiguration;
 }
 

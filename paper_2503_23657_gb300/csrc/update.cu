@@ -48,6 +48,38 @@ __device__ __forceinline__ void block_reduce2(double &a, double &m, double *sh) 
     }
 }
 
+// Sum of the S partial sets of one (band, cell): they are contiguous
+// ([B][N][Spad] layout, rows 16-byte aligned), read with vector loads that
+// are all independent; summed in the sweep precision in a fixed order.
+__device__ __forceinline__ float sum_sets(const float *pp, int S) {
+    const float4 *p4 = reinterpret_cast<const float4 *>(pp);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const int n4 = S >> 2;
+#pragma unroll 8
+    for (int q = 0; q < n4; ++q) {
+        const float4 v = p4[q];
+        a0 += v.x;
+        a1 += v.y;
+        a2 += v.z;
+        a3 += v.w;
+    }
+    for (int s = n4 << 2; s < S; ++s) a0 += pp[s];
+    return (a0 + a1) + (a2 + a3);
+}
+__device__ __forceinline__ double sum_sets(const double *pp, int S) {
+    const double2 *p2 = reinterpret_cast<const double2 *>(pp);
+    double a0 = 0.0, a1 = 0.0;
+    const int n2 = S >> 1;
+#pragma unroll 8
+    for (int q = 0; q < n2; ++q) {
+        const double2 v = p2[q];
+        a0 += v.x;
+        a1 += v.y;
+    }
+    if (S & 1) a0 += pp[S - 1];
+    return a0 + a1;
+}
+
 // Threads of a cell block are laid out [band slot y][cell x] (32 cells x 8
 // band slots): each thread sums the partial sets of its bands (within a band
 // in the sweep precision, i.e. over directions), the weighted band sums are
@@ -72,18 +104,8 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_consta
         double acc = 0.0;
         if (r != 0) {
             for (int b = ty; b < P.B; b += kBandSlots) {
-                const real *pp = P.part + (long long)b * P.N + c;
-                const long long stride = (long long)P.B * P.N;
-                real s0 = real(0), s1 = real(0), s2 = real(0), s3 = real(0);
-                int s = 0;
-                for (; s + 4 <= P.S; s += 4) {
-                    s0 += pp[(s + 0) * stride];
-                    s1 += pp[(s + 1) * stride];
-                    s2 += pp[(s + 2) * stride];
-                    s3 += pp[(s + 3) * stride];
-                }
-                for (; s < P.S; ++s) s0 += pp[s * stride];
-                acc += (double)((s0 + s1) + (s2 + s3)) * P.wgt[(r - 1) * P.B + b];
+                const real *pp = P.part + ((long long)b * P.N + c) * P.Spad;
+                acc += (double)sum_sets(pp, P.S) * P.wgt[(r - 1) * P.B + b];
             }
         }
         sband[ty][tx] = acc;
@@ -146,13 +168,16 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_consta
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // last block: combine in block order (deterministic)
+    // last block: every thread sums a fixed, strided slice of the block
+    // partials, then a fixed reduction tree -> deterministic result
+    double tss = 0.0, tmx = -INFINITY;
+    for (int i = threadIdx.x; i < cell_blocks; i += blockDim.x) {
+        tss += __ldcg(&P.blockpart[2 * i]);
+        tmx = fmax(tmx, __ldcg(&P.blockpart[2 * i + 1]));
+    }
+    __syncthreads();
+    block_reduce2(tss, tmx, sh);
     if (threadIdx.x == 0) {
-        double tss = 0.0, tmx = -INFINITY;
-        for (int i = 0; i < cell_blocks; ++i) {
-            tss += ((volatile double *)P.blockpart)[2 * i];
-            tmx = fmax(tmx, ((volatile double *)P.blockpart)[2 * i + 1]);
-        }
         *P.counter = 0u;
         const double eps = (tmx > 0.0) ? sqrt(tss / (double)P.n_active) / tmx : 0.0;
         const int it = *P.iter;
@@ -284,7 +309,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
         if (is_cell && r != 0) {
             double gs = 0.0, ms = 0.0;
             for (int s = 0; s < G.S; ++s) {
-                const long long o = ((long long)s * G.B + b) * G.N + i;
+                const long long o = ((long long)b * G.N + i) * G.Spad + s;
                 gs += (double)G.gpart[o];
                 ms += (double)G.apart[o];
             }
@@ -312,10 +337,12 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+    for (int o = 0; o < NO; ++o) {
         double acc = 0.0;
-        for (int blk = 0; blk < (int)gridDim.x; ++blk) acc += ((volatile double *)G.blockpart)[(long long)blk * NO + o];
-        G.out[o] = acc;
+        for (int blk = threadIdx.x; blk < (int)gridDim.x; blk += blockDim.x)
+            acc += __ldcg(&G.blockpart[(long long)blk * NO + o]);
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) G.out[o] = acc;
     }
     if (threadIdx.x == 0) *G.counter = 0u;
 }

@@ -72,7 +72,7 @@ def test_fp64_fixed_iterations(bte, name, dim, kw, k, kind):
     np.testing.assert_allclose(plan.eps_history(k), ref["eps"], rtol=1e-9, atol=1e-300)
 
 
-TILES = [(0, 0), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4), (2, 8)]
+TILES = [(0, 0), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4)]
 
 
 @pytest.mark.parametrize("name,dim,kw", TINY, ids=[t[0] for t in TINY])
@@ -127,7 +127,7 @@ def test_square2d_full_size_fixed_iterations(bte):
     for kind in (1, 2):
         plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=k, tile_kind=kind)
         assert rel(T, ref["T"]) < 1e-12
-    for kind, dw in [(1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (2, 8), (0, 0)]:
+    for kind, dw in [(1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (0, 0)]:
         T32 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
         plan.solve(T32, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=kind)
         assert rel(T32.cpu().numpy(), ref["T"]) < 1e-5
