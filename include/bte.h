@@ -134,6 +134,7 @@ typedef struct {
     int store_e_every_iter; /* 1: write e to HBM on every sweep; 0: only the final one */
     int tile_kind;          /* 0 = autotuned; 1 = general wavefront kernel (any grid);
                                2 = row-block kernel (unmasked 1D/2D, one region) */
+    int dirs_per_cta;       /* row-block kernel: directions per CTA (0 = autotuned) */
 } bte_solve_opts;
 
 typedef struct {

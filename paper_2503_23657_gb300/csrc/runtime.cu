@@ -234,7 +234,8 @@ bool rowblock_ok(const bte_plan *p, int real_bytes, int *stage, int warps = 1) {
 }
 
 // Candidate tiles for a precision; kind_req 0 = any, 1 = general only, 2 = row-block only.
-std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req = 0, int dw_req = 0) {
+std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req = 0, int dw_req = 0,
+                                 int cw_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
     if (lz != 0 && kind_req != 2) {
@@ -255,6 +256,7 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
             for (int warps : {1, 2, 4, 8, 16}) {
                 if (warps > 1 && dw * warps > gmax) break;
                 if (!rowblock_ok(p, real_bytes, &stage, warps)) break;
+                if (cw_req && dw * warps != cw_req) continue;
                 out.push_back(tile_id(1, dw, dw * warps));  // cw = directions per CTA chunk
             }
         }
@@ -647,9 +649,10 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     if ((rc = upload_tables(p, ws))) return rc;
     // tile: the caller's restriction, then the autotuned choice (cached)
     if (o->tile_kind < 0 || o->tile_kind > 2) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1 or 2");
-    std::vector<int> cand = tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane);
+    std::vector<int> cand =
+        tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane, o->dirs_per_cta);
     if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
-    const int tkey = o->tile_kind * 100 + o->dirs_per_lane;
+    const int tkey = (o->tile_kind * 100 + o->dirs_per_lane) * 1000 + o->dirs_per_cta;
     int tid;
     if (ws.tuned.count(tkey)) {
         tid = ws.tuned[tkey];

@@ -95,66 +95,88 @@ struct RowSweep {
     long long eoff;    // b * D + d0
     int BD, ndir;
 
-    template <int R>
-    __device__ __forceinline__ void block(int t, int slot) {
-        const int dx = t - t_lo[R];
-        const bool valid = (unsigned)dx < (unsigned)nx;
-        const int c = c_base[R] + cstep * t;
-        real base = valid ? src_t[c] : real(0);
-        base *= srck;
-        if (with_phi) base = fma(valid ? src_phi[c] : real(0), qb, base);
+    // One wavefront step over the active blocks LO..HI, written as four
+    // phases in program order: (A) indices and shared-memory loads of every
+    // block, (B) all warp shuffles, (C) all arithmetic, (D) all stores.
+    // The shuffles read the previous step's registers, so they all precede
+    // the updates; keeping loads, shuffles and stores in separate phases
+    // lets the independent recurrences of all blocks and directions overlap.
+    template <int LO, int HI>
+    __device__ __forceinline__ void step(int t, int slot) {
+        constexpr int NB = HI - LO + 1;
+        int dxs[NB], cs[NB];
+        bool vals[NB];
+        real base[NB];
         real Ey = real(0);
-        if (R == 0) Ey = (lane == 0 && valid) ? wy[c - nx * yrow[0]] : real(0);
-        real acc = real(0);
 #pragma unroll
-        for (int dd = 0; dd < DW; ++dd) {
-            real vy;
-            if (R > 0) {
+        for (int i = 0; i < NB; ++i) {
+            const int R = LO + i;
+            dxs[i] = t - t_lo[R];
+            vals[i] = (unsigned)dxs[i] < (unsigned)nx;
+            cs[i] = c_base[R] + cstep * t;
+            real bv = vals[i] ? src_t[cs[i]] : real(0);
+            bv *= srck;
+            if (with_phi) bv = fma(vals[i] ? src_phi[cs[i]] : real(0), qb, bv);
+            base[i] = bv;
+            if (R == 0) Ey = (lane == 0 && vals[i]) ? wy[cs[i] - nx * yrow[0]] : real(0);
+        }
+        real vy[NB][DW];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int R = LO + i;
+#pragma unroll
+            for (int dd = 0; dd < DW; ++dd) {
                 // lane 31 hands row 32R-1 (block R-1) to lane 0 of block R
-                const real prov = (lane == 31) ? old[R > 0 ? R - 1 : 0][dd] : old[R][dd];
-                vy = __shfl_sync(0xffffffffu, prov, (lane + 31) & 31);
-            } else {
-                vy = __shfl_sync(0xffffffffu, old[0][dd], (lane + 31) & 31);
-                vy = (lane == 0) ? (ADJ ? Ey * w[dd] : Ey) : vy;  // row 0: upwind y-wall
+                real prov = old[R][dd];
+                if (R > 0) prov = (lane == 31) ? old[R > 0 ? R - 1 : 0][dd] : prov;
+                vy[i][dd] = __shfl_sync(0xffffffffu, prov, (lane + 31) & 31);
             }
-            real r0 = ADJ ? base * w[dd] : base;
-            r0 = fma(ax[dd], old[R][dd], r0);  // x-upwind (the wall value before x = 0)
-            r0 = fma(ay[dd], vy, r0);
-            const real en = r0 * invd[dd];
-            old[R][dd] = valid ? en : old[R][dd];
-            acc = ADJ ? acc + en : fma(w[dd], en, acc);
         }
-        if (direct) {
-            if (valid) part_b[(long long)c * spad] = acc;
-        } else {
-            ring[(slot * RB + R) * 32 + lane] = acc;
-        }
-        if (store_e && valid) {
-            real *ep = e + (long long)c * BD + eoff;
+        real acc[NB];
 #pragma unroll
-            for (int dd = 0; dd < DW; ++dd)
-                if (dd < ndir) ep[dd] = old[R][dd];
-        }
-        if (32 * R + lane == last_row && valid) {
-            real fs = real(0);
+        for (int i = 0; i < NB; ++i) {
+            const int R = LO + i;
+            acc[i] = real(0);
 #pragma unroll
-            for (int dd = 0; dd < DW; ++dd) fs = fma(wsy[dd], old[R][dd], fs);
-            fsy[c - nx * yrow[R]] = fs;
+            for (int dd = 0; dd < DW; ++dd) {
+                real yv = vy[i][dd];
+                if (R == 0) yv = (lane == 0) ? (ADJ ? Ey * w[dd] : Ey) : yv;  // row 0: upwind y-wall
+                real r0 = ADJ ? base[i] * w[dd] : base[i];
+                r0 = fma(ax[dd], old[R][dd], r0);  // x-upwind (the wall value before x = 0)
+                r0 = fma(ay[dd], yv, r0);
+                const real en = r0 * invd[dd];
+                old[R][dd] = vals[i] ? en : old[R][dd];
+                acc[i] = ADJ ? acc[i] + en : fma(w[dd], en, acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int R = LO + i;
+            const bool valid = vals[i];
+            const int c = cs[i];
+            if (direct) {
+                if (valid) part_b[(long long)c * spad] = acc[i];
+            } else {
+                ring[(slot * RB + R) * 32 + lane] = acc[i];
+            }
+            if (store_e && valid) {
+                real *ep = e + (long long)c * BD + eoff;
+#pragma unroll
+                for (int dd = 0; dd < DW; ++dd)
+                    if (dd < ndir) ep[dd] = old[R][dd];
+            }
+            if (32 * R + lane == last_row && valid) {
+                real fs = real(0);
+#pragma unroll
+                for (int dd = 0; dd < DW; ++dd) fs = fma(wsy[dd], old[R][dd], fs);
+                fsy[c - nx * yrow[R]] = fs;
+            }
         }
     }
 
-    // the active blocks R = HI..LO of one step, highest first, so block R
-    // reads block R-1's previous-step values before they change
-    template <int R, int LO>
-    __device__ __forceinline__ void blocks_desc(int t, int slot) {
-        if constexpr (R >= LO) {
-            block<R>(t, slot);
-            blocks_desc<R - 1, LO>(t, slot);
-        }
-    }
     template <int LO, int HI>
     __device__ __forceinline__ void steps(int t_begin, int t_end, int t0) {
-        for (int t = t_begin; t < t_end; ++t) blocks_desc<HI, LO>(t, t - t0);
+        for (int t = t_begin; t < t_end; ++t) step<LO, HI>(t, t - t0);
     }
 };
 
