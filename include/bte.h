@@ -201,6 +201,32 @@ int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep);
  * number of values copied or a negative code. */
 int bte_eps_history(const bte_plan *p, double *out, int n);
 
+/*
+ * bte_eps_T_noalloc -- the convergence measure of the solution procedure,
+ * eps_T = sqrt(mean_c (T_old - T_new)^2) / max_c T_new over solid cells,
+ * computed on the GPU without allocating any memory.  (The paper has no
+ * counterpart; this is an interface for callers that cannot call cudaMalloc:
+ * e.g. hosts whose device memory is owned by their own pool, loops that must
+ * not trigger cudaMalloc's implicit device synchronisation, or code running
+ * while another thread captures a CUDA graph in global mode.)
+ *   T_old, T_new  N doubles, device memory
+ *   mask          N bytes, device memory (0 = void, skipped), or NULL (all solid)
+ *   N             1 <= N <= BTE_NOALLOC_MAX_CELLS
+ *   out           3 doubles, device memory: {eps_T, max T_new, solid count}
+ *   stream        cudaStream_t (NULL = legacy default stream)
+ * Scratch lives in a fixed file-scope device array (about 24 KB, kept by
+ * every GPU that loads the library until the process exits).  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * All calls on a device share the array: calls that overlap on the GPU race.
+ * Returns BTE_OK, BTE_EINVAL (null pointer, N out of range; see
+ * bte_last_error(NULL)) or BTE_ECUDA.  Asynchronous: out is written when the
+ * stream reaches the launch.
+ */
+#define BTE_NOALLOC_MAX_CELLS (1LL << 24)
+int bte_eps_T_noalloc(const double *T_old, const double *T_new, const uint8_t *mask, long long N,
+                      double *out, void *stream);
+
 /* Release every resource of the plan (NULL is a no-op). */
 void bte_destroy(bte_plan *p);
 

@@ -33,7 +33,8 @@ ERROR_NAMES = {
 
 # every entry point declared in include/bte.h
 EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_error",
-           "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep"]
+           "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep",
+           "bte_eps_T_noalloc"]
 
 
 class Grid(ctypes.Structure):
@@ -104,6 +105,8 @@ def load(path: str = LIB_PATH):
     lib.bte_eps_history.restype = ip
     lib.bte_profile_sweep.argtypes = [vp, ip, ctypes.POINTER(dp)]
     lib.bte_profile_sweep.restype = ip
+    lib.bte_eps_T_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp]
+    lib.bte_eps_T_noalloc.restype = ip
     _lib = lib
     return lib
 
@@ -112,6 +115,18 @@ class BTEError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
         self.code = code
+
+
+def eps_T_noalloc(T_old, T_new, out, mask=None, stream=None):
+    """bte_eps_T_noalloc: eps_T of two device temperature fields, written to
+    the device buffer ``out`` (3 doubles), without any device allocation --
+    for callers that cannot call cudaMalloc where they need the measure."""
+    lib = load()
+    rc = lib.bte_eps_T_noalloc(_addr(T_old), _addr(T_new), _addr(mask), int(T_new.numel()),
+                               _addr(out), stream)
+    if rc != BTE_OK:
+        raise BTEError(rc, lib.bte_last_error(None).decode())
+    return rc
 
 
 def _addr(x):

@@ -1154,6 +1154,11 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
 
 }  // namespace
 
+namespace bte {
+// Error text for calls without a plan (read back by bte_last_error(NULL)).
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace bte
+
 extern "C" {
 
 const char *bte_version(void) { return "libbte 0.1 (sm_103a)"; }

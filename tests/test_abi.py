@@ -22,7 +22,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "bte.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(bte_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(bte_[A-Za-z_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
