@@ -44,10 +44,10 @@ struct SweepParams {
     const real *__restrict__ tsrc;    // fwd: T - T_ref; adj: Theta   [N]
     const real *__restrict__ phi;     // fwd source profile [N] or null
     const real *__restrict__ ein;     // [B][F] boundary values
-    real *__restrict__ part;          // [B][N][Spad] per-subset reduction
+    real *__restrict__ part;          // [B][Spad][N] per-subset reduction
     real *__restrict__ fsum;          // [S][B][F] per-subset face sums
     real *__restrict__ e;             // [N][B][D] store (fwd) / read (adj)
-    real *__restrict__ gpart;         // [B][N][Spad] adj: sum_d (mu_d - w_d Theta)(e_d - e0)
+    real *__restrict__ gpart;         // [B][Spad][N] adj: sum_d (mu_d - w_d Theta)(e_d - e0)
     const Subset *__restrict__ sub;   // [S]
     const real *__restrict__ coef;    // [B][D][8]: a_x a_y a_z w ws_x ws_y ws_z pad
     const real *__restrict__ invdiag; // [R][B][D]
@@ -67,13 +67,16 @@ struct SweepParams {
 template <typename real>
 struct Sweep2DParams {
     int nx, ny;
-    int B, D, F, S;                   // S = number of chunks
-    int Spad;                         // S rounded up to a multiple of 4
+    int B, D, F, S;                   // S = number of chunks (face-sum sets)
+    int Spad;                         // cell partial sets rounded up to a multiple of 4
     int warps_per_cta;
+    int ring;                         // 1: warps of a chunk combine per-cell sums through shared-
+                                      //    memory slices (one cell partial set per chunk); 0: every
+                                      //    warp writes its own set (chunk * warps_per_cta + warp)
     const real *__restrict__ tsrc;    // fwd: T - T_ref; adj: Theta [N, padded to 16 elements]
     const real *__restrict__ phi;     // fwd source profile [N, padded] or null
     const real *__restrict__ ein;     // [B][F] boundary values
-    real *__restrict__ part;          // [B][N][Spad]
+    real *__restrict__ part;          // [B][Spad][N]
     real *__restrict__ fsum;          // [S][B][F]
     real *__restrict__ e;             // [N][B][D] (store_e)
     const Subset *__restrict__ sub;   // [S] chunks
@@ -92,19 +95,20 @@ struct Sweep2DParams {
 template <typename real>
 cudaError_t launch_sweep2d(const Sweep2DParams<real> &p, int dirs_per_warp, int row_blocks, bool adjoint,
                            cudaStream_t st);
-size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, int real_bytes);
+size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, int ring, int real_bytes);
 
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.
 template <typename real>
 struct UpdateParams {
     long long N;
-    int B, S, F, R;
+    int B, S, F, R;                   // S = cell partial sets
     int Spad;
+    int Sf;                           // face-sum sets (entries of sub)
     int adjoint;
     double T_ref;
     const int2 *__restrict__ cell;
     const Subset *__restrict__ sub;
-    const real *__restrict__ part;    // [B][N][Spad]
+    const real *__restrict__ part;    // [B][Spad][N]
     const real *__restrict__ fsum;    // [S][B][F]
     const double *__restrict__ x_in;  // fwd T_old / adj Theta_old [N]
     double *__restrict__ x_out;       // [N]
@@ -162,8 +166,8 @@ struct GradParams {
     int B, S, F;
     int Spad;
     const int2 *__restrict__ cell;
-    const real *__restrict__ apart;     // [B][N][Spad] sum_d mu_d
-    const real *__restrict__ gpart;     // [B][N][Spad] sum_d (mu_d - w_d Theta)(e_d - e0)
+    const real *__restrict__ apart;     // [B][Spad][N] sum_d mu_d
+    const real *__restrict__ gpart;     // [B][Spad][N] sum_d (mu_d - w_d Theta)(e_d - e0)
     const double *__restrict__ phi;     // [N] source profile or null
     const double *__restrict__ inv_tt;  // [R][B] 1/(tau_rb tau_b)
     const double *__restrict__ qcoef;   // [B] Q_amp derivative weight C_b/(4 pi sum C)

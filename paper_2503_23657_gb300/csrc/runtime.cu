@@ -180,7 +180,9 @@ bool is_device_ptr(const void *ptr) {
 long long cell_index(const bte_plan *p, int i, int j, int k) { return i + (long long)p->nx * (j + (long long)p->ny * k); }
 
 // A sweep tile: kernel kind (0 = general wavefront kernel, 1 = row-block 2D
-// kernel), directions per lane/warp (dw) and directions per CTA chunk (cw).
+// kernel with one partial set per warp, 2 = row-block 2D kernel combining its
+// warps' per-cell sums through shared-memory slices), directions per lane/warp (dw) and
+// directions per CTA chunk (cw).
 struct Tile {
     int kind, dw, cw;
 };
@@ -223,14 +225,14 @@ int rowblock_rb(const bte_plan *p) {
 // CTA's shared memory (reduction ring for `warps` warps, wall values) fits.
 // *stage tells whether the per-cell inputs also fit (else they are read
 // from global memory).
-bool rowblock_ok(const bte_plan *p, int real_bytes, int *stage, int warps = 1) {
+bool rowblock_ok(const bte_plan *p, int real_bytes, int *stage, int warps = 1, int ring = 0) {
     const int rb = rowblock_rb(p);
     if (p->dim > 2 || rb == 0 || p->n_active != p->N) return false;
     for (long long c = 0; c < p->N; ++c)
         if (p->mask[c] != 1) return false;
     const size_t lim = 200 * 1024;
-    *stage = sweep2d_smem(p->nx, p->ny, 1, p->phi.empty() ? 0 : 1, warps, rb, real_bytes) <= lim ? 1 : 0;
-    return sweep2d_smem(p->nx, p->ny, 0, 0, warps, rb, real_bytes) <= lim;
+    *stage = 1;
+    return sweep2d_smem(p->nx, p->ny, 1, p->phi.empty() ? 0 : 1, warps, rb, ring, real_bytes) <= lim;
 }
 
 // Candidate tiles for a precision; kind_req 0 = any, 1 = general only, 2 = row-block only.
@@ -255,8 +257,8 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
             if (dw_req && dw != dw_req) continue;
             for (int warps : {1, 2, 4, 8, 16}) {
                 if (warps > 1 && dw * warps > gmax) break;
-                if (!rowblock_ok(p, real_bytes, &stage, warps)) break;
                 if (cw_req && dw * warps != cw_req) continue;
+                if (!rowblock_ok(p, real_bytes, &stage, warps, 0)) continue;
                 out.push_back(tile_id(1, dw, dw * warps));  // cw = directions per CTA chunk
             }
         }
@@ -292,10 +294,19 @@ int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
 // set; the row-block kernel down to 1 direction per set).
 int max_subsets(const bte_plan *p) {
     int dummy = 0;
-    const int per = (rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy)) ? 1 : 4;  // row-block: dw >= 1
+    const bool rb = rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy);
+    const int per = rb ? 1 : 4;  // row-block: one set per warp of >= 1 direction
     int s = 0;
     for (size_t g = 0; g < p->groups_cnt.size(); ++g) s += (p->groups_cnt[g] + per - 1) / per;
+    // a partly filled chunk still has all its warps' sets
+    if (rb) s += 16 * (int)p->groups_cnt.size();
     return s;
+}
+
+// Cell partial sets a tile writes (direct row-block tiles: one per warp).
+int cell_sets(int tid, int chunks) {
+    const Tile tl = tile_of(tid);
+    return tl.kind == 1 ? chunks * (tl.cw / tl.dw) : chunks;
 }
 
 // Per-solve tables (depend on tau overrides, wall temperatures, Q_amp, T_ref).
@@ -445,7 +456,8 @@ UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool
     UpdateParams<real> u{};
     u.N = p->N;
     u.B = p->B;
-    u.S = (int)ws.subsets.at(tid).first.size();
+    u.Sf = (int)ws.subsets.at(tid).first.size();
+    u.S = cell_sets(tid, u.Sf);
     u.Spad = (u.S + 3) & ~3;
     u.F = p->F;
     u.R = p->R;
@@ -498,13 +510,14 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     auto pr = ws.dsub.at(tid);
     sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
     sp.S = (int)ws.subsets.at(tid).first.size();
-    sp.Spad = (sp.S + 3) & ~3;
+    sp.ring = tl.kind == 2 ? 1 : 0;
+    sp.Spad = (cell_sets(tid, sp.S) + 3) & ~3;
     sp.wall_face = ws.wall.template as<int>();
     sp.wall_stride = p->wall_stride;
     sp.done = p->d_status.as<int>();
     sp.status = &p->d_status.as<Status>()->status;
     int stage = 0;
-    rowblock_ok(p, (int)sizeof(real), &stage, sp.warps_per_cta);
+    rowblock_ok(p, (int)sizeof(real), &stage, sp.warps_per_cta, sp.ring);
     sp.stage = stage;
     return sp;
 }
@@ -514,7 +527,7 @@ template <typename real>
 cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool adj, const real *tsrc,
                               const real *ein, bool store_e, bool use_done, cudaStream_t stream) {
     const Tile tl = tile_of(tid);
-    if (tl.kind == 1) {
+    if (tl.kind >= 1) {
         Sweep2DParams<real> sp = sweep2d_params(p, ws, tid, adj);
         sp.tsrc = tsrc;
         sp.ein = ein;
@@ -772,7 +785,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         st->seconds = ms * 1e-3;
         st->updates_per_s = st->seconds > 0 ? (double)n * p->n_active * p->B * p->D / st->seconds : 0.0;
         st->dirs_per_lane = tile_of(tid).dw;
-        st->tile_kind = tile_of(tid).kind + 1;
+        st->tile_kind = tile_of(tid).kind == 0 ? 1 : 2;
         st->dirs_per_cta = tile_of(tid).cw;
         st->kernel_launches = launches;
     }
@@ -979,7 +992,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         st->seconds = ms * 1e-3;
         st->updates_per_s = st->seconds > 0 ? (double)(n + 1) * p->n_active * p->B * p->D / st->seconds : 0.0;
         st->dirs_per_lane = tile_of(dw).dw;
-        st->tile_kind = tile_of(dw).kind + 1;
+        st->tile_kind = tile_of(dw).kind == 0 ? 1 : 2;
         st->dirs_per_cta = tile_of(dw).cw;
         st->kernel_launches = launches + 3;  // final sweep + update + gradient reduction
     }

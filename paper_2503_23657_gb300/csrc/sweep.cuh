@@ -105,9 +105,9 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
 
     const bool vec_ok = (sub.cnt == DW) && ((D & 3) == 0) && ((sub.d0 & 3) == 0) && (DW % 4 == 0);
     const int n_steps = P.nx + P.ny + P.nz - 2;
-    // partial sums [B][N][Spad]: this CTA's set s of band b
-    real *const part_sb = P.part + (long long)b * N * P.Spad + s;
-    real *const gpart_sb = (ADJ && P.read_e) ? P.gpart + (long long)b * N * P.Spad + s : nullptr;
+    // partial sums [B][Spad][N]: this CTA's set s of band b
+    real *const part_sb = P.part + ((long long)b * P.Spad + s) * N;
+    real *const gpart_sb = (ADJ && P.read_e) ? P.gpart + ((long long)b * P.Spad + s) * N : nullptr;
 
     for (int t = 0; t < n_steps; ++t) {
         const int rb = (t + 1) & 1;  // buffer written at step t-1
@@ -175,7 +175,7 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
                 }
             }
             if (act) {
-                part_sb[c * P.Spad] = acc;
+                part_sb[c] = acc;
                 real *ep = P.e + (c * B + b) * (long long)D + sub.d0;
                 if (!ADJ && P.store_e) {
                     if (vec_ok) {
@@ -202,7 +202,7 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
 #pragma unroll
                     for (int dd = 0; dd < DW; ++dd)
                         if (dd < sub.cnt) g = fma(old[l][dd] - w[dd] * thc, ep[dd] - e0, g);
-                    gpart_sb[c * P.Spad] = g;
+                    gpart_sb[c] = g;
                 }
                 // face sums at the boundary sides the traversal leaves by
                 if (bm & ((1u << (up_x ^ 1)) | (1u << (up_y ^ 1)) | (Z ? (1u << (up_z ^ 1)) : 0u))) {

@@ -17,12 +17,12 @@
 //   * the per-cell temperature deviation (and source profile) is brought
 //     into shared memory once per CTA by a TMA bulk copy (cp.async.bulk on
 //     an mbarrier, bounded wait), the band's upwind wall values are staged;
-//   * the warps of a CTA visit the same cells at the same step, so their
-//     per-cell weighted direction sums go to a shared-memory ring of
-//     kRing diagonals; every kRing steps the CTA sums the ring over its
-//     warps in a fixed order and writes one partial per cell (no atomics,
-//     bitwise reproducible), and the wall face sums are combined the same
-//     way at the end.
+//   * per-cell weighted direction sums: every warp stores its own partial
+//     set directly (one 4-byte store per lane and step; the lanes of a step
+//     sit on a diagonal, so a warp store touches 32 sectors -- the store path,
+//     not the arithmetic, is what larger DW amortises).  Results do not depend
+//     on scheduling.  Wall face sums are combined over the CTA's warps in a
+//     fixed order.
 #pragma once
 
 #include <stdint.h>
@@ -68,8 +68,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 constexpr long long kWaitPolls = 1LL << 22;
 
-constexpr int kRing = 16;  // diagonals per CTA reduction round
-
 template <int DW, int RB>
 struct Sweep2DTile {
     static constexpr int kMaxThreads = 512;
@@ -87,9 +85,7 @@ struct RowSweep {
     real srck, qb;
     bool with_phi, store_e, direct;
     const real *src_t, *src_phi, *wy;
-    real *ring;        // this warp's ring [kRing][RB][32] (direct == false)
-    real *part_b;      // band b's partials, set `set` (direct == true)
-    int spad;
+    real *part_b;      // band b's partials, this warp's set
     real *fsy;         // this warp's downwind y-wall sums, by X
     real *e;
     long long eoff;    // b * D + d0
@@ -154,11 +150,7 @@ struct RowSweep {
             const int R = LO + i;
             const bool valid = vals[i];
             const int c = cs[i];
-            if (direct) {
-                if (valid) part_b[(long long)c * spad] = acc[i];
-            } else {
-                ring[(slot * RB + R) * 32 + lane] = acc[i];
-            }
+            if (valid) part_b[c] = acc[i];
             if (store_e && valid) {
                 real *ep = e + (long long)c * BD + eoff;
 #pragma unroll
@@ -178,6 +170,8 @@ struct RowSweep {
     __device__ __forceinline__ void steps(int t_begin, int t_end, int t0) {
         for (int t = t_begin; t < t_end; ++t) step<LO, HI>(t, t - t0);
     }
+
+    static_assert(RB >= 1 && RB <= 5, "row blocks");
 };
 
 template <typename real, int DW, int RB, bool ADJ>
@@ -189,12 +183,11 @@ sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     const int N = P.nx * P.ny;
     const int Npad = (N + 15) & ~15;
     const int W = P.warps_per_cta;
-    const bool direct = (W == 1);
+    const bool direct = (P.ring == 0);
     const bool with_phi = (!ADJ && P.phi != nullptr);
     real *s_t = reinterpret_cast<real *>(smem_raw);                  // [Npad] T - T_ref or Theta
-    real *s_phi = s_t + (P.stage ? Npad : 0);                        // [Npad] source profile (fwd)
-    real *s_ring = s_phi + ((P.stage && with_phi) ? Npad : 0);       // [W][kRing][RB][32] (W > 1)
-    real *s_fs = s_ring + (direct ? 0 : W * kRing * RB * 32);        // [W][nx + ny] wall sums
+    real *s_phi = s_t + Npad;                                        // [Npad] source profile (fwd)
+    real *s_fs = s_phi + (with_phi ? Npad : 0);                      // [W][nx + ny] wall sums
     real *s_wx = s_fs + W * (P.ny + P.nx);                           // [ny] upwind x-wall values
     real *s_wy = s_wx + P.ny;                                        // [nx] upwind y-wall values
 
@@ -209,7 +202,7 @@ sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     const int up_x = negx ? 1 : 0, up_y = negy ? 3 : 2;
 
     // ---- prologue: TMA bulk copy of the per-cell inputs, wall values ----
-    if (P.stage) {
+    {
         if (threadIdx.x == 0) {
             mbar_init(&s_bar, 1);
             mbar_fence_init();
@@ -234,8 +227,7 @@ sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
         }
         for (int i = threadIdx.x; i < W * (P.ny + P.nx); i += nthr) s_fs[i] = real(0);
     }
-    bool ok = true;
-    if (P.stage) ok = mbar_wait_bounded(&s_bar, 0, kWaitPolls);
+    const bool ok = mbar_wait_bounded(&s_bar, 0, kWaitPolls);
     __syncthreads();
     if (!ok) {
         // the bulk copy did not complete: report, wait once more for it, stop
@@ -255,13 +247,13 @@ sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     S.with_phi = with_phi;
     S.store_e = P.store_e != 0;
     S.direct = direct;
-    S.set = s;
-    S.src_t = P.stage ? s_t : P.tsrc;
-    S.src_phi = P.stage ? s_phi : P.phi;
+    S.set = direct ? s * W + warp : s;
+    // staged inputs only: shared-memory pointers the compiler can see as such
+    S.src_t = s_t;
+    S.src_phi = s_phi;
     S.wy = s_wy;
-    S.ring = s_ring + warp * kRing * RB * 32;
-    S.part_b = P.part + (long long)b * N * P.Spad + s;
-    S.spad = P.Spad;
+    // partial sums [B][sets][N]
+    S.part_b = P.part + ((long long)b * P.Spad + S.set) * N;
     S.fsy = s_fs + warp * (P.ny + P.nx);
     real *fsx = S.fsy + P.nx;
     S.e = P.e;
@@ -302,54 +294,30 @@ sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
         for (int dd = 0; dd < DW; ++dd) S.old[r][dd] = ADJ ? ex * S.w[dd] : ex;
     }
 
-    // ---- wavefront: phases of constant active blocks (ring flush every kRing steps) ----
+    // ---- wavefront: phases of constant active blocks ----
     const int n_steps = P.nx + P.ny - 1;
     const int nblk = (P.ny + 31) / 32;
-    const int round = direct ? n_steps : kRing;
-    for (int t0 = 0; t0 < n_steps; t0 += round) {
-        const int t1 = min(t0 + round, n_steps);
-        int tt = t0;
-        while (tt < t1) {
-            const int lo = (tt - 31 - P.nx < 0) ? 0 : (tt - 31 - P.nx) / 32 + 1;
-            const int hi = min(nblk - 1, tt / 32);
-            int tn = t1;
-            if (hi + 1 < nblk) tn = min(tn, 32 * (hi + 1));
-            tn = min(tn, 32 * lo + 31 + P.nx);
-#define BTE_PHASE(L, H)                                                 \
-    case (L) * 8 + (H):                                                 \
-        if constexpr ((H) < RB) S.template steps<(L), (H)>(tt, tn, t0); \
+    int tt = 0;
+    while (tt < n_steps) {
+        const int lo = (tt - 31 - P.nx < 0) ? 0 : (tt - 31 - P.nx) / 32 + 1;
+        const int hi = min(nblk - 1, tt / 32);
+        int tn = n_steps;
+        if (hi + 1 < nblk) tn = min(tn, 32 * (hi + 1));
+        tn = min(tn, 32 * lo + 31 + P.nx);
+#define BTE_PHASE(L, H)                                                \
+    case (L) * 8 + (H):                                                \
+        if constexpr ((H) < RB) S.template steps<(L), (H)>(tt, tn, 0); \
         break;
-            switch (lo * 8 + hi) {
-                BTE_PHASE(0, 0) BTE_PHASE(0, 1) BTE_PHASE(0, 2) BTE_PHASE(0, 3) BTE_PHASE(0, 4)
-                BTE_PHASE(1, 1) BTE_PHASE(1, 2) BTE_PHASE(1, 3) BTE_PHASE(1, 4)
-                BTE_PHASE(2, 2) BTE_PHASE(2, 3) BTE_PHASE(2, 4)
-                BTE_PHASE(3, 3) BTE_PHASE(3, 4)
-                BTE_PHASE(4, 4)
-                default: break;
-            }
+        switch (lo * 8 + hi) {
+            BTE_PHASE(0, 0) BTE_PHASE(0, 1) BTE_PHASE(0, 2) BTE_PHASE(0, 3) BTE_PHASE(0, 4)
+            BTE_PHASE(1, 1) BTE_PHASE(1, 2) BTE_PHASE(1, 3) BTE_PHASE(1, 4)
+            BTE_PHASE(2, 2) BTE_PHASE(2, 3) BTE_PHASE(2, 4)
+            BTE_PHASE(3, 3) BTE_PHASE(3, 4)
+            BTE_PHASE(4, 4)
+            default: break;
+        }
 #undef BTE_PHASE
-            tt = tn;
-        }
-        if (!direct) {
-            __syncthreads();
-            // sum the ring over the warps (fixed order): warp q takes ring rows
-            // (slot, block) q, q+W, ...; lane = row within the block
-            for (int slot = 0; slot < t1 - t0; ++slot) {
-                const int t = t0 + slot;
-                for (int rr = warp; rr < nblk; rr += W) {
-                    const int j = 32 * rr + lane;
-                    const int x = t - j;
-                    real sum = real(0);
-                    for (int q = 0; q < W; ++q) sum += s_ring[((q * kRing + slot) * RB + rr) * 32 + lane];
-                    if (j < P.ny && x >= 0 && x < P.nx) {
-                        const int X = negx ? P.nx - 1 - x : x;
-                        const int Y = negy ? P.ny - 1 - j : j;
-                        P.part[((long long)b * N + X + P.nx * Y) * P.Spad + s] = sum;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+        tt = tn;
     }
     // downwind x-wall sums: after its last column every row keeps that value
 #pragma unroll
@@ -377,11 +345,14 @@ sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
 }
 
 template <typename real>
-size_t sweep2d_smem_bytes(int nx, int ny, int stage, int with_phi, int warps, int rb) {
+size_t sweep2d_smem_bytes(int nx, int ny, int stage, int with_phi, int warps, int rb, int ring) {
     const size_t N = (size_t)nx * ny;
     const size_t Npad = (N + 15) & ~(size_t)15;
-    size_t n = (warps > 1 ? (size_t)warps * kRing * rb * 32 : 0) + (size_t)warps * (nx + ny) + nx + ny;
-    if (stage) n += Npad * (with_phi ? 2 : 1);
+    (void)ring;
+    (void)rb;
+    size_t n = (size_t)warps * (nx + ny) + nx + ny;
+    (void)stage;
+    n += Npad * (with_phi ? 2 : 1);  // per-cell inputs are always staged
     return n * sizeof(real);
 }
 
@@ -390,7 +361,8 @@ cudaError_t launch_sweep2d_t(const Sweep2DParams<real> &p, cudaStream_t st) {
     const int threads = p.warps_per_cta * 32;
     if (threads > Sweep2DTile<DW, RB>::kMaxThreads || p.ny > 32 * RB) return cudaErrorInvalidConfiguration;
     const size_t smem =
-        sweep2d_smem_bytes<real>(p.nx, p.ny, p.stage, (!ADJ && p.phi != nullptr) ? 1 : 0, p.warps_per_cta, RB);
+        sweep2d_smem_bytes<real>(p.nx, p.ny, p.stage, (!ADJ && p.phi != nullptr) ? 1 : 0, p.warps_per_cta, RB,
+                                 p.ring);
     auto kern = sweep2d_kernel<real, DW, RB, ADJ>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

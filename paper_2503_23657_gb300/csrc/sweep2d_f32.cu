@@ -26,8 +26,8 @@ cudaError_t launch_sweep2d<float>(const Sweep2DParams<float> &p, int dw, int rb,
     return launch_sweep2d_float(p, dw, rb, adj, st);
 }
 
-size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, int real_bytes) {
-    return real_bytes == 4 ? sweep2d_smem_bytes<float>(nx, ny, stage, with_phi, warps, rb)
-                           : sweep2d_smem_bytes<double>(nx, ny, stage, with_phi, warps, rb);
+size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, int ring, int real_bytes) {
+    return real_bytes == 4 ? sweep2d_smem_bytes<float>(nx, ny, stage, with_phi, warps, rb, ring)
+                           : sweep2d_smem_bytes<double>(nx, ny, stage, with_phi, warps, rb, ring);
 }
 }  // namespace bte

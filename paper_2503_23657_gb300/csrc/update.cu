@@ -48,36 +48,20 @@ __device__ __forceinline__ void block_reduce2(double &a, double &m, double *sh) 
     }
 }
 
-// Sum of the S partial sets of one (band, cell): they are contiguous
-// ([B][N][Spad] layout, rows 16-byte aligned), read with vector loads that
-// are all independent; summed in the sweep precision in a fixed order.
-__device__ __forceinline__ float sum_sets(const float *pp, int S) {
-    const float4 *p4 = reinterpret_cast<const float4 *>(pp);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    const int n4 = S >> 2;
-#pragma unroll 8
-    for (int q = 0; q < n4; ++q) {
-        const float4 v = p4[q];
-        a0 += v.x;
-        a1 += v.y;
-        a2 += v.z;
-        a3 += v.w;
+// Sum of the S partial sets of one (band, cell); sets are N apart
+// ([B][Spad][N] layout), so a warp's loads of one set are coalesced; eight
+// independent loads are in flight, summed in a fixed order in the sweep
+// precision.
+template <typename real>
+__device__ __forceinline__ real sum_sets(const real *pp, int S, long long N) {
+    real a[8] = {real(0), real(0), real(0), real(0), real(0), real(0), real(0), real(0)};
+    int s = 0;
+    for (; s + 8 <= S; s += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] += pp[(long long)(s + q) * N];
     }
-    for (int s = n4 << 2; s < S; ++s) a0 += pp[s];
-    return (a0 + a1) + (a2 + a3);
-}
-__device__ __forceinline__ double sum_sets(const double *pp, int S) {
-    const double2 *p2 = reinterpret_cast<const double2 *>(pp);
-    double a0 = 0.0, a1 = 0.0;
-    const int n2 = S >> 1;
-#pragma unroll 8
-    for (int q = 0; q < n2; ++q) {
-        const double2 v = p2[q];
-        a0 += v.x;
-        a1 += v.y;
-    }
-    if (S & 1) a0 += pp[S - 1];
-    return a0 + a1;
+    for (int q = 0; s < S; ++s, ++q) a[q] += pp[(long long)s * N];
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 // Threads of a cell block are laid out [band slot y][cell x] (32 cells x 8
@@ -104,8 +88,8 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_consta
         double acc = 0.0;
         if (r != 0) {
             for (int b = ty; b < P.B; b += kBandSlots) {
-                const real *pp = P.part + ((long long)b * P.N + c) * P.Spad;
-                acc += (double)sum_sets(pp, P.S) * P.wgt[(r - 1) * P.B + b];
+                const real *pp = P.part + (long long)b * P.Spad * P.N + c;
+                acc += (double)sum_sets(pp, P.S, P.N) * P.wgt[(r - 1) * P.B + b];
             }
         }
         sband[ty][tx] = acc;
@@ -147,7 +131,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_consta
                 P.ein_out[fb] = P.ein_fixed[fb];
             } else {
                 double sum = 0.0;
-                for (int s = 0; s < P.S; ++s) {
+                for (int s = 0; s < P.Sf; ++s) {
                     const bool neg = (P.sub[s].neg >> a) & 1;
                     // the subset leaves a cell by the plus side iff it runs upward on axis a
                     if (neg != plus) sum += (double)P.fsum[((long long)s * P.B + b) * P.F + f];
@@ -309,7 +293,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
         if (is_cell && r != 0) {
             double gs = 0.0, ms = 0.0;
             for (int s = 0; s < G.S; ++s) {
-                const long long o = ((long long)b * G.N + i) * G.Spad + s;
+                const long long o = ((long long)b * G.Spad + s) * G.N + i;
                 gs += (double)G.gpart[o];
                 ms += (double)G.apart[o];
             }
