@@ -33,6 +33,7 @@ WORKLOAD = "square2d_128x128_B15_D64_fwd+adj_eps1e-6"
 METRIC = "cell*band*direction updates/s (fwd+adj to eps_T<1e-6, FP32 sweeps)"
 TOL = 1e-6
 L2_FLUSH_BYTES = 512 << 20
+TIME_EVERY = 8   # sweeps timed with CUDA events: one in every TIME_EVERY iterations
 
 
 def dist_env():
@@ -94,6 +95,21 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
+# capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
+# since the capture has no entry)
+NCU_TRAFFIC = {}
+
+
+def sweep_kernel_name(p, st):
+    """The forward sweep kernel a solve ran, as ncu names it."""
+    dw = st["dirs_per_lane"]
+    if st["tile_kind"] == 2:
+        rb = next(r for r in (1, 2, 3, 4, 5) if 32 * r >= p.n[1])
+        return f"sweep2d_kernel<float, {dw}, {rb}, false>"
+    return f"sweep_kernel<float, {dw}, 1, false, false>"
 
 
 def cpu_baseline_oracle(iters: int = 20):
@@ -200,6 +216,10 @@ def main():
         rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g, tol=TOL, max_iter=100000)
         return sf, sa
 
+    # the sweep of every 8th iteration of the timed steps is bracketed by CUDA
+    # events on its stream (inside the captured graphs): the dominant kernel's
+    # mean duration, sampled over the whole timed region
+    plan.set_sweep_timing(TIME_EVERY)
     for _ in range(args.warmup):
         step(T, g)
     torch.cuda.synchronize()
@@ -208,6 +228,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("bench_timed")   # lets a profiler select the timed steps
     times, fstats, astats = [], [], []
     for _ in range(args.steps):
         flush.fill_(1.0)   # evict the previous step's working set from L2
@@ -221,6 +242,7 @@ def main():
         fstats.append(sf)
         astats.append(sa)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
 
@@ -245,22 +267,31 @@ def main():
     rc, s64 = plan.solve(T64, precision=m.BTE_FP64, tol=TOL, max_iter=100000, stream=sp)
     dT_fp64 = float((T - T64).abs().max() / T64.abs().max())
 
-    # dominant kernel: the sweep (FP32, last solve's tile), timed with CUDA events
-    plan.solve(T, precision=m.BTE_FP32, tol=TOL, max_iter=100000, stream=sp,
-               store_e_every_iter=args.store_e_every_iter)
-    sweep_ms = plan.profile_sweep(reps=200)
+    plan.set_sweep_timing(0)
+    # dominant kernel: the forward sweep, its mean launch duration from the
+    # CUDA events of the timed steps
+    fwd_sweep_s = sum(f["sweep_seconds"] for f in fstats)
+    fwd_sweeps = sum(f["sweep_launches"] for f in fstats)
+    adj_sweep_s = sum(a["sweep_seconds"] for a in astats)
+    adj_sweeps = sum(a["sweep_launches"] for a in astats)
+    sweep_ms = fwd_sweep_s / fwd_sweeps * 1e3
     dw = fstats[-1]["dirs_per_lane"]
-    flops_per_update = 7.0   # 3 FMA + 1 MUL (x, y coupling, source, 1/diag, weighted sum)
+    kernel = sweep_kernel_name(p, fstats[-1])
+    flops_per_update = 7.0   # 3 FMA + 1 MUL per cell x band x direction (Eq. 3 upwind update + weighted sum)
     sweep_flops = flops_per_update * per_update
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
-    smax = clk.get("sm_max_mhz") or 2070.0
+    smax = 2070.0
     peak_fp32 = sm_count * 128 * 2 * smax * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes at max clock
     achieved = sweep_flops / (sweep_ms * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC.get(kernel)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp32, "traffic": None,
-                "kernel": f"sweep_kernel<float,{dw},1,false,false>",
-                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz",
-                "sweep_ms": sweep_ms}
+                "frac": achieved / peak_fp32, "traffic": traffic,
+                "kernel": kernel,
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (max SM clock)",
+                "algorithmic": f"{flops_per_update:g} flop x {per_update} cell*band*direction updates per launch",
+                "sweep_ms": sweep_ms, "sweep_launches_timed": fwd_sweeps,
+                "adj_sweep_ms": adj_sweep_s / max(adj_sweeps, 1) * 1e3,
+                "sweep_share_of_step": (fwd_sweep_s + adj_sweep_s) / t_total}
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     T_init_h = torch.full((p.n_cells,), 300.0, dtype=torch.float64).pin_memory()

@@ -133,8 +133,9 @@ typedef struct {
     int dirs_per_lane;      /* sweep tile: directions per lane/warp (0 = autotuned) */
     int store_e_every_iter; /* 1: write e to HBM on every sweep; 0: only the final one */
     int tile_kind;          /* 0 = autotuned; 1 = general wavefront kernel (any grid);
-                               2 = row-block kernel (unmasked 1D/2D, one region) */
-    int dirs_per_cta;       /* row-block kernel: directions per CTA (0 = autotuned) */
+                               2 = row-block kernel (unmasked 1D/2D, one region);
+                               3 = row-pipeline kernel (unmasked 1D/2D, one region) */
+    int dirs_per_cta;       /* row kernels: directions per CTA (0 = autotuned) */
 } bte_solve_opts;
 
 typedef struct {
@@ -146,8 +147,12 @@ typedef struct {
     double updates_per_s;   /* iterations * solid cells * B * D / seconds */
     int dirs_per_lane;      /* tile used: directions per lane/warp */
     long long kernel_launches; /* kernels launched by the call (incl. early-exit ones) */
-    int tile_kind;          /* tile used: 1 general, 2 row-block (see bte_solve_opts) */
+    int tile_kind;          /* tile used: 1 general, 2 row-block, 3 row-pipeline (see bte_solve_opts) */
     int dirs_per_cta;       /* tile used: directions per CTA */
+    double sweep_seconds;   /* with sweep timing on (bte_set_sweep_timing): summed device
+                               time of the call's timed source-iteration sweep launches,
+                               each bracketed by CUDA events on its stream; else 0 */
+    long long sweep_launches; /* number of sweep launches summed in sweep_seconds */
 } bte_stats;
 
 /* Fill opts with defaults: FP32, tol 1e-6, max_iter 100000, T_init 300 K,
@@ -195,6 +200,19 @@ int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, doub
  * no solve preceded it.
  */
 int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep);
+
+/*
+ * bte_set_sweep_timing -- every >= 1: every following bte_solve / bte_adjoint
+ * brackets the sweep launch of every `every`-th source iteration (counted
+ * within each convergence poll interval, whose first iteration is always
+ * timed; also inside the captured CUDA graphs) with a pair of CUDA events
+ * and reports the summed durations and their number in
+ * bte_stats.sweep_seconds / sweep_launches.  Each timed sweep adds a few
+ * microseconds of launch latency; every = 0 (the default) records nothing.
+ * Returns BTE_OK, BTE_EINVAL (null plan, every < 0) or BTE_ECUDA (event
+ * creation failed).
+ */
+int bte_set_sweep_timing(bte_plan *p, int every);
 
 /* Copy the eps_T history of the last bte_solve (one value per iteration,
  * at most n, the first 65536 iterations) into out (host).  Returns the

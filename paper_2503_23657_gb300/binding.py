@@ -34,7 +34,7 @@ ERROR_NAMES = {
 # every entry point declared in include/bte.h
 EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_error",
            "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep",
-           "bte_eps_T_noalloc"]
+           "bte_set_sweep_timing", "bte_eps_T_noalloc"]
 
 
 class Grid(ctypes.Structure):
@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("T_max", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("updates_per_s", ctypes.c_double), ("dirs_per_lane", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong), ("tile_kind", ctypes.c_int),
-                ("dirs_per_cta", ctypes.c_int)]
+                ("dirs_per_cta", ctypes.c_int), ("sweep_seconds", ctypes.c_double),
+                ("sweep_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -105,6 +106,8 @@ def load(path: str = LIB_PATH):
     lib.bte_eps_history.restype = ip
     lib.bte_profile_sweep.argtypes = [vp, ip, ctypes.POINTER(dp)]
     lib.bte_profile_sweep.restype = ip
+    lib.bte_set_sweep_timing.argtypes = [vp, ip]
+    lib.bte_set_sweep_timing.restype = ip
     lib.bte_eps_T_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp]
     lib.bte_eps_T_noalloc.restype = ip
     _lib = lib
@@ -244,6 +247,14 @@ class Plan:
         if rc != BTE_OK:
             raise BTEError(rc, self.error())
         return ms.value
+
+    def set_sweep_timing(self, every=1):
+        """bte_set_sweep_timing: bracket the sweep launch of every `every`-th
+        iteration with CUDA events (0 = off); stats then carry sweep_seconds /
+        sweep_launches."""
+        rc = self._lib.bte_set_sweep_timing(self._h, int(every))
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
 
     def eps_history(self, n):
         out = np.zeros(n)

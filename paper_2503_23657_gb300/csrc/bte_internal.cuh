@@ -90,12 +90,18 @@ struct Sweep2DParams {
     int *__restrict__ status;         // set to 2 if a bounded wait expires
     int store_e;
     int stage;                        // stage per-cell inputs in shared memory (TMA bulk copy)
+    int groups;                       // row-pipeline kernel: direction groups per CTA
+    int adj;                          // row-pipeline kernel: 1 = adjoint sweep
 };
 
 template <typename real>
 cudaError_t launch_sweep2d(const Sweep2DParams<real> &p, int dirs_per_warp, int row_blocks, bool adjoint,
                            cudaStream_t st);
 size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, int ring, int real_bytes);
+// Row-pipeline 2D kernel (groups of DW directions, one warp per 32 rows).
+template <typename real>
+cudaError_t launch_sweep2dp(const Sweep2DParams<real> &p, int dirs_per_warp, cudaStream_t st);
+size_t sweep2dp_smem(int nx, int ny, int with_phi, int groups, int dw, int real_bytes);
 
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.
 template <typename real>

@@ -81,6 +81,7 @@ struct Workspace {
     std::vector<std::unique_ptr<DevBuf>> subbufs;
     std::map<int, int> tuned;  // tile request -> chosen tile
     DevBuf wall;  // [6][wall_stride] face index of each wall position (-1: none)
+    DevBuf gradpart;  // gradient reduction block partials
     // graph cache
     cudaGraphExec_t graph = nullptr;
     std::tuple<int, int, double, int> graph_key{-1, -1, 0.0, -1};
@@ -119,6 +120,10 @@ struct bte_plan {
     Workspace<float> ws32;
     Workspace<double> ws64;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // per-sweep timing (bte_set_sweep_timing): an event pair around the sweep
+    // of every time_every-th iteration of a graph (0 = off)
+    int time_every = 0;
+    std::vector<cudaEvent_t> tev;
     std::string err;
     // last forward solve
     bool solved = false;
@@ -138,6 +143,7 @@ struct bte_plan {
         if (h_status) cudaFreeHost(h_status);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        for (cudaEvent_t e : tev) cudaEventDestroy(e);
     }
 };
 
@@ -181,13 +187,16 @@ long long cell_index(const bte_plan *p, int i, int j, int k) { return i + (long 
 
 // A sweep tile: kernel kind (0 = general wavefront kernel, 1 = row-block 2D
 // kernel with one partial set per warp, 2 = row-block 2D kernel combining its
-// warps' per-cell sums through shared-memory slices), directions per lane/warp (dw) and
-// directions per CTA chunk (cw).
+// warps' per-cell sums through shared-memory slices, 3 = row-pipeline 2D
+// kernel with one partial set per direction group), directions per lane/warp
+// (dw) and directions per CTA chunk (cw).
 struct Tile {
     int kind, dw, cw;
 };
 inline int tile_id(int kind, int dw, int cw) { return kind * 100000 + cw * 100 + dw; }
 inline Tile tile_of(int id) { return Tile{id / 100000, id % 100, (id / 100) % 1000}; }
+// the bte_solve_opts.tile_kind value of an internal kernel kind
+inline int abi_kind(int kind) { return kind == 0 ? 1 : (kind == 3 ? 3 : 2); }
 
 // Directions of one orientation group split into subsets of at most dw.
 std::vector<Subset> make_subsets(const bte_plan *p, int dw, bool flip) {
@@ -235,12 +244,24 @@ bool rowblock_ok(const bte_plan *p, int real_bytes, int *stage, int warps = 1, i
     return sweep2d_smem(p->nx, p->ny, 1, p->phi.empty() ? 0 : 1, warps, rb, ring, real_bytes) <= lim;
 }
 
-// Candidate tiles for a precision; kind_req 0 = any, 1 = general only, 2 = row-block only.
+// Row-pipeline 2D kernel: unmasked 1D/2D grid with one region, `groups`
+// groups of ceil(ny / 32) warps per CTA (at most 16 warps), shared memory fits.
+bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw) {
+    if (p->dim > 2 || p->n_active != p->N) return false;
+    const int nrb = (p->ny + 31) / 32;
+    if (groups < 1 || groups * nrb > 16) return false;
+    for (long long c = 0; c < p->N; ++c)
+        if (p->mask[c] != 1) return false;
+    return sweep2dp_smem(p->nx, p->ny, p->phi.empty() ? 0 : 1, groups, dw, real_bytes) <= 200 * 1024;
+}
+
+// Candidate tiles for a precision; kind_req 0 = any, 1 = general only,
+// 2 = row-block only, 3 = row-pipeline only.
 std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req = 0, int dw_req = 0,
                                  int cw_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
-    if (lz != 0 && kind_req != 2) {
+    if (lz != 0 && (kind_req == 0 || kind_req == 1)) {
         const bool z = p->dim == 3;
         const int WY = (p->ny + 31) / 32;
         const int WZ = z ? (p->nz + lz - 1) / lz : 1;
@@ -250,9 +271,20 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
         }
     }
     int stage = 0;
-    if (kind_req != 1 && rowblock_ok(p, real_bytes, &stage)) {
-        int gmax = 0;
-        for (int c : p->groups_cnt) gmax = std::max(gmax, c);
+    int gmax = 0;
+    for (int c : p->groups_cnt) gmax = std::max(gmax, c);
+    if (kind_req == 0 || kind_req == 3) {
+        for (int dw : {1, 2, 4}) {
+            if (dw_req && dw != dw_req) continue;
+            for (int groups : {1, 2, 4, 8, 16}) {
+                if (groups > 1 && dw * groups > gmax) break;
+                if (cw_req && dw * groups != cw_req) continue;
+                if (!rowpipe_ok(p, real_bytes, groups, dw)) continue;
+                out.push_back(tile_id(3, dw, dw * groups));
+            }
+        }
+    }
+    if ((kind_req == 0 || kind_req == 2) && rowblock_ok(p, real_bytes, &stage)) {
         for (int dw : {1, 2, 4}) {
             if (dw_req && dw != dw_req) continue;
             for (int warps : {1, 2, 4, 8, 16}) {
@@ -294,19 +326,20 @@ int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
 // set; the row-block kernel down to 1 direction per set).
 int max_subsets(const bte_plan *p) {
     int dummy = 0;
-    const bool rb = rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy);
-    const int per = rb ? 1 : 4;  // row-block: one set per warp of >= 1 direction
+    const bool rb = rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy) || rowpipe_ok(p, 4, 1, 1) ||
+                    rowpipe_ok(p, 8, 1, 1);
+    const int per = rb ? 1 : 4;  // row kernels: one set per warp / group of >= 1 direction
     int s = 0;
     for (size_t g = 0; g < p->groups_cnt.size(); ++g) s += (p->groups_cnt[g] + per - 1) / per;
-    // a partly filled chunk still has all its warps' sets
-    if (rb) s += 16 * (int)p->groups_cnt.size();
+    // a partly filled chunk still has all its warps' / groups' sets
+    if (rb) s += 32 * (int)p->groups_cnt.size();
     return s;
 }
 
 // Cell partial sets a tile writes (direct row-block tiles: one per warp).
 int cell_sets(int tid, int chunks) {
     const Tile tl = tile_of(tid);
-    return tl.kind == 1 ? chunks * (tl.cw / tl.dw) : chunks;
+    return (tl.kind == 1 || tl.kind == 3) ? chunks * (tl.cw / tl.dw) : chunks;
 }
 
 // Per-solve tables (depend on tau overrides, wall temperatures, Q_amp, T_ref).
@@ -511,6 +544,11 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
     sp.S = (int)ws.subsets.at(tid).first.size();
     sp.ring = tl.kind == 2 ? 1 : 0;
+    if (tl.kind == 3) {
+        sp.groups = tl.cw / tl.dw;
+        sp.warps_per_cta = sp.groups * ((p->ny + 31) / 32);
+    }
+    sp.adj = adj ? 1 : 0;
     sp.Spad = (cell_sets(tid, sp.S) + 3) & ~3;
     sp.wall_face = ws.wall.template as<int>();
     sp.wall_stride = p->wall_stride;
@@ -534,6 +572,7 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
         sp.store_e = store_e ? 1 : 0;
         sp.e = ws.e.template as<real>();
         if (!use_done) sp.done = nullptr;
+        if (tl.kind == 3) return launch_sweep2dp<real>(sp, tl.dw, stream);
         return launch_sweep2d<real>(sp, tl.dw, rowblock_rb(p), adj, stream);
     }
     SweepParams<real> sp = sweep_params(p, ws, tid, adj);
@@ -545,11 +584,24 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
     return launch_sweep<real>(sp, tl.dw, tile_layers(p), p->dim == 3, adj, stream);
 }
 
+// a timing event: inside a stream capture it must become an event-record
+// node of the graph (a plain record only marks a fork/join point there)
+inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t stream) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return e;
+    if (cap == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, stream, cudaEventRecordExternal);
+    return cudaEventRecord(ev, stream);
+}
+
 template <typename real>
 cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int tid, int parity, double tol, bool store_e,
-                            bool replay, cudaStream_t stream) {
-    cudaError_t e = launch_tile_sweep(p, ws, tid, false, ws.tdev[parity].template as<real>(),
-                                      ws.ein[parity].template as<real>(), store_e, !replay, stream);
+                            bool replay, cudaStream_t stream, cudaEvent_t ta = nullptr, cudaEvent_t tb = nullptr) {
+    cudaError_t e = ta ? record_timing_event(ta, stream) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = launch_tile_sweep(p, ws, tid, false, ws.tdev[parity].template as<real>(), ws.ein[parity].template as<real>(),
+                              store_e, !replay, stream);
+    if (e == cudaSuccess && tb) e = record_timing_event(tb, stream);
     if (e != cudaSuccess || replay) return e;
     UpdateParams<real> u = update_params(p, ws, tid, false, tol);
     u.x_in = ws.T[parity].template as<double>();
@@ -632,7 +684,7 @@ int autotune(bte_plan *p, Workspace<real> &ws, const std::vector<int> &cand, cud
             if (rep >= 2) tmin = std::min(tmin, ms);
         }
         if (std::getenv("BTE_TUNE_VERBOSE"))
-            std::fprintf(stderr, "bte tune: kind %d dw %d cw %d: %.4f ms/iteration\n", tile_of(tid).kind + 1,
+            std::fprintf(stderr, "bte tune: kind %d dw %d cw %d: %.4f ms/iteration\n", abi_kind(tile_of(tid).kind),
                          tile_of(tid).dw, tile_of(tid).cw, tmin);
         if (tmin < best) {
             best = tmin;
@@ -640,6 +692,36 @@ int autotune(bte_plan *p, Workspace<real> &ws, const std::vector<int> &cand, cud
         }
     }
     return best_tid;
+}
+
+// event pair i brackets the sweep of iteration i of a graph replay
+cudaError_t ensure_timing_events(bte_plan *p, int pairs) {
+    while ((int)p->tev.size() < 2 * pairs) {
+        cudaEvent_t e;
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) return ce;
+        p->tev.push_back(e);
+    }
+    return cudaSuccess;
+}
+
+bool timed_iter(const bte_plan *p, int i) { return p->time_every > 0 && i % p->time_every == 0; }
+cudaEvent_t tev_a(bte_plan *p, int i) { return timed_iter(p, i) ? p->tev[2 * (i / p->time_every)] : nullptr; }
+cudaEvent_t tev_b(bte_plan *p, int i) { return timed_iter(p, i) ? p->tev[2 * (i / p->time_every) + 1] : nullptr; }
+
+// after the stream reached the last of k iterations: add the durations of
+// their timed sweeps (ms) and count them; cudaSuccess only if every pair was
+// recorded
+cudaError_t sum_timing_events(bte_plan *p, int k, double *ms, long long *n) {
+    for (int i = 0; i < k; ++i) {
+        if (!timed_iter(p, i)) continue;
+        float t = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&t, tev_a(p, i), tev_b(p, i));
+        if (e != cudaSuccess) return e;
+        *ms += t;
+        *n += 1;
+    }
+    return cudaSuccess;
 }
 
 template <typename real>
@@ -661,7 +743,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     if ((rc = begin_state(p, o, ws, stream))) return rc;
     if ((rc = upload_tables(p, ws))) return rc;
     // tile: the caller's restriction, then the autotuned choice (cached)
-    if (o->tile_kind < 0 || o->tile_kind > 2) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1 or 2");
+    if (o->tile_kind < 0 || o->tile_kind > 3) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1, 2 or 3");
     std::vector<int> cand =
         tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane, o->dirs_per_cta);
     if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
@@ -687,8 +769,9 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     int poll = o->poll_every > 0 ? o->poll_every : 32;
     poll = std::max(2, poll + (poll & 1));
     const bool store_every = o->store_e_every_iter != 0;
+    if (p->time_every) CK(p, ensure_timing_events(p, poll));
     // graph of `poll` iterations (even, so every replay starts at parity 0)
-    auto key = std::make_tuple(dw, poll, tol, store_every ? 1 : 0);
+    auto key = std::make_tuple(dw, poll, tol, (store_every ? 1 : 0) | (p->time_every << 1));
     if (!ws.graph || ws.graph_key != key) {
         if (ws.graph) {
             cudaGraphExecDestroy(ws.graph);
@@ -699,7 +782,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         cudaGraph_t g;
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         for (int i = 0; i < poll && ce == cudaSuccess; ++i)
-            ce = enqueue_forward(p, ws, dw, i & 1, tol, store_every, false, cs);
+            ce = enqueue_forward(p, ws, dw, i & 1, tol, store_every, false, cs, tev_a(p, i), tev_b(p, i));
         cudaError_t ce2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
         if (ce != cudaSuccess) return fail(p, BTE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -715,18 +798,22 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     const int max_iter = o->max_iter;
     int enq = 0;
     long long launches = 0;
+    double sweep_ms = 0.0;
+    long long n_timed = 0;
     CK(p, cudaEventRecord(p->ev0, stream));
     while (enq < max_iter) {
         const int k = std::min(poll, max_iter - enq);
         if (k == poll) {
             CK(p, cudaGraphLaunch(ws.graph, stream));
         } else {
-            for (int i = 0; i < k; ++i) CK(p, enqueue_forward(p, ws, dw, (enq + i) & 1, tol, store_every, false, stream));
+            for (int i = 0; i < k; ++i)
+                CK(p, enqueue_forward(p, ws, dw, (enq + i) & 1, tol, store_every, false, stream, tev_a(p, i), tev_b(p, i)));
         }
         enq += k;
         launches += 2LL * k;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
         CK(p, cudaStreamSynchronize(stream));
+        if (p->time_every) CK(p, sum_timing_events(p, k, &sweep_ms, &n_timed));
         if (p->h_status->done || p->h_status->status) break;
     }
     CK(p, cudaEventRecord(p->ev1, stream));
@@ -785,9 +872,11 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         st->seconds = ms * 1e-3;
         st->updates_per_s = st->seconds > 0 ? (double)n * p->n_active * p->B * p->D / st->seconds : 0.0;
         st->dirs_per_lane = tile_of(tid).dw;
-        st->tile_kind = tile_of(tid).kind == 0 ? 1 : 2;
+        st->tile_kind = abi_kind(tile_of(tid).kind);
         st->dirs_per_cta = tile_of(tid).cw;
         st->kernel_launches = launches;
+        st->sweep_seconds = sweep_ms * 1e-3;
+        st->sweep_launches = n_timed;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the temperature update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "max_iter reached before eps_T < tol");
@@ -799,10 +888,13 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
 // ---------------------------------------------------------------------------
 template <typename real>
 cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity, double tol, bool final_pass,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, cudaEvent_t ta = nullptr, cudaEvent_t tb = nullptr) {
     if (!final_pass) {
-        cudaError_t e = launch_tile_sweep(p, ws, dw, true, ws.thdev[parity].template as<real>(),
-                                          ws.mein[parity].template as<real>(), false, true, stream);
+        cudaError_t e = ta ? record_timing_event(ta, stream) : cudaSuccess;
+        if (e == cudaSuccess)
+            e = launch_tile_sweep(p, ws, dw, true, ws.thdev[parity].template as<real>(), ws.mein[parity].template as<real>(),
+                                  false, true, stream);
+        if (e == cudaSuccess && tb) e = record_timing_event(tb, stream);
         if (e != cudaSuccess) return e;
         UpdateParams<real> u = update_params(p, ws, dw, true, tol);
         u.eps_hist = nullptr;
@@ -898,7 +990,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
     const int poll = 32;
-    auto key = std::make_tuple(dw, poll, tol, 0);
+    if (p->time_every) CK(p, ensure_timing_events(p, poll));
+    auto key = std::make_tuple(dw, poll, tol, p->time_every << 1);
     if (!ws.agraph || ws.agraph_key != key) {
         if (ws.agraph) {
             cudaGraphExecDestroy(ws.agraph);
@@ -908,7 +1001,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         CK(p, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t gr;
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        for (int i = 0; i < poll && ce == cudaSuccess; ++i) ce = enqueue_adjoint(p, ws, dw, i & 1, tol, false, cs);
+        for (int i = 0; i < poll && ce == cudaSuccess; ++i)
+            ce = enqueue_adjoint(p, ws, dw, i & 1, tol, false, cs, tev_a(p, i), tev_b(p, i));
         cudaError_t ce2 = cudaStreamEndCapture(cs, &gr);
         cudaStreamDestroy(cs);
         if (ce != cudaSuccess || ce2 != cudaSuccess)
@@ -923,6 +1017,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     }
     int enq = 0;
     long long launches = p->e_current ? 0 : 1;
+    double sweep_ms = 0.0;
+    long long n_timed = 0;
     CK(p, cudaEventRecord(p->ev0, stream));
     while (enq < max_iter) {
         const int k = std::min(poll, max_iter - enq);
@@ -930,11 +1026,13 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         if (k == poll) {
             CK(p, cudaGraphLaunch(ws.agraph, stream));
         } else {
-            for (int i = 0; i < k; ++i) CK(p, enqueue_adjoint(p, ws, dw, (enq + i) & 1, tol, false, stream));
+            for (int i = 0; i < k; ++i)
+                CK(p, enqueue_adjoint(p, ws, dw, (enq + i) & 1, tol, false, stream, tev_a(p, i), tev_b(p, i)));
         }
         enq += k;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
         CK(p, cudaStreamSynchronize(stream));
+        if (p->time_every) CK(p, sum_timing_events(p, k, &sweep_ms, &n_timed));
         if (p->h_status->done || p->h_status->status) break;
     }
     const int n = p->h_status->iter;
@@ -967,9 +1065,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     gp.face_kind = p->d_face_kind.as<int>();
     gp.msum = ws.msum.template as<double>();
     const int nblk = (int)((N + 255) / 256) + (p->F + 255) / 256;
-    DevBuf bp;
-    CK(p, bp.ensure(sizeof(double) * (size_t)nblk * (B + 7)));
-    gp.blockpart = bp.as<double>();
+    CK(p, ws.gradpart.ensure(sizeof(double) * (size_t)nblk * (B + 7)));
+    gp.blockpart = ws.gradpart.template as<double>();
     gp.counter = p->d_counter.as<unsigned int>();
     gp.out = ws.grad_out.template as<double>();
     CK(p, launch_grad<real>(gp, stream));
@@ -992,9 +1089,11 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         st->seconds = ms * 1e-3;
         st->updates_per_s = st->seconds > 0 ? (double)(n + 1) * p->n_active * p->B * p->D / st->seconds : 0.0;
         st->dirs_per_lane = tile_of(dw).dw;
-        st->tile_kind = tile_of(dw).kind == 0 ? 1 : 2;
+        st->tile_kind = abi_kind(tile_of(dw).kind);
         st->dirs_per_cta = tile_of(dw).cw;
         st->kernel_launches = launches + 3;  // final sweep + update + gradient reduction
+        st->sweep_seconds = sweep_ms * 1e-3;
+        st->sweep_launches = n_timed;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the adjoint update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "adjoint: max_iter reached before tol");
@@ -1260,6 +1359,18 @@ int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep) {
     if (!p->solved || p->solved_iters < 1) return fail(p, BTE_ESTATE, "bte_profile_sweep needs a preceding bte_solve");
     if (p->solved_precision == BTE_FP32) return profile_t<float>(p, reps, ms_per_sweep);
     return profile_t<double>(p, reps, ms_per_sweep);
+}
+
+int bte_set_sweep_timing(bte_plan *p, int every) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (every < 0) return fail(p, BTE_EINVAL, "bte_set_sweep_timing: every must be >= 0");
+    p->time_every = every;
+    if (every && ensure_timing_events(p, 32) != cudaSuccess) {
+        cudaGetLastError();
+        p->time_every = 0;
+        return fail(p, BTE_ECUDA, "bte_set_sweep_timing: cudaEventCreate failed");
+    }
+    return BTE_OK;
 }
 
 int bte_eps_history(const bte_plan *p, double *out, int n) {

@@ -75,6 +75,27 @@ def test_adjoint_rowblock_matches_general(bte):
     np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-9, atol=1e-15)
 
 
+def test_adjoint_rowpipe_matches_general(bte):
+    """2D unmasked 70 x 70 square (three 32-row blocks, the last ragged): the
+    row-pipeline and row-block kernels' adjoints equal the general kernel's
+    (FP64)."""
+    p = bi.square_2d(n=70, L=0.6e-6)
+    p = p.copy(C=p.C[:3], v=p.v[:3], tau=p.tau[:3])
+    plan = bte.Plan(p)
+    g = np.zeros(p.n_cells)
+    g[[5, 777, 2300, 4899]] = [1.0, -0.5, 0.25, 2.0]
+    out = []
+    for kind in (1, 2, 3):
+        T = np.zeros(p.n_cells)
+        rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=1e-13, tile_kind=kind)
+        assert st["tile_kind"] == kind
+        rc, g_tau, g_Tw, g_Q, st = plan.adjoint(g, tol=1e-13)
+        out.append((g_tau, g_Tw, g_Q))
+    for o in out[1:]:
+        np.testing.assert_allclose(o[0], out[0][0], rtol=1e-9)
+        np.testing.assert_allclose(o[1], out[0][1], rtol=1e-9, atol=1e-15)
+
+
 @pytest.mark.parametrize("name,dim,kw", CASES, ids=[c[0] for c in CASES])
 def test_fp32_adjoint_within_fd_tolerance(bte, name, dim, kw):
     p, ref, probes, T_obs = _setup(dim, kw)

@@ -52,10 +52,10 @@ TINY = [
 
 @pytest.mark.parametrize("name,dim,kw", TINY, ids=[t[0] for t in TINY])
 @pytest.mark.parametrize("k", [1, 7])
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 def test_fp64_fixed_iterations(bte, name, dim, kw, k, kind):
     p = bi.tiny(dim, **kw)
-    if kind == 2 and not rowblock_eligible(p):
+    if kind >= 2 and not rowblock_eligible(p):
         pytest.skip("row-block kernel needs an unmasked 1D/2D grid")
     ref = oracle.solve(p, max_iter=k, tol=0.0)
     plan = bte.Plan(p)
@@ -72,14 +72,14 @@ def test_fp64_fixed_iterations(bte, name, dim, kw, k, kind):
     np.testing.assert_allclose(plan.eps_history(k), ref["eps"], rtol=1e-9, atol=1e-300)
 
 
-TILES = [(0, 0), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4)]
+TILES = [(0, 0), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4), (3, 1), (3, 2), (3, 4)]
 
 
 @pytest.mark.parametrize("name,dim,kw", TINY, ids=[t[0] for t in TINY])
 @pytest.mark.parametrize("kind,dw", TILES, ids=[f"k{a}dw{b}" for a, b in TILES])
 def test_fp32_fixed_iterations(bte, name, dim, kw, kind, dw):
     p = bi.tiny(dim, **kw)
-    if kind == 2 and not rowblock_eligible(p):
+    if kind >= 2 and not rowblock_eligible(p):
         pytest.skip("row-block kernel needs an unmasked 1D/2D grid")
     k = 12
     ref = oracle.solve(p, max_iter=k, tol=0.0)
@@ -124,13 +124,15 @@ def test_square2d_full_size_fixed_iterations(bte):
     ref = oracle.solve(p, max_iter=k, tol=0.0)
     plan = bte.Plan(p)
     T = np.zeros(p.n_cells)
-    for kind in (1, 2):
+    for kind in (1, 2, 3):
         plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=k, tile_kind=kind)
         assert rel(T, ref["T"]) < 1e-12
-    for kind, dw in [(1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (0, 0)]:
+    for kind, dw in [(1, 4), (1, 8), (1, 16), (2, 1), (2, 2), (2, 4), (3, 1), (3, 2), (3, 4), (0, 0)]:
         T32 = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
-        plan.solve(T32, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=kind)
+        rc, st = plan.solve(T32, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=kind)
         assert rel(T32.cpu().numpy(), ref["T"]) < 1e-5
+        if kind:
+            assert st["tile_kind"] == kind
 
 
 def test_square2d_reduced_converged(bte):
@@ -171,6 +173,23 @@ def test_finfet_reduced_fixed_iterations(bte):
     assert rel(T, ref["T"], act) < 1e-5
 
 
+@pytest.mark.parametrize("cw", [1, 2, 4, 8, 16])
+def test_rowpipe_direction_chunks(bte, cw):
+    """Row-pipeline kernel with every chunk width on a 37 x 70 grid (three
+    row blocks, the last one ragged) with a source and diffuse walls: FP64
+    within 1e-12 of the oracle after 5 iterations."""
+    p = bi.tiny(2, n=(37, 70, 1), B=2, diffuse=(1, 2), source=True, n_polar=4, n_az=16)
+    k = 5
+    ref = oracle.solve(p, max_iter=k, tol=0.0)
+    plan = bte.Plan(p)
+    T = np.zeros(p.n_cells)
+    dw = min(cw, 4)
+    rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=k, tile_kind=3, dirs_per_lane=dw,
+                        dirs_per_cta=cw)
+    assert st["tile_kind"] == 3 and st["dirs_per_cta"] == cw
+    assert rel(T, ref["T"]) < 1e-12
+
+
 def test_device_and_host_outputs_agree(bte):
     p = bi.tiny(2, n=(6, 5, 1), B=2, diffuse=(2,), source=True)
     plan = bte.Plan(p)
@@ -184,11 +203,12 @@ def test_device_and_host_outputs_agree(bte):
     np.testing.assert_array_equal(ed.cpu().numpy(), eh)
 
 
-def test_rowblock_rejected_for_masked_grid(bte):
+@pytest.mark.parametrize("kind", [2, 3])
+def test_row_kernels_rejected_for_masked_grid(bte, kind):
     p = bi.tiny(2, n=(7, 6, 1), B=2, masked=True, diffuse=(2,))
     plan = bte.Plan(p)
     T = np.zeros(p.n_cells)
-    rc, st = plan.solve(T, tol=0.0, max_iter=2, tile_kind=2, check=False)
+    rc, st = plan.solve(T, tol=0.0, max_iter=2, tile_kind=kind, check=False)
     assert rc == -1
 
 
@@ -225,3 +245,35 @@ def test_adjoint_before_solve_is_state_error(bte):
     plan = bte.Plan(p)
     rc, *_ = plan.adjoint(np.zeros(p.n_cells), check=False)
     assert rc == -7
+
+
+def test_sweep_timing_events(bte):
+    """bte_set_sweep_timing: one event-timed sweep per iteration (forward and
+    adjoint), durations inside the loop time, results unchanged."""
+    p = bi.square_2d(n=40)
+    plan = bte.Plan(p)
+    a = np.zeros(p.n_cells)
+    rc, s0 = plan.solve(a, tol=0.0, max_iter=37)
+    assert s0["sweep_launches"] == 0 and s0["sweep_seconds"] == 0.0
+    plan.set_sweep_timing(1)
+    b = np.zeros(p.n_cells)
+    rc, s1 = plan.solve(b, tol=0.0, max_iter=37)     # one 32-iteration graph + 5 direct
+    np.testing.assert_array_equal(a, b)
+    assert s1["sweep_launches"] == 37
+    assert 0.0 < s1["sweep_seconds"] < s1["seconds"]
+    rc, s3 = plan.solve(b, tol=0.0, max_iter=64)     # graph replays only
+    assert s3["sweep_launches"] == 64
+    assert 0.3 * s3["seconds"] < s3["sweep_seconds"] < s3["seconds"]
+    g = np.zeros(p.n_cells)
+    g[::7] = 1.0
+    rc, *_, sa = plan.adjoint(g, tol=0.0, max_iter=21)
+    assert sa["sweep_launches"] == 21 and 0.0 < sa["sweep_seconds"] < sa["seconds"]
+    plan.set_sweep_timing(8)                          # iterations 0, 8, 16, 24 of each graph
+    rc, s4 = plan.solve(b, tol=0.0, max_iter=64)
+    assert s4["sweep_launches"] == 8
+    assert 0.0 < s4["sweep_seconds"] < s4["seconds"] / 4
+    plan.set_sweep_timing(0)
+    c = np.zeros(p.n_cells)
+    rc, s2 = plan.solve(c, tol=0.0, max_iter=37)
+    np.testing.assert_array_equal(a, c)
+    assert s2["sweep_launches"] == 0
