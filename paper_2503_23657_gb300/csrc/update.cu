@@ -64,63 +64,33 @@ __device__ __forceinline__ real sum_sets(const real *pp, int S, long long N) {
     return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-// Threads of a cell block are laid out [band slot y][cell x] (32 cells x 8
-// band slots): each thread sums the partial sets of its bands (within a band
-// in the sweep precision, i.e. over directions), the weighted band sums are
-// combined in FP64 in a fixed order.
+// Sum and max over one warp (fixed shuffle tree: deterministic).
+__device__ __forceinline__ void warp_reduce2(double &a, double &m) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+}
+
+// Face blocks come first (they start with the cell blocks instead of after
+// them); a cell block is 32 cells x 8 band slots: each thread sums the
+// partial sets of its bands (within a band in the sweep precision, i.e. over
+// directions), warp 0 combines the weighted band sums in FP64 in a fixed
+// order, updates its 32 cells and reduces the residual over them.  FP64
+// arithmetic is kept to what the result needs (a warp-wide FP64 operation is
+// slow on this GPU), so only warp 0 of a block reduces.
 constexpr int kCellsPerBlock = 32;
 constexpr int kBandSlots = kUpdThreads / kCellsPerBlock;
 
 template <typename real>
-__global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_constant__ UpdateParams<real> P,
-                                                             int cell_blocks) {
-    if (!P.ignore_done && *((volatile int *)P.done) != 0) return;
-    __shared__ double sh[2 * (kUpdThreads / 32)];
+__global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(const __grid_constant__ UpdateParams<real> P,
+                                                             int face_blocks, int cell_blocks) {
     __shared__ double sband[kBandSlots][kCellsPerBlock];
     __shared__ int is_last;
-    double ss = 0.0, mx = -INFINITY;
-    if ((int)blockIdx.x < cell_blocks) {
-        const int tx = threadIdx.x % kCellsPerBlock;
-        const int ty = threadIdx.x / kCellsPerBlock;
-        const long long c = (long long)blockIdx.x * kCellsPerBlock + tx;
-        int r = 0;
-        if (c < P.N) r = P.cell[c].y & kRegionMask;
-        double acc = 0.0;
-        if (r != 0) {
-            for (int b = ty; b < P.B; b += kBandSlots) {
-                const real *pp = P.part + (long long)b * P.Spad * P.N + c;
-                acc += (double)sum_sets(pp, P.S, P.N) * P.wgt[(r - 1) * P.B + b];
-            }
-        }
-        sband[ty][tx] = acc;
-        __syncthreads();
-        if (ty == 0 && c < P.N) {
-            if (r != 0) {
-                double tot = 0.0;
-#pragma unroll
-                for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
-                double xn;
-                if (!P.adjoint) {
-                    const double dev = tot * P.Kinv[r - 1];
-                    xn = P.T_ref + dev;
-                    P.xdev_out[c] = (real)dev;
-                    mx = xn;
-                } else {
-                    xn = (P.g[c] + tot) * P.Kinv[r - 1];
-                    P.xdev_out[c] = (real)xn;
-                    mx = fabs(xn);
-                }
-                const double d = xn - P.x_in[c];
-                ss = d * d;
-                if (!isfinite(xn)) ss = NAN;
-                P.x_out[c] = xn;
-            } else {
-                P.x_out[c] = 0.0;
-                P.xdev_out[c] = (real)0;
-            }
-        }
-    } else {
-        const long long fb = (long long)(blockIdx.x - cell_blocks) * blockDim.x + threadIdx.x;
+    if ((int)blockIdx.x < face_blocks) {
+        if (!P.ignore_done && *((volatile int *)P.done) != 0) return;
+        const long long fb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         if (fb < (long long)P.F * P.B) {
             const int b = (int)(fb / P.F);
             const int f = (int)(fb % P.F);
@@ -130,41 +100,121 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const __grid_consta
             if (P.face_kind[f] == 0 && !P.adjoint) {
                 P.ein_out[fb] = P.ein_fixed[fb];
             } else {
+                // sets leaving the cell through this face: those running
+                // upward on axis a for a plus face, downward otherwise
                 double sum = 0.0;
                 for (int s = 0; s < P.Sf; ++s) {
                     const bool neg = (P.sub[s].neg >> a) & 1;
-                    // the subset leaves a cell by the plus side iff it runs upward on axis a
                     if (neg != plus) sum += (double)P.fsum[((long long)s * P.B + b) * P.F + f];
                 }
                 if (P.fsum_total) P.fsum_total[fb] = sum;
                 P.ein_out[fb] = (P.face_kind[f] == 0) ? (real)0 : (real)(sum * P.side_scale[side * P.B + b]);
             }
         }
+        return;
     }
-    block_reduce2(ss, mx, sh);
-    if (threadIdx.x == 0) {
-        P.blockpart[2 * blockIdx.x] = ss;
-        P.blockpart[2 * blockIdx.x + 1] = mx;
+    const int cb = blockIdx.x - face_blocks;
+    const int tx = threadIdx.x % kCellsPerBlock;
+    const int ty = threadIdx.x / kCellsPerBlock;
+    const long long c = (long long)cb * kCellsPerBlock + tx;
+    const bool cin = c < P.N;
+    const long long cc = cin ? c : 0;
+    // everything this block reads is independent of everything else it reads:
+    // issue the loads together (the stop flag, the cell's region, the old
+    // value, both band slots' partial sets) before any of them is used
+    const int stop = P.ignore_done ? 0 : *((volatile int *)P.done);
+    const int it_prev = (threadIdx.x == 0) ? *P.iter : 0;  // only the last block's lane 0 uses it
+    const int r = cin ? (P.cell[cc].y & kRegionMask) : 0;
+    const double x_old = (ty == 0) ? P.x_in[cc] : 0.0;
+    const int b0 = ty, b1 = ty + kBandSlots;
+    const real *pp0 = P.part + (long long)b0 * P.Spad * P.N + cc;
+    const real *pp1 = P.part + (long long)b1 * P.Spad * P.N + cc;
+    real s0 = real(0), s1 = real(0);
+    for (int s = 0; s < P.S; s += 8) {
+        real a0[8], a1[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const bool in_s = s + q < P.S;
+            a0[q] = (in_s && b0 < P.B) ? __ldcg(pp0 + (long long)(s + q) * P.N) : real(0);
+            a1[q] = (in_s && b1 < P.B) ? __ldcg(pp1 + (long long)(s + q) * P.N) : real(0);
+        }
+        s0 += ((a0[0] + a0[1]) + (a0[2] + a0[3])) + ((a0[4] + a0[5]) + (a0[6] + a0[7]));
+        s1 += ((a1[0] + a1[1]) + (a1[2] + a1[3])) + ((a1[4] + a1[5]) + (a1[6] + a1[7]));
+    }
+    if (stop) return;  // converged earlier: this replayed iteration does nothing
+    double acc = 0.0;
+    if (r != 0) {
+        const double *wr = P.wgt + (r - 1) * P.B;
+        if (b0 < P.B) acc += (double)s0 * wr[b0];
+        if (b1 < P.B) acc += (double)s1 * wr[b1];
+        for (int b = ty + 2 * kBandSlots; b < P.B; b += kBandSlots) {
+            const real *pp = P.part + (long long)b * P.Spad * P.N + c;
+            acc += (double)sum_sets(pp, P.S, P.N) * wr[b];
+        }
+    }
+    sband[ty][tx] = acc;
+    __syncthreads();
+    if (ty != 0) return;
+    double ss = 0.0, mx = -INFINITY;
+    if (cin) {
+        if (r != 0) {
+            double tot = 0.0;
+#pragma unroll
+            for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
+            double xn;
+            if (!P.adjoint) {
+                const double dev = tot * P.Kinv[r - 1];
+                xn = P.T_ref + dev;
+                P.xdev_out[c] = (real)dev;
+                mx = xn;
+            } else {
+                xn = (P.g[c] + tot) * P.Kinv[r - 1];
+                P.xdev_out[c] = (real)xn;
+                mx = fabs(xn);
+            }
+            const double d = xn - x_old;
+            ss = d * d;
+            if (!isfinite(xn)) ss = NAN;
+            P.x_out[c] = xn;
+        } else {
+            P.x_out[c] = 0.0;
+            P.xdev_out[c] = (real)0;
+        }
+    }
+    warp_reduce2(ss, mx);
+    if (tx == 0) {
+        P.blockpart[2 * cb] = ss;
+        P.blockpart[2 * cb + 1] = mx;
         __threadfence();
         const unsigned ticket = atomicAdd(P.counter, 1u);
-        is_last = (ticket == gridDim.x - 1);
+        is_last = (ticket == (unsigned)cell_blocks - 1);
     }
-    __syncthreads();
+    __syncwarp();
     if (!is_last) return;
     __threadfence();
-    // last block: every thread sums a fixed, strided slice of the block
-    // partials, then a fixed reduction tree -> deterministic result
+    // last cell block, warp 0: every lane sums a fixed, strided slice of the
+    // block partials (loads issued sixteen at a time, summed in slice order),
+    // then the fixed shuffle tree -> deterministic result
     double tss = 0.0, tmx = -INFINITY;
-    for (int i = threadIdx.x; i < cell_blocks; i += blockDim.x) {
-        tss += __ldcg(&P.blockpart[2 * i]);
-        tmx = fmax(tmx, __ldcg(&P.blockpart[2 * i + 1]));
+    for (int i0 = tx; i0 < cell_blocks; i0 += 32 * 16) {
+        double2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int i = i0 + 32 * q;
+            v[q] = i < cell_blocks ? __ldcg(reinterpret_cast<const double2 *>(P.blockpart) + i)
+                                   : make_double2(0.0, -INFINITY);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            tss += v[q].x;
+            tmx = fmax(tmx, v[q].y);
+        }
     }
-    __syncthreads();
-    block_reduce2(tss, tmx, sh);
-    if (threadIdx.x == 0) {
+    warp_reduce2(tss, tmx);
+    if (tx == 0) {
         *P.counter = 0u;
         const double eps = (tmx > 0.0) ? sqrt(tss / (double)P.n_active) / tmx : 0.0;
-        const int it = *P.iter;
+        const int it = it_prev;
         if (P.eps_hist && it < P.max_hist) P.eps_hist[it] = eps;
         P.last[0] = eps;
         P.last[1] = tmx;
@@ -186,7 +236,7 @@ cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st) {
     const int cell_blocks = (int)((p.N + kCellsPerBlock - 1) / kCellsPerBlock);
     const long long fb = (long long)p.F * p.B;
     const int face_blocks = (int)((fb + kUpdThreads - 1) / kUpdThreads);
-    update_kernel<real><<<cell_blocks + face_blocks, kUpdThreads, 0, st>>>(p, cell_blocks);
+    update_kernel<real><<<face_blocks + cell_blocks, kUpdThreads, 0, st>>>(p, face_blocks, cell_blocks);
     return cudaGetLastError();
 }
 
