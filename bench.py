@@ -100,12 +100,36 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
 # since the capture has no entry)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/sweep2dp_square128.md: 177.9 KB read + 0.8 KB written (128 x 128 square, tile 3:4:4)
+    ("sweep2dp_kernel<float, 4, 8, 0, 0>", "3:4:4"): 178688,
+}
+
+
+def measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) measured on this GPU pool, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured: MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback: 6.8 TB/s"
+
+
+def timed_sweep_scale(stats):
+    """Timed sweeps are a sample (one in TIME_EVERY per poll interval): the
+    factor from the sampled sweep time to all sweeps of these solves."""
+    timed = sum(s["sweep_launches"] for s in stats)
+    total = sum(s["iterations"] for s in stats)
+    return total / timed if timed else 0.0
 
 
 def sweep_kernel_name(p, st):
-    """The forward sweep kernel a solve ran, as ncu names it."""
+    """The sweep kernel a solve ran (forward and adjoint share it), as ncu
+    names it."""
     dw = st["dirs_per_lane"]
+    if st["tile_kind"] == 3:
+        return f"sweep2dp_kernel<float, {dw}, 8, 0, 0>"
     if st["tile_kind"] == 2:
         rb = next(r for r in (1, 2, 3, 4, 5) if 32 * r >= p.n[1])
         return f"sweep2d_kernel<float, {dw}, {rb}, false>"
@@ -169,6 +193,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--store-e-every-iter", action="store_true")
+    ap.add_argument("--tile", default="0:0:0",
+                    help="sweep tile kind:dirs_per_lane:dirs_per_cta (0:0:0 = autotuned); profiling runs pin "
+                         "the tile the autotuner chose, since timings under a profiler are not representative")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -208,9 +235,12 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     per_update = p.n_active * p.B * p.D
 
+    tile_kind, tile_dw, tile_cw = (int(x) for x in args.tile.split(":"))
+
     def step(T, g):
         rc, sf = plan.solve(T, precision=m.BTE_FP32, tol=TOL, max_iter=100000, stream=sp,
-                            store_e_every_iter=args.store_e_every_iter)
+                            store_e_every_iter=args.store_e_every_iter, tile_kind=tile_kind,
+                            dirs_per_lane=tile_dw, dirs_per_cta=tile_cw)
         g.zero_()
         g[probes_d] = T[probes_d] - T_obs_d
         rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g, tol=TOL, max_iter=100000)
@@ -268,30 +298,43 @@ def main():
     dT_fp64 = float((T - T64).abs().max() / T64.abs().max())
 
     plan.set_sweep_timing(0)
-    # dominant kernel: the forward sweep, its mean launch duration from the
-    # CUDA events of the timed steps
+    # dominant kernel: the sweep (forward and adjoint launches of the same
+    # kernel), its mean launch duration from the CUDA events of the timed steps
     fwd_sweep_s = sum(f["sweep_seconds"] for f in fstats)
     fwd_sweeps = sum(f["sweep_launches"] for f in fstats)
     adj_sweep_s = sum(a["sweep_seconds"] for a in astats)
     adj_sweeps = sum(a["sweep_launches"] for a in astats)
-    sweep_ms = fwd_sweep_s / fwd_sweeps * 1e3
+    sweep_ms = (fwd_sweep_s + adj_sweep_s) / (fwd_sweeps + adj_sweeps) * 1e3
     dw = fstats[-1]["dirs_per_lane"]
     kernel = sweep_kernel_name(p, fstats[-1])
-    flops_per_update = 7.0   # 3 FMA + 1 MUL per cell x band x direction (Eq. 3 upwind update + weighted sum)
-    sweep_flops = flops_per_update * per_update
+    # algorithmic HBM bytes per cell x band x direction update: one FP32
+    # write of e, plus per cell the T read (8 B) and S, q writes (32 B)
+    # shared by its B x D updates
+    bytes_per_update = 4.0 + 40.0 / (p.B * p.D)
+    sweep_bytes = bytes_per_update * per_update
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    peak_hbm, peak_src = measured_hbm_peak()
+    tile = f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}"
+    traffic = NCU_TRAFFIC.get((kernel, tile))
+    flops_per_update = 7.0   # 3 FMA + 1 MUL per update (upwind update + weighted sum)
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     smax = 2070.0
-    peak_fp32 = sm_count * 128 * 2 * smax * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes at max clock
-    achieved = sweep_flops / (sweep_ms * 1e-3) / 1e12
-    traffic = NCU_TRAFFIC.get(kernel)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp32, "traffic": traffic,
-                "kernel": kernel,
-                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (max SM clock)",
-                "algorithmic": f"{flops_per_update:g} flop x {per_update} cell*band*direction updates per launch",
-                "sweep_ms": sweep_ms, "sweep_launches_timed": fwd_sweeps,
+    peak_fp32 = sm_count * 128 * 2 * smax * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes at max SM clock
+    alu_achieved = flops_per_update * per_update / (sweep_ms * 1e-3) / 1e12
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved / peak_hbm, "traffic": traffic,
+                "kernel": kernel, "tile": tile, "peak_source": peak_src,
+                "algorithmic": f"{bytes_per_update:.4f} B x {per_update} cell*band*direction updates per launch "
+                               f"(e write per update + per-cell T, S, q); the kernel itself keeps e on chip "
+                               f"(e is regenerated once after convergence), so DRAM traffic is far lower",
+                "sweep_ms": sweep_ms, "sweep_launches_timed": fwd_sweeps + adj_sweeps,
+                "fwd_sweep_ms": fwd_sweep_s / max(fwd_sweeps, 1) * 1e3,
                 "adj_sweep_ms": adj_sweep_s / max(adj_sweeps, 1) * 1e3,
-                "sweep_share_of_step": (fwd_sweep_s + adj_sweep_s) / t_total}
+                "sweep_share_of_step": (fwd_sweep_s * timed_sweep_scale(fstats) +
+                                        adj_sweep_s * timed_sweep_scale(astats)) / t_total,
+                "alu": {"achieved": alu_achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                        "frac": alu_achieved / peak_fp32,
+                        "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz"}}
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     T_init_h = torch.full((p.n_cells,), 300.0, dtype=torch.float64).pin_memory()
@@ -301,7 +344,8 @@ def main():
     for i in range(max(2, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rc, sf = plan.solve(T_h, T_init=T_init_h, precision=m.BTE_FP32, tol=TOL, max_iter=100000, stream=sp)
+        rc, sf = plan.solve(T_h, T_init=T_init_h, precision=m.BTE_FP32, tol=TOL, max_iter=100000, stream=sp,
+                            tile_kind=tile_kind, dirs_per_lane=tile_dw, dirs_per_cta=tile_cw)
         g_h.zero_()
         g_h[probes] = T_h[probes] - torch.as_tensor(T_obs)
         rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g_h, tol=TOL, max_iter=100000)
@@ -319,7 +363,8 @@ def main():
             "config": {"workload": WORKLOAD, "cells": p.n_cells, "bands": p.B, "directions": p.D,
                        "tol_eps_T": TOL, "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)",
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "store_e_every_iter": bool(args.store_e_every_iter), "dirs_per_lane": dw},
+                       "store_e_every_iter": bool(args.store_e_every_iter),
+                       "tile": f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}"},
             "fwd_iterations": fstats[-1]["iterations"], "adj_iterations": astats[-1]["iterations"],
             "fwd_time_to_converge_ms": fwd_ms, "fwd_updates_per_s": fwd_ups,
             "fwd_adj_ms_per_step": statistics.median(times),
