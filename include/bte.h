@@ -214,6 +214,50 @@ int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep);
  */
 int bte_set_sweep_timing(bte_plan *p, int every);
 
+/*
+ * Batched solves (the paper has none; many independent 2D problems on one
+ * GPU).  A batch borrows N plans made by bte_create -- unmasked 1D/2D grids
+ * with one region, all with the same band and direction counts, any sizes --
+ * and solves all of them together: every outer iteration is one graph node
+ * per size class (instances grouped by their number of 32-row blocks; the
+ * classes run concurrently) plus one update launch over every instance, and
+ * the iterations are replayed from a captured CUDA graph.  Each instance
+ * keeps its own convergence test (eps_T < tol) and stops iterating when it
+ * converges; the solve ends when all have converged or after max_iter.
+ * Results are those of bte_solve on each plan with the same tile.
+ *
+ * bte_batch_create -- n >= 1 distinct plans (the batch keeps the pointers;
+ *   destroy the batch before the plans).  BTE_EINVAL for null or mismatched
+ *   plans, BTE_ECUDA if device state cannot be allocated; the message is
+ *   read with bte_batch_last_error(NULL).
+ * bte_batch_solve -- o: as for bte_solve, except that T_init must be NULL
+ *   (T_init_uniform applies to all), T_wall must be NULL (each plan's walls
+ *   apply), and tile_kind is 0 or 3 (the row-pipeline kernel; the tile is
+ *   autotuned per size class unless dirs_per_lane / dirs_per_cta pin it).
+ *   T_out: sum of the instances' cell counts doubles (host or device), the
+ *   instances' temperatures concatenated in plan order.  st: n entries or
+ *   NULL.  bs: batch totals or NULL.  Returns BTE_OK, BTE_EINVAL,
+ *   BTE_ENOTCONVERGED (T_out still written), BTE_ENUMERIC, BTE_ETIMEOUT,
+ *   BTE_ECUDA.  The plans hold no adjoint-ready state afterwards.
+ */
+typedef struct bte_batch bte_batch; /* opaque, library-owned */
+
+typedef struct {
+    int instances;           /* n */
+    int converged;           /* instances that reached eps_T < tol */
+    int max_iterations;      /* largest per-instance iteration count */
+    double seconds;          /* device time of the iteration loop */
+    double updates;          /* sum over instances of iterations * cells * B * D */
+    double updates_per_s;    /* updates / seconds */
+    long long kernel_launches; /* kernels launched by the iteration loop */
+    int classes;             /* size classes (concurrent sweep launches per iteration) */
+} bte_batch_stats;
+
+int bte_batch_create(int n, bte_plan *const *plans, bte_batch **out);
+int bte_batch_solve(bte_batch *b, const bte_solve_opts *o, double *T_out, bte_stats *st, bte_batch_stats *bs);
+void bte_batch_destroy(bte_batch *b);
+const char *bte_batch_last_error(const bte_batch *b);
+
 /* Copy the eps_T history of the last bte_solve (one value per iteration,
  * at most n, the first 65536 iterations) into out (host).  Returns the
  * number of values copied or a negative code. */

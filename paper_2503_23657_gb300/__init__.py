@@ -6,6 +6,6 @@ include/bte.h); ``binding`` marshals arguments to it and ``autograd`` wraps
 solve + adjoint in a ``torch.autograd.Function``.  Nothing here computes on
 the CPU.
 """
-from .binding import Plan, BTEError, load, BTE_FP32, BTE_FP64  # noqa: F401
+from .binding import Batch, Plan, BTEError, load, BTE_FP32, BTE_FP64  # noqa: F401
 
-__all__ = ["Plan", "BTEError", "load", "BTE_FP32", "BTE_FP64"]
+__all__ = ["Batch", "Plan", "BTEError", "load", "BTE_FP32", "BTE_FP64"]

@@ -34,7 +34,8 @@ ERROR_NAMES = {
 # every entry point declared in include/bte.h
 EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_error",
            "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep",
-           "bte_set_sweep_timing", "bte_eps_T_noalloc"]
+           "bte_set_sweep_timing", "bte_eps_T_noalloc", "bte_batch_create", "bte_batch_solve",
+           "bte_batch_destroy", "bte_batch_last_error"]
 
 
 class Grid(ctypes.Structure):
@@ -78,6 +79,15 @@ class Stats(ctypes.Structure):
 _lib = None
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int), ("converged", ctypes.c_int), ("max_iterations", ctypes.c_int),
+                ("seconds", ctypes.c_double), ("updates", ctypes.c_double), ("updates_per_s", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("classes", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 def load(path: str = LIB_PATH):
     """Load libbte.so (built in-tree by ``paper_2503_23657_gb300.build``)."""
     global _lib
@@ -108,6 +118,14 @@ def load(path: str = LIB_PATH):
     lib.bte_profile_sweep.restype = ip
     lib.bte_set_sweep_timing.argtypes = [vp, ip]
     lib.bte_set_sweep_timing.restype = ip
+    lib.bte_batch_create.argtypes = [ip, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.bte_batch_create.restype = ip
+    lib.bte_batch_solve.argtypes = [vp, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(BatchStats)]
+    lib.bte_batch_solve.restype = ip
+    lib.bte_batch_destroy.argtypes = [vp]
+    lib.bte_batch_destroy.restype = None
+    lib.bte_batch_last_error.argtypes = [vp]
+    lib.bte_batch_last_error.restype = ctypes.c_char_p
     lib.bte_eps_T_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp]
     lib.bte_eps_T_noalloc.restype = ip
     _lib = lib
@@ -262,3 +280,62 @@ class Plan:
         if m < 0:
             raise BTEError(m, "eps history")
         return out[:m]
+
+
+class Batch:
+    """A batch of 2D plans solved together (bte_batch_create / bte_batch_solve).
+    The plans must outlive the batch."""
+
+    def __init__(self, plans):
+        lib = load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[pl._h for pl in self.plans])
+        out = ctypes.c_void_p()
+        rc = lib.bte_batch_create(len(self.plans), arr, ctypes.byref(out))
+        if rc != BTE_OK:
+            raise BTEError(rc, lib.bte_batch_last_error(None).decode())
+        self._h = out.value
+        self._lib = lib
+        self.n_cells = [pl.problem.n_cells for pl in self.plans]
+        self.offsets = np.concatenate([[0], np.cumsum(self.n_cells)]).astype(np.int64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bte_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self) -> str:
+        return self._lib.bte_batch_last_error(self._h).decode()
+
+    def solve(self, T_out, precision=BTE_FP32, tol=1e-6, max_iter=100000, T_init_uniform=300.0, Q_amp=0.0,
+              tau=None, stream=None, poll_every=32, dirs_per_lane=0, dirs_per_cta=0, check=True):
+        """Run bte_batch_solve.  T_out holds sum(n_cells) doubles (numpy or
+        torch, host or CUDA), instances concatenated in plan order.  Returns
+        (rc, [per-instance stats], batch stats)."""
+        o = SolveOpts()
+        self._lib.bte_default_opts(ctypes.byref(o))
+        o.precision = precision
+        o.tol = tol
+        o.max_iter = max_iter
+        o.T_init_uniform = T_init_uniform
+        o.Q_amp = Q_amp
+        tau_a = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
+        o.tau = _addr(tau_a)
+        o.stream = stream
+        o.poll_every = poll_every
+        o.dirs_per_lane = dirs_per_lane
+        o.dirs_per_cta = dirs_per_cta
+        o.tile_kind = 0
+        st = (Stats * len(self.plans))()
+        bs = BatchStats()
+        rc = self._lib.bte_batch_solve(self._h, ctypes.byref(o), _addr(T_out), ctypes.cast(st, ctypes.c_void_p),
+                                       ctypes.byref(bs))
+        if check and rc != BTE_OK:
+            raise BTEError(rc, self.error())
+        return rc, [s.as_dict() for s in st], bs.as_dict()

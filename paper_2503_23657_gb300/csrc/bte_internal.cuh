@@ -101,7 +101,19 @@ size_t sweep2d_smem(int nx, int ny, int stage, int with_phi, int warps, int rb, 
 // Row-pipeline 2D kernel (groups of DW directions, one warp per 32 rows).
 template <typename real>
 cudaError_t launch_sweep2dp(const Sweep2DParams<real> &p, int dirs_per_warp, cudaStream_t st);
-size_t sweep2dp_smem(int nx, int ny, int with_phi, int groups, int dw, int real_bytes);
+// A batched row-pipeline launch over the instances of one size class (same
+// row-block count, groups and direction chunks).
+template <typename real>
+struct Sweep2DBatch {
+    const Sweep2DParams<real> *params;  // device [all instances]
+    const int *inst;                    // device [n_inst] instance indices of this class
+    int n_inst, chunks, B, groups, nrb, nx_max, ny_max;
+    int phi;                            // any instance with a source profile (forward)
+    int stage;                          // per-cell source staged in shared memory (else read ahead)
+};
+template <typename real>
+cudaError_t launch_sweep2dp_batch(const Sweep2DBatch<real> &bt, int dirs_per_warp, cudaStream_t st);
+size_t sweep2dp_smem(int nx, int ny, int with_phi, int groups, int dw, int stage, int real_bytes);
 
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.
 template <typename real>
@@ -141,6 +153,7 @@ struct UpdateParams {
     long long n_active;
     int max_hist;
     int ignore_done;                  // final replay passes
+    int *batch_done;                  // batched solves: instances converged so far (or null)
 };
 
 // Launchers (sweep_*.cu / update.cu).  launch_sweep returns
@@ -155,6 +168,10 @@ int sweep_max_threads(int dirs_per_lane, int layers_per_lane, bool three_d);
 
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st);
+// batched update: table[i] = {instance, block of that instance}, `blocks` entries
+template <typename real>
+cudaError_t launch_update_batch(const UpdateParams<real> *params, const int2 *table, int blocks, cudaStream_t st);
+int update_blocks(long long N, int F, int B);  // blocks of one instance's update launch
 
 template <typename real>
 cudaError_t launch_flux(long long N, int B, int D, const int2 *cell, const real *e,

@@ -148,6 +148,48 @@ struct bte_plan {
 };
 
 namespace {
+// Device state of a batched solve in one precision.
+template <typename real>
+struct BatchState {
+    DevBuf sweep[2], update[2];  // Sweep2DParams<real>[n], UpdateParams<real>[n] per parity
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int> graph_key;
+    std::map<std::vector<int>, std::vector<int>> tuned;  // tile request -> tile per class
+    ~BatchState() {
+        if (graph) cudaGraphExecDestroy(graph);
+    }
+};
+}  // namespace
+
+// A batch of 2D instances solved together (one graph of batched launches).
+struct bte_batch {
+    std::vector<bte_plan *> plans;  // borrowed
+    int n = 0;
+    struct Cls {
+        int nrb, begin, count, nx_max, ny_max;
+    };
+    std::vector<Cls> classes;       // instances with the same 32-row block count
+    std::vector<int> inst;          // instance indices, class by class, largest first
+    DevBuf d_inst, d_table, d_status, d_done;
+    int upd_blocks = 0;
+    int *h_done = nullptr;          // pinned
+    std::vector<cudaStream_t> side; // one capture stream per class
+    std::vector<cudaEvent_t> join;  // one per class
+    cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
+    BatchState<float> bs32;
+    BatchState<double> bs64;
+    std::string err;
+    ~bte_batch() {
+        if (h_done) cudaFreeHost(h_done);
+        for (cudaStream_t s : side) cudaStreamDestroy(s);
+        for (cudaEvent_t e : join) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+namespace {
 
 int fail(bte_plan *p, int code, const std::string &msg) {
     if (p)
@@ -188,15 +230,18 @@ long long cell_index(const bte_plan *p, int i, int j, int k) { return i + (long 
 // A sweep tile: kernel kind (0 = general wavefront kernel, 1 = row-block 2D
 // kernel with one partial set per warp, 2 = row-block 2D kernel combining its
 // warps' per-cell sums through shared-memory slices, 3 = row-pipeline 2D
-// kernel with one partial set per direction group), directions per lane/warp
-// (dw) and directions per CTA chunk (cw).
+// kernel with one partial set per direction group and the per-cell source
+// staged in shared memory, 4 = the same kernel reading the source ahead from
+// global memory), directions per lane/warp (dw) and directions per CTA chunk
+// (cw).
 struct Tile {
     int kind, dw, cw;
 };
 inline int tile_id(int kind, int dw, int cw) { return kind * 100000 + cw * 100 + dw; }
 inline Tile tile_of(int id) { return Tile{id / 100000, id % 100, (id / 100) % 1000}; }
 // the bte_solve_opts.tile_kind value of an internal kernel kind
-inline int abi_kind(int kind) { return kind == 0 ? 1 : (kind == 3 ? 3 : 2); }
+inline int abi_kind(int kind) { return kind == 0 ? 1 : (kind >= 3 ? 3 : 2); }
+inline bool is_rowpipe(int kind) { return kind == 3 || kind == 4; }
 
 // Directions of one orientation group split into subsets of at most dw.
 std::vector<Subset> make_subsets(const bte_plan *p, int dw, bool flip) {
@@ -246,13 +291,13 @@ bool rowblock_ok(const bte_plan *p, int real_bytes, int *stage, int warps = 1, i
 
 // Row-pipeline 2D kernel: unmasked 1D/2D grid with one region, `groups`
 // groups of ceil(ny / 32) warps per CTA (at most 16 warps), shared memory fits.
-bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw) {
+bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw, int stage = 1) {
     if (p->dim > 2 || p->n_active != p->N) return false;
     const int nrb = (p->ny + 31) / 32;
     if (groups < 1 || groups * nrb > 16) return false;
     for (long long c = 0; c < p->N; ++c)
         if (p->mask[c] != 1) return false;
-    return sweep2dp_smem(p->nx, p->ny, p->phi.empty() ? 0 : 1, groups, dw, real_bytes) <= 200 * 1024;
+    return sweep2dp_smem(p->nx, p->ny, p->phi.empty() ? 0 : 1, groups, dw, stage, real_bytes) <= 200 * 1024;
 }
 
 // Candidate tiles for a precision; kind_req 0 = any, 1 = general only,
@@ -274,13 +319,15 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
     int gmax = 0;
     for (int c : p->groups_cnt) gmax = std::max(gmax, c);
     if (kind_req == 0 || kind_req == 3) {
-        for (int dw : {1, 2, 4}) {
-            if (dw_req && dw != dw_req) continue;
-            for (int groups : {1, 2, 4, 8, 16}) {
-                if (groups > 1 && dw * groups > gmax) break;
-                if (cw_req && dw * groups != cw_req) continue;
-                if (!rowpipe_ok(p, real_bytes, groups, dw)) continue;
-                out.push_back(tile_id(3, dw, dw * groups));
+        for (int stage : {1, 0}) {
+            for (int dw : {1, 2, 4}) {
+                if (dw_req && dw != dw_req) continue;
+                for (int groups : {1, 2, 4, 8, 16}) {
+                    if (groups > 1 && dw * groups > gmax) break;
+                    if (cw_req && dw * groups != cw_req) continue;
+                    if (!rowpipe_ok(p, real_bytes, groups, dw, stage)) continue;
+                    out.push_back(tile_id(stage ? 3 : 4, dw, dw * groups));
+                }
             }
         }
     }
@@ -339,7 +386,7 @@ int max_subsets(const bte_plan *p) {
 // Cell partial sets a tile writes (direct row-block tiles: one per warp).
 int cell_sets(int tid, int chunks) {
     const Tile tl = tile_of(tid);
-    return (tl.kind == 1 || tl.kind == 3) ? chunks * (tl.cw / tl.dw) : chunks;
+    return (tl.kind == 1 || is_rowpipe(tl.kind)) ? chunks * (tl.cw / tl.dw) : chunks;
 }
 
 // Per-solve tables (depend on tau overrides, wall temperatures, Q_amp, T_ref).
@@ -544,10 +591,6 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
     sp.S = (int)ws.subsets.at(tid).first.size();
     sp.ring = tl.kind == 2 ? 1 : 0;
-    if (tl.kind == 3) {
-        sp.groups = tl.cw / tl.dw;
-        sp.warps_per_cta = sp.groups * ((p->ny + 31) / 32);
-    }
     sp.adj = adj ? 1 : 0;
     sp.Spad = (cell_sets(tid, sp.S) + 3) & ~3;
     sp.wall_face = ws.wall.template as<int>();
@@ -557,6 +600,11 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     int stage = 0;
     rowblock_ok(p, (int)sizeof(real), &stage, sp.warps_per_cta, sp.ring);
     sp.stage = stage;
+    if (is_rowpipe(tl.kind)) {
+        sp.groups = tl.cw / tl.dw;
+        sp.warps_per_cta = sp.groups * ((p->ny + 31) / 32);
+        sp.stage = tl.kind == 3 ? 1 : 0;
+    }
     return sp;
 }
 
@@ -572,7 +620,7 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
         sp.store_e = store_e ? 1 : 0;
         sp.e = ws.e.template as<real>();
         if (!use_done) sp.done = nullptr;
-        if (tl.kind == 3) return launch_sweep2dp<real>(sp, tl.dw, stream);
+        if (is_rowpipe(tl.kind)) return launch_sweep2dp<real>(sp, tl.dw, stream);
         return launch_sweep2d<real>(sp, tl.dw, rowblock_rb(p), adj, stream);
     }
     SweepParams<real> sp = sweep_params(p, ws, tid, adj);
@@ -1264,6 +1312,320 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
     return BTE_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// batched solves (many 2D instances, one graph of batched launches)
+// ---------------------------------------------------------------------------
+int bfail(bte_batch *bt, int code, const std::string &msg) {
+    if (bt)
+        bt->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+#define BCK(bt, expr)                                                                               \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess) {                                                                    \
+            return bfail(bt, _e == cudaErrorMemoryAllocation ? BTE_ENOMEM : BTE_ECUDA,              \
+                         std::string(#expr) + ": " + cudaGetErrorString(_e));                       \
+        }                                                                                           \
+    } while (0)
+
+template <typename real>
+BatchState<real> &bstate_of(bte_batch *bt);
+template <>
+BatchState<float> &bstate_of<float>(bte_batch *bt) { return bt->bs32; }
+template <>
+BatchState<double> &bstate_of<double>(bte_batch *bt) { return bt->bs64; }
+
+// Row-pipeline candidates valid for every instance of a class (its largest
+// instance needs the most shared memory).
+std::vector<int> batch_class_candidates(bte_batch *bt, const bte_batch::Cls &c, int real_bytes, int dw_req,
+                                        int cw_req) {
+    return tile_candidates(bt->plans[bt->inst[c.begin]], real_bytes, 3, dw_req, cw_req);
+}
+
+template <typename real>
+Sweep2DBatch<real> batch_launch_desc(bte_batch *bt, BatchState<real> &bs, const bte_batch::Cls &c, int tid,
+                                     int parity) {
+    const Tile tl = tile_of(tid);
+    const bte_plan *p0 = bt->plans[bt->inst[c.begin]];
+    Sweep2DBatch<real> d{};
+    d.params = bs.sweep[parity].template as<Sweep2DParams<real>>();
+    d.inst = bt->d_inst.as<int>() + c.begin;
+    d.n_inst = c.count;
+    d.chunks = (int)ws_of<real>(bt->plans[bt->inst[c.begin]]).subsets.at(tid).first.size();
+    d.B = p0->B;
+    d.groups = tl.cw / tl.dw;
+    d.nrb = c.nrb;
+    d.nx_max = c.nx_max;
+    d.ny_max = c.ny_max;
+    d.phi = 0;
+    d.stage = tl.kind == 3 ? 1 : 0;
+    for (int q = 0; q < c.count; ++q)
+        if (!bt->plans[bt->inst[c.begin + q]]->phi.empty()) d.phi = 1;
+    return d;
+}
+
+// Per-instance launch parameters of every class's tile, both parities.
+template <typename real>
+int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<int> &tiles, double tol) {
+    std::vector<Sweep2DParams<real>> sw((size_t)bt->n);
+    std::vector<UpdateParams<real>> up((size_t)bt->n);
+    Status *st_all = bt->d_status.as<Status>();
+    for (int par = 0; par < 2; ++par) {
+        for (size_t c = 0; c < bt->classes.size(); ++c) {
+            const bte_batch::Cls &cl = bt->classes[c];
+            for (int q = 0; q < cl.count; ++q) {
+                const int i = bt->inst[cl.begin + q];
+                bte_plan *p = bt->plans[i];
+                Workspace<real> &ws = ws_of<real>(p);
+                const int tid = tiles[c];
+                if (int rc = ensure_subsets(p, ws, tid)) return bfail(bt, rc, p->err);
+                Sweep2DParams<real> sp = sweep2d_params(p, ws, tid, false);
+                sp.tsrc = ws.tdev[par].template as<real>();
+                sp.ein = ws.ein[par].template as<real>();
+                sp.store_e = 0;
+                sp.e = nullptr;
+                sp.done = &st_all[i].done;
+                sp.status = &st_all[i].status;
+                sw[i] = sp;
+                UpdateParams<real> u = update_params(p, ws, tid, false, tol);
+                u.x_in = ws.T[par].template as<double>();
+                u.x_out = ws.T[par ^ 1].template as<double>();
+                u.xdev_out = ws.tdev[par ^ 1].template as<real>();
+                u.ein_out = ws.ein[par ^ 1].template as<real>();
+                u.done = &st_all[i].done;
+                u.iter = &st_all[i].iter;
+                u.status = &st_all[i].status;
+                u.last = st_all[i].last;
+                u.batch_done = bt->d_done.as<int>();
+                up[i] = u;
+            }
+        }
+        BCK(bt, bs.sweep[par].ensure(sizeof(Sweep2DParams<real>) * bt->n));
+        BCK(bt, bs.update[par].ensure(sizeof(UpdateParams<real>) * bt->n));
+        BCK(bt, cudaMemcpy(bs.sweep[par].p, sw.data(), sizeof(Sweep2DParams<real>) * bt->n, cudaMemcpyHostToDevice));
+        BCK(bt, cudaMemcpy(bs.update[par].p, up.data(), sizeof(UpdateParams<real>) * bt->n, cudaMemcpyHostToDevice));
+    }
+    return BTE_OK;
+}
+
+// One batched iteration: the class sweeps (concurrently on the side streams,
+// joined back into `stream`), then one update launch over every instance.
+template <typename real>
+cudaError_t batch_enqueue(bte_batch *bt, BatchState<real> &bs, const std::vector<int> &tiles, int parity,
+                          cudaStream_t stream) {
+    cudaError_t e = cudaEventRecord(bt->fork, stream);
+    for (size_t c = 0; c < bt->classes.size() && e == cudaSuccess; ++c) {
+        cudaStream_t s = bt->side[c];
+        e = cudaStreamWaitEvent(s, bt->fork, 0);
+        if (e == cudaSuccess)
+            e = launch_sweep2dp_batch<real>(batch_launch_desc(bt, bs, bt->classes[c], tiles[c], parity),
+                                           tile_of(tiles[c]).dw, s);
+        if (e == cudaSuccess) e = cudaEventRecord(bt->join[c], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, bt->join[c], 0);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_update_batch<real>(bs.update[parity].template as<UpdateParams<real>>(), bt->d_table.as<int2>(),
+                                     bt->upd_blocks, stream);
+}
+
+template <typename real>
+int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_stats *st, bte_batch_stats *bst) {
+    cudaStream_t stream = (cudaStream_t)o->stream;
+    BatchState<real> &bs = bstate_of<real>(bt);
+    if (o->T_wall) return bfail(bt, BTE_EINVAL, "bte_batch_solve: wall temperatures come from each instance's plan");
+    if (o->tile_kind != 0 && o->tile_kind != 3)
+        return bfail(bt, BTE_EINVAL, "bte_batch_solve: batched solves use the row-pipeline kernel (tile_kind 0 or 3)");
+    // per-instance state
+    for (int i = 0; i < bt->n; ++i) {
+        bte_plan *p = bt->plans[i];
+        Workspace<real> &ws = ws_of<real>(p);
+        if (int rc = ensure_workspace(p, ws)) return bfail(bt, rc, p->err);
+        p->cur_tau = p->tau;
+        if (o->tau) {
+            for (int b = 0; b < p->B; ++b)
+                if (!(o->tau[b] > 0.0) || !std::isfinite(o->tau[b])) return bfail(bt, BTE_EINVAL, "tau override must be > 0");
+            p->cur_tau.assign(o->tau, o->tau + p->B);
+        }
+        p->cur_Tw.assign(p->bc_T, p->bc_T + 6);
+        p->cur_Q = o->Q_amp;
+        if (int rc = begin_state(p, o, ws, stream)) return bfail(bt, rc, p->err);
+        if (int rc = upload_tables(p, ws)) return bfail(bt, rc, p->err);
+        p->solved = false;  // a batch solve leaves no adjoint-ready state in the plans
+    }
+    BCK(bt, cudaMemsetAsync(bt->d_status.p, 0, sizeof(Status) * bt->n, stream));
+    BCK(bt, cudaMemsetAsync(bt->d_done.p, 0, sizeof(int), stream));
+    const double tol = o->tol;
+    // tiles: per class, the caller's restriction, then the autotuned choice (cached)
+    const std::vector<int> req = {o->dirs_per_lane, o->dirs_per_cta};
+    std::vector<int> tiles;
+    if (bs.tuned.count(req)) {
+        tiles = bs.tuned[req];
+    } else {
+        for (size_t c = 0; c < bt->classes.size(); ++c) {
+            std::vector<int> cand = batch_class_candidates(bt, bt->classes[c], (int)sizeof(real), o->dirs_per_lane,
+                                                           o->dirs_per_cta);
+            if (cand.empty()) return bfail(bt, BTE_EINVAL, "no row-pipeline tile fits a size class of the batch");
+            tiles.push_back(cand[0]);
+        }
+        for (size_t c = 0; c < bt->classes.size(); ++c) {
+            std::vector<int> cand = batch_class_candidates(bt, bt->classes[c], (int)sizeof(real), o->dirs_per_lane,
+                                                           o->dirs_per_cta);
+            if (cand.size() == 1) continue;
+            float best = 1e30f;
+            for (int tid : cand) {
+                std::vector<int> trial = tiles;
+                trial[c] = tid;
+                if (int rc = batch_upload_params<real>(bt, bs, trial, 0.0)) return rc;
+                float tmin = 1e30f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    cudaEventRecord(bt->ev0, stream);
+                    cudaError_t e = launch_sweep2dp_batch<real>(batch_launch_desc(bt, bs, bt->classes[c], tid, 0),
+                                                                tile_of(tid).dw, stream);
+                    cudaEventRecord(bt->ev1, stream);
+                    cudaEventSynchronize(bt->ev1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, bt->ev0, bt->ev1);
+                    if (e != cudaSuccess) {
+                        cudaGetLastError();
+                        tmin = 1e30f;
+                        break;
+                    }
+                    if (rep >= 1) tmin = std::min(tmin, ms);
+                }
+                if (std::getenv("BTE_TUNE_VERBOSE"))
+                    std::fprintf(stderr, "bte batch tune: class nrb %d dw %d cw %d: %.4f ms\n", bt->classes[c].nrb,
+                                 tile_of(tid).dw, tile_of(tid).cw, tmin);
+                if (tmin < best) {
+                    best = tmin;
+                    tiles[c] = tid;
+                }
+            }
+        }
+        bs.tuned[req] = tiles;
+        // autotuning ran sweeps on the initial state: start again
+        for (int i = 0; i < bt->n; ++i) {
+            bte_plan *p = bt->plans[i];
+            if (int rc = begin_state(p, o, ws_of<real>(p), stream)) return bfail(bt, rc, p->err);
+        }
+        BCK(bt, cudaMemsetAsync(bt->d_status.p, 0, sizeof(Status) * bt->n, stream));
+        BCK(bt, cudaMemsetAsync(bt->d_done.p, 0, sizeof(int), stream));
+    }
+    if (int rc = batch_upload_params<real>(bt, bs, tiles, tol)) return rc;
+    int poll = o->poll_every > 0 ? o->poll_every : 32;
+    poll = std::max(2, poll + (poll & 1));
+    std::vector<int> key = tiles;
+    key.push_back(poll);
+    key.push_back((int)(tol * 1e15 > 2e9 ? 2e9 : tol * 1e15));
+    if (!bs.graph || bs.graph_key != key) {
+        if (bs.graph) {
+            cudaGraphExecDestroy(bs.graph);
+            bs.graph = nullptr;
+        }
+        // one batched iteration outside any capture sets the kernels'
+        // shared-memory attributes; then the state starts again
+        BCK(bt, batch_enqueue<real>(bt, bs, tiles, 0, stream));
+        for (int i = 0; i < bt->n; ++i) {
+            bte_plan *p = bt->plans[i];
+            if (int rc = begin_state(p, o, ws_of<real>(p), stream)) return bfail(bt, rc, p->err);
+        }
+        BCK(bt, cudaMemsetAsync(bt->d_status.p, 0, sizeof(Status) * bt->n, stream));
+        BCK(bt, cudaMemsetAsync(bt->d_done.p, 0, sizeof(int), stream));
+        cudaStream_t cs;
+        BCK(bt, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int i = 0; i < poll && ce == cudaSuccess; ++i) ce = batch_enqueue<real>(bt, bs, tiles, i & 1, cs);
+        cudaError_t ce2 = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess) return bfail(bt, BTE_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce));
+        if (ce2 != cudaSuccess) return bfail(bt, BTE_ECUDA, std::string("batch graph capture end: ") + cudaGetErrorString(ce2));
+        ce = cudaGraphInstantiate(&bs.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            bs.graph = nullptr;
+            return bfail(bt, BTE_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        bs.graph_key = key;
+    }
+    const int max_iter = o->max_iter;
+    int enq = 0;
+    long long launches = 0;
+    BCK(bt, cudaEventRecord(bt->ev0, stream));
+    while (enq < max_iter) {
+        const int k = std::min(poll, max_iter - enq);
+        if (k == poll) {
+            BCK(bt, cudaGraphLaunch(bs.graph, stream));
+        } else {
+            for (int i = 0; i < k; ++i) BCK(bt, batch_enqueue<real>(bt, bs, tiles, (enq + i) & 1, stream));
+        }
+        enq += k;
+        launches += (long long)k * (long long)(bt->classes.size() + 1);
+        BCK(bt, cudaMemcpyAsync(bt->h_done, bt->d_done.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        BCK(bt, cudaStreamSynchronize(stream));
+        if (*bt->h_done >= bt->n) break;
+    }
+    BCK(bt, cudaEventRecord(bt->ev1, stream));
+    BCK(bt, cudaEventSynchronize(bt->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, bt->ev0, bt->ev1);
+    std::vector<Status> hs((size_t)bt->n);
+    BCK(bt, cudaMemcpy(hs.data(), bt->d_status.p, sizeof(Status) * bt->n, cudaMemcpyDeviceToHost));
+    long long off = 0;
+    double updates = 0.0;
+    int n_conv = 0, max_it = 0, n_bad = 0;
+    for (int i = 0; i < bt->n; ++i) {
+        bte_plan *p = bt->plans[i];
+        Workspace<real> &ws = ws_of<real>(p);
+        const int it = hs[i].iter;
+        BCK(bt, cudaMemcpyAsync(T_out + off, ws.T[it & 1].p, sizeof(double) * p->N, cudaMemcpyDefault, stream));
+        off += p->N;
+        updates += (double)it * p->n_active * p->B * p->D;
+        const bool bad = hs[i].status != 0;
+        const bool conv = tol > 0.0 && hs[i].done && !bad;
+        n_conv += conv ? 1 : 0;
+        n_bad += bad ? 1 : 0;
+        max_it = std::max(max_it, it);
+        if (st) {
+            bte_stats &s = st[i];
+            std::memset(&s, 0, sizeof(s));
+            s.iterations = it;
+            s.converged = conv ? 1 : 0;
+            s.eps_T = hs[i].last[0];
+            s.T_max = hs[i].last[1];
+            s.seconds = ms * 1e-3;
+            const int ci = [&] {
+                for (size_t c = 0; c < bt->classes.size(); ++c)
+                    if (p->ny <= 32 * bt->classes[c].nrb && p->ny > 32 * (bt->classes[c].nrb - 1)) return (int)c;
+                return 0;
+            }();
+            s.dirs_per_lane = tile_of(tiles[ci]).dw;
+            s.dirs_per_cta = tile_of(tiles[ci]).cw;
+            s.tile_kind = 3;
+        }
+    }
+    BCK(bt, cudaStreamSynchronize(stream));
+    if (bst) {
+        std::memset(bst, 0, sizeof(*bst));
+        bst->instances = bt->n;
+        bst->converged = n_conv;
+        bst->max_iterations = max_it;
+        bst->seconds = ms * 1e-3;
+        bst->updates = updates;
+        bst->updates_per_s = ms > 0 ? updates / (ms * 1e-3) : 0.0;
+        bst->kernel_launches = launches;
+        bst->classes = (int)bt->classes.size();
+    }
+    for (int i = 0; i < bt->n; ++i)
+        if (hs[i].status == 2) return bfail(bt, BTE_ETIMEOUT, "a bounded device wait expired in a batched sweep");
+    if (n_bad) return bfail(bt, BTE_ENUMERIC, "NaN or Inf in the temperature update of an instance");
+    if (tol > 0.0 && n_conv < bt->n) return bfail(bt, BTE_ENOTCONVERGED, "max_iter reached before every instance converged");
+    return BTE_OK;
+}
 }  // namespace
 
 namespace bte {
@@ -1379,6 +1741,82 @@ int bte_eps_history(const bte_plan *p, double *out, int n) {
     if (m > 0 && cudaMemcpy(out, p->d_hist.p, sizeof(double) * m, cudaMemcpyDeviceToHost) != cudaSuccess) return BTE_ECUDA;
     return m;
 }
+
+int bte_batch_create(int n, bte_plan *const *plans, bte_batch **out) {
+    if (!out) return bfail(nullptr, BTE_EINVAL, "bte_batch_create: out is null");
+    *out = nullptr;
+    if (n < 1 || !plans) return bfail(nullptr, BTE_EINVAL, "bte_batch_create: n >= 1 plans required");
+    for (int i = 0; i < n; ++i) {
+        const bte_plan *p = plans[i];
+        if (!p) return bfail(nullptr, BTE_EINVAL, "bte_batch_create: null plan");
+        const bte_plan *q = plans[0];
+        if (p->B != q->B || p->D != q->D)
+            return bfail(nullptr, BTE_EINVAL, "bte_batch_create: every instance needs the same band and direction counts");
+        if (p->dim > 2 || p->n_active != p->N || p->R != 1 || (p->ny + 31) / 32 > 16)
+            return bfail(nullptr, BTE_EINVAL, "bte_batch_create: instances must be unmasked 1D/2D grids with one region");
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == p) return bfail(nullptr, BTE_EINVAL, "bte_batch_create: a plan appears twice");
+    }
+    std::unique_ptr<bte_batch> bt(new bte_batch());
+    bt->plans.assign(plans, plans + n);
+    bt->n = n;
+    // size classes by 32-row block count; inside a class, largest first
+    std::map<int, std::vector<int>> by;
+    for (int i = 0; i < n; ++i) by[(plans[i]->ny + 31) / 32].push_back(i);
+    for (auto &kv : by) {
+        std::vector<int> v = kv.second;
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return plans[a]->N > plans[b]->N; });
+        bte_batch::Cls c{kv.first, (int)bt->inst.size(), (int)v.size(), 0, 0};
+        for (int i : v) {
+            c.nx_max = std::max(c.nx_max, plans[i]->nx);
+            c.ny_max = std::max(c.ny_max, plans[i]->ny);
+            bt->inst.push_back(i);
+        }
+        bt->classes.push_back(c);
+    }
+    // update blocks: largest classes first
+    std::vector<int2> table;
+    for (int ci = (int)bt->classes.size() - 1; ci >= 0; --ci) {
+        const bte_batch::Cls &c = bt->classes[ci];
+        for (int q = 0; q < c.count; ++q) {
+            const int i = bt->inst[c.begin + q];
+            const int nb = update_blocks(plans[i]->N, plans[i]->F, plans[i]->B);
+            for (int k = 0; k < nb; ++k) table.push_back(make_int2(i, k));
+        }
+    }
+    bt->upd_blocks = (int)table.size();
+    if (cudaSuccess != upload(bt->d_inst, bt->inst) || cudaSuccess != upload(bt->d_table, table) ||
+        cudaSuccess != bt->d_status.ensure(sizeof(Status) * n) || cudaSuccess != bt->d_done.ensure(sizeof(int)) ||
+        cudaSuccess != cudaMallocHost(&bt->h_done, sizeof(int)) || cudaSuccess != cudaEventCreate(&bt->fork) ||
+        cudaSuccess != cudaEventCreate(&bt->ev0) || cudaSuccess != cudaEventCreate(&bt->ev1)) {
+        cudaGetLastError();
+        return bfail(nullptr, BTE_ECUDA, "bte_batch_create: device allocation failed");
+    }
+    for (size_t c = 0; c < bt->classes.size(); ++c) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaSuccess != cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) return bfail(nullptr, BTE_ECUDA, "stream");
+        bt->side.push_back(s);
+        if (cudaSuccess != cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return bfail(nullptr, BTE_ECUDA, "event");
+        bt->join.push_back(e);
+    }
+    *out = bt.release();
+    return BTE_OK;
+}
+
+int bte_batch_solve(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_stats *st, bte_batch_stats *bs) {
+    if (!bt) return bfail(nullptr, BTE_EINVAL, "batch is null");
+    if (!o || !T_out) return bfail(bt, BTE_EINVAL, "opts and T_out are required");
+    if (o->max_iter < 1) return bfail(bt, BTE_EINVAL, "max_iter must be >= 1");
+    if (o->T_init) return bfail(bt, BTE_EINVAL, "bte_batch_solve: use T_init_uniform");
+    if (o->precision == BTE_FP32) return batch_solve_t<float>(bt, o, T_out, st, bs);
+    if (o->precision == BTE_FP64) return batch_solve_t<double>(bt, o, T_out, st, bs);
+    return bfail(bt, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+}
+
+void bte_batch_destroy(bte_batch *bt) { delete bt; }
+
+const char *bte_batch_last_error(const bte_batch *bt) { return bt ? bt->err.c_str() : g_create_error.c_str(); }
 
 void bte_destroy(bte_plan *p) { delete p; }
 

@@ -63,9 +63,9 @@ __device__ __forceinline__ bool pipe_wait(const int *prog, int need, volatile in
 
 constexpr int kPipeMaxThreads = 512;
 
-template <typename real, int DW, int K, bool PHI, bool STORE_E>
-__global__ void __launch_bounds__(kPipeMaxThreads, 1)
-sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
+// One CTA's work: direction chunk s of band b of the problem P.
+template <typename real, int DW, int K, bool PHI, bool STORE_E, bool STAGE>
+__device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, const int s, const int b) {
     if (P.done != nullptr && *((volatile const int *)P.done) != 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
@@ -76,16 +76,16 @@ sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     const int G = P.groups;
     const int NRB = (ny + 31) / 32;
     const bool adj = P.adj != 0;
-    real *s_t = reinterpret_cast<real *>(smem_raw);               // [Npad] T - T_ref or Theta
-    real *s_phi = s_t + Npad;                                     // [Npad] source profile (forward)
-    real *s_hand = s_phi + (PHI ? Npad : 0);                      // [G][NRB+1][nx][DW] row values
+    // STAGE: the per-cell source is copied to shared memory; otherwise every
+    // lane reads its own row from global memory one chunk ahead
+    real *s_t = reinterpret_cast<real *>(smem_raw);               // [Npad] T - T_ref or Theta (STAGE)
+    real *s_phi = s_t + (STAGE ? Npad : 0);                       // [Npad] source profile (STAGE, forward)
+    real *s_hand = s_phi + ((STAGE && PHI) ? Npad : 0);           // [G][NRB+1][nx][DW] row values
     real *s_tiles = s_hand + (size_t)G * (NRB + 1) * nx * DW;     // [G*NRB][32][33] transpose tiles
     real *s_fs = s_tiles + (size_t)G * NRB * 32 * 33;             // [G][nx + ny] wall sums
     real *s_wx = s_fs + G * (nx + ny);                            // [ny] upwind x-wall values
     int *s_prog = reinterpret_cast<int *>(s_wx + ny);             // [G][NRB+1] published columns
 
-    const int s = blockIdx.x;  // chunk
-    const int b = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nthr = blockDim.x;
@@ -102,7 +102,7 @@ sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
         s_abort = 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (STAGE && threadIdx.x == 0) {
         const uint32_t bytes = (uint32_t)(Npad * sizeof(real));
         mbar_arrive_expect_tx(&s_bar, PHI ? 2 * bytes : bytes);
         bulk_copy_g2s(s_t, P.tsrc, bytes, &s_bar);
@@ -127,7 +127,7 @@ sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
         for (int q = threadIdx.x; q < G * (ny + nx); q += nthr) s_fs[q] = real(0);
         for (int q = threadIdx.x; q < G * (NRB + 1); q += nthr) s_prog[q] = (q % (NRB + 1) == 0) ? nx : 0;
     }
-    const bool ok = mbar_wait_bounded(&s_bar, 0, kWaitPolls);
+    const bool ok = STAGE ? mbar_wait_bounded(&s_bar, 0, kWaitPolls) : true;
     __syncthreads();
     if (!ok) {
         // the bulk copy did not complete: report, wait once more for it, stop
@@ -192,8 +192,32 @@ sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     }
 
     const int n_steps = (nx + 31 + 31) & ~31;  // whole tiles of 32 steps
+    // unstaged: the sources of the next chunk, loaded while this one runs
+    real pre_t[STAGE ? 1 : K], pre_p[(STAGE || !PHI) ? 1 : K];
+    if constexpr (!STAGE) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool v = (unsigned)(k - t_lo) < (unsigned)nx;
+            const int c = c_base + cstep * k;
+            pre_t[k] = v ? __ldg(P.tsrc + c) : real(0);
+            if constexpr (PHI) pre_p[k] = v ? __ldg(P.phi + c) : real(0);
+        }
+    }
     bool waited_ok = true;
     for (int t0 = 0; t0 < n_steps; t0 += K) {
+        real cur_t[STAGE ? 1 : K], cur_p[(STAGE || !PHI) ? 1 : K];
+        if constexpr (!STAGE) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                cur_t[k] = pre_t[k];
+                if constexpr (PHI) cur_p[k] = pre_p[k];
+                const int t = t0 + K + k;
+                const bool v = (unsigned)(t - t_lo) < (unsigned)nx;
+                const int c = c_base + cstep * t;
+                pre_t[k] = v ? __ldg(P.tsrc + c) : real(0);
+                if constexpr (PHI) pre_p[k] = v ? __ldg(P.phi + c) : real(0);
+            }
+        }
         if (waited_ok) {
             // columns [t0, t0 + K) of row 32 R - 1 (row -1: the wall) must be final
             waited_ok = pipe_wait(prog_in, min(t0 + K, nx), &s_abort);
@@ -208,9 +232,16 @@ sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
             const int i = t - t_lo;
             const bool valid = (unsigned)i < (unsigned)nx;
             const int c = c_base + cstep * t;
-            real base = valid ? s_t[c] : real(0);
+            real base, srcp = real(0);
+            if constexpr (STAGE) {
+                base = valid ? s_t[c] : real(0);
+                if constexpr (PHI) srcp = valid ? s_phi[c] : real(0);
+            } else {
+                base = cur_t[k];
+                if constexpr (PHI) srcp = cur_p[k];
+            }
             base *= srck;
-            if (PHI) base = fma(valid ? s_phi[c] : real(0), qb, base);
+            if (PHI) base = fma(srcp, qb, base);
             const bool take = (lane == 0) && valid;
             real vy[DW];
 #pragma unroll
@@ -289,24 +320,39 @@ sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     }
 }
 
+template <typename real, int DW, int K, bool PHI, bool STORE_E, bool STAGE>
+__global__ void __launch_bounds__(kPipeMaxThreads, 1)
+sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
+    sweep2dp_body<real, DW, K, PHI, STORE_E, STAGE>(P, blockIdx.x, blockIdx.y);
+}
+
+// Batched form: blockIdx.z picks the instance (through `inst`, which lists
+// the instances of one size class, largest first); every instance has its
+// own parameters, buffers and convergence flag.
+template <typename real, int DW, int K, bool PHI, bool STAGE>
+__global__ void __launch_bounds__(kPipeMaxThreads, 1)
+sweep2dp_batch_kernel(const Sweep2DParams<real> *__restrict__ params, const int *__restrict__ inst) {
+    sweep2dp_body<real, DW, K, PHI, false, STAGE>(params[inst[blockIdx.z]], blockIdx.x, blockIdx.y);
+}
+
 // Dynamic shared memory of the row-pipeline kernel (bytes).
 template <typename real>
-size_t sweep2dp_smem_bytes(int nx, int ny, int with_phi, int groups, int dw) {
+size_t sweep2dp_smem_bytes(int nx, int ny, int with_phi, int groups, int dw, int stage) {
     const size_t N = (size_t)nx * ny;
     const size_t Npad = (N + 15) & ~(size_t)15;
     const size_t nrb = (size_t)(ny + 31) / 32;
-    size_t n = Npad * (with_phi ? 2 : 1) + (size_t)groups * (nrb + 1) * nx * dw + (size_t)groups * nrb * 32 * 33 +
+    size_t n = (stage ? Npad * (with_phi ? 2 : 1) : 0) + (size_t)groups * (nrb + 1) * nx * dw + (size_t)groups * nrb * 32 * 33 +
                (size_t)groups * (nx + ny) + ny;
     return n * sizeof(real) + sizeof(int) * (size_t)groups * (nrb + 1);
 }
 
-template <typename real, int DW, int K, bool PHI, bool STORE_E>
+template <typename real, int DW, int K, bool PHI, bool STORE_E, bool STAGE>
 cudaError_t launch_sweep2dp_v(const Sweep2DParams<real> &p, cudaStream_t st) {
     const int nrb = (p.ny + 31) / 32;
     const int threads = p.groups * nrb * 32;
     if (p.groups < 1 || threads > kPipeMaxThreads) return cudaErrorInvalidConfiguration;
-    const size_t smem = sweep2dp_smem_bytes<real>(p.nx, p.ny, PHI ? 1 : 0, p.groups, DW);
-    auto kern = sweep2dp_kernel<real, DW, K, PHI, STORE_E>;
+    const size_t smem = sweep2dp_smem_bytes<real>(p.nx, p.ny, PHI ? 1 : 0, p.groups, DW, STAGE ? 1 : 0);
+    auto kern = sweep2dp_kernel<real, DW, K, PHI, STORE_E, STAGE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -315,12 +361,43 @@ cudaError_t launch_sweep2dp_v(const Sweep2DParams<real> &p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename real, int DW, int K, bool PHI, bool STAGE>
+cudaError_t launch_sweep2dp_batch_v(const Sweep2DBatch<real> &bt, cudaStream_t st) {
+    const int threads = bt.groups * bt.nrb * 32;
+    if (bt.groups < 1 || threads > kPipeMaxThreads || bt.n_inst < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = sweep2dp_smem_bytes<real>(bt.nx_max, bt.ny_max, PHI ? 1 : 0, bt.groups, DW, STAGE ? 1 : 0);
+    auto kern = sweep2dp_batch_kernel<real, DW, K, PHI, STAGE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<dim3(bt.chunks, bt.B, bt.n_inst), threads, smem, st>>>(bt.params, bt.inst);
+    return cudaGetLastError();
+}
+
+template <typename real, int DW, int K>
+cudaError_t launch_sweep2dp_batch_t(const Sweep2DBatch<real> &bt, cudaStream_t st) {
+    if (bt.stage)
+        return bt.phi ? launch_sweep2dp_batch_v<real, DW, K, true, true>(bt, st)
+                      : launch_sweep2dp_batch_v<real, DW, K, false, true>(bt, st);
+    return bt.phi ? launch_sweep2dp_batch_v<real, DW, K, true, false>(bt, st)
+                  : launch_sweep2dp_batch_v<real, DW, K, false, false>(bt, st);
+}
+
 // the source-profile term only in forward sweeps with a source; e only when asked
+template <typename real, int DW, int K, bool STAGE>
+cudaError_t launch_sweep2dp_s(const Sweep2DParams<real> &p, cudaStream_t st) {
+    const bool phi = !p.adj && p.phi != nullptr;
+    if (p.store_e)
+        return phi ? launch_sweep2dp_v<real, DW, K, true, true, STAGE>(p, st)
+                   : launch_sweep2dp_v<real, DW, K, false, true, STAGE>(p, st);
+    return phi ? launch_sweep2dp_v<real, DW, K, true, false, STAGE>(p, st)
+               : launch_sweep2dp_v<real, DW, K, false, false, STAGE>(p, st);
+}
+
 template <typename real, int DW, int K>
 cudaError_t launch_sweep2dp_t(const Sweep2DParams<real> &p, cudaStream_t st) {
-    const bool phi = !p.adj && p.phi != nullptr;
-    if (p.store_e) return phi ? launch_sweep2dp_v<real, DW, K, true, true>(p, st) : launch_sweep2dp_v<real, DW, K, false, true>(p, st);
-    return phi ? launch_sweep2dp_v<real, DW, K, true, false>(p, st) : launch_sweep2dp_v<real, DW, K, false, false>(p, st);
+    return p.stage ? launch_sweep2dp_s<real, DW, K, true>(p, st) : launch_sweep2dp_s<real, DW, K, false>(p, st);
 }
 
 }  // namespace bte

@@ -10,8 +10,16 @@ cudaError_t launch_sweep2dp<float>(const Sweep2DParams<float> &p, int dw, cudaSt
     return cudaErrorInvalidConfiguration;
 }
 
-size_t sweep2dp_smem(int nx, int ny, int with_phi, int groups, int dw, int real_bytes) {
-    return real_bytes == 4 ? sweep2dp_smem_bytes<float>(nx, ny, with_phi, groups, dw)
-                           : sweep2dp_smem_bytes<double>(nx, ny, with_phi, groups, dw);
+template <>
+cudaError_t launch_sweep2dp_batch<float>(const Sweep2DBatch<float> &bt, int dw, cudaStream_t st) {
+    if (dw == 1) return launch_sweep2dp_batch_t<float, 1, 8>(bt, st);
+    if (dw == 2) return launch_sweep2dp_batch_t<float, 2, 8>(bt, st);
+    if (dw == 4) return launch_sweep2dp_batch_t<float, 4, 8>(bt, st);
+    return cudaErrorInvalidConfiguration;
+}
+
+size_t sweep2dp_smem(int nx, int ny, int with_phi, int groups, int dw, int stage, int real_bytes) {
+    return real_bytes == 4 ? sweep2dp_smem_bytes<float>(nx, ny, with_phi, groups, dw, stage)
+                           : sweep2dp_smem_bytes<double>(nx, ny, with_phi, groups, dw, stage);
 }
 }  // namespace bte

@@ -83,14 +83,21 @@ __device__ __forceinline__ void warp_reduce2(double &a, double &m) {
 constexpr int kCellsPerBlock = 32;
 constexpr int kBandSlots = kUpdThreads / kCellsPerBlock;
 
+__host__ __device__ inline int update_cell_blocks(long long N) { return (int)((N + kCellsPerBlock - 1) / kCellsPerBlock); }
+__host__ __device__ inline int update_face_blocks(int F, int B) {
+    return (int)(((long long)F * B + kUpdThreads - 1) / kUpdThreads);
+}
+
+// Block `blk` of the update of problem P (face blocks, then cell blocks).
 template <typename real>
-__global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(const __grid_constant__ UpdateParams<real> P,
-                                                             int face_blocks, int cell_blocks) {
+__device__ __forceinline__ void update_body(const UpdateParams<real> &P, const int blk) {
     __shared__ double sband[kBandSlots][kCellsPerBlock];
     __shared__ int is_last;
-    if ((int)blockIdx.x < face_blocks) {
+    const int face_blocks = update_face_blocks(P.F, P.B);
+    const int cell_blocks = update_cell_blocks(P.N);
+    if (blk < face_blocks) {
         if (!P.ignore_done && *((volatile int *)P.done) != 0) return;
-        const long long fb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long fb = (long long)blk * kUpdThreads + threadIdx.x;
         if (fb < (long long)P.F * P.B) {
             const int b = (int)(fb / P.F);
             const int f = (int)(fb % P.F);
@@ -113,7 +120,7 @@ __global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(const __grid_con
         }
         return;
     }
-    const int cb = blockIdx.x - face_blocks;
+    const int cb = blk - face_blocks;
     const int tx = threadIdx.x % kCellsPerBlock;
     const int ty = threadIdx.x / kCellsPerBlock;
     const long long c = (long long)cb * kCellsPerBlock + tx;
@@ -221,24 +228,44 @@ __global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(const __grid_con
         P.last[2] = tss;
         if (!P.ignore_done) {
             *P.iter = it + 1;
-            if (!isfinite(eps)) {
-                *P.status = 1;
+            const bool stop_now = !isfinite(eps) || (P.tol > 0.0 && eps < P.tol);
+            if (!isfinite(eps)) *P.status = 1;
+            if (stop_now) {
                 *P.done = 1;
-            } else if (P.tol > 0.0 && eps < P.tol) {
-                *P.done = 1;
+                if (P.batch_done) atomicAdd(P.batch_done, 1);
             }
         }
     }
 }
 
 template <typename real>
+__global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(const __grid_constant__ UpdateParams<real> P) {
+    update_body<real>(P, blockIdx.x);
+}
+
+// Batched form: table[blockIdx.x] = {instance, block of that instance}.
+template <typename real>
+__global__ void __launch_bounds__(kUpdThreads, 4)
+update_batch_kernel(const UpdateParams<real> *__restrict__ params, const int2 *__restrict__ table) {
+    const int2 e = table[blockIdx.x];
+    update_body<real>(params[e.x], e.y);
+}
+
+template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st) {
-    const int cell_blocks = (int)((p.N + kCellsPerBlock - 1) / kCellsPerBlock);
-    const long long fb = (long long)p.F * p.B;
-    const int face_blocks = (int)((fb + kUpdThreads - 1) / kUpdThreads);
-    update_kernel<real><<<face_blocks + cell_blocks, kUpdThreads, 0, st>>>(p, face_blocks, cell_blocks);
+    const int blocks = update_face_blocks(p.F, p.B) + update_cell_blocks(p.N);
+    update_kernel<real><<<blocks, kUpdThreads, 0, st>>>(p);
     return cudaGetLastError();
 }
+
+template <typename real>
+cudaError_t launch_update_batch(const UpdateParams<real> *params, const int2 *table, int blocks, cudaStream_t st) {
+    if (blocks < 1) return cudaErrorInvalidConfiguration;
+    update_batch_kernel<real><<<blocks, kUpdThreads, 0, st>>>(params, table);
+    return cudaGetLastError();
+}
+
+int update_blocks(long long N, int F, int B) { return update_face_blocks(F, B) + update_cell_blocks(N); }
 
 // ---------------------------------------------------------------------------
 // heat flux q_c = sum_b v_b sum_d w_d s_d e_cbd (one warp per cell)
@@ -391,6 +418,8 @@ cudaError_t launch_grad(const GradParams<real> &g, cudaStream_t st) {
 
 template cudaError_t launch_update<float>(const UpdateParams<float> &, cudaStream_t);
 template cudaError_t launch_update<double>(const UpdateParams<double> &, cudaStream_t);
+template cudaError_t launch_update_batch<float>(const UpdateParams<float> *, const int2 *, int, cudaStream_t);
+template cudaError_t launch_update_batch<double>(const UpdateParams<double> *, const int2 *, int, cudaStream_t);
 template cudaError_t launch_flux<float>(long long, int, int, const int2 *, const float *, const double *,
                                         const double *, double *, cudaStream_t);
 template cudaError_t launch_flux<double>(long long, int, int, const int2 *, const double *, const double *,

@@ -1,0 +1,114 @@
+"""Batched solves (many uneven 2D instances in one graph of batched launches)
+against the FP64 oracle and against one-plan solves.
+
+A small ensemble of the batched-ensemble recipe (uneven squares, log-uniform
+sizes, per-instance wall temperature) spans three 32-row size classes; the
+oracle runs a fixed number of source iterations per instance.
+"""
+import numpy as np
+import pytest
+
+import bte_inputs as bi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bte():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_23657_gb300 as m
+    m.load()
+    return m
+
+
+def small_ensemble(n_instances=9, n_min=12, n_max=80, B=4):
+    probs = bi.ensemble_2d(n_instances=n_instances, n_min=n_min, n_max=n_max)
+    return [p.copy(C=p.C[:B], v=p.v[:B], tau=p.tau[:B]) for p in probs]
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.fixture(scope="module")
+def ensemble(bte):
+    probs = small_ensemble()
+    plans = [bte.Plan(p) for p in probs]
+    batch = bte.Batch(plans)
+    return probs, plans, batch
+
+
+def test_classes_span_row_blocks(ensemble):
+    probs, plans, batch = ensemble
+    nrb = {(p.n[1] + 31) // 32 for p in probs}
+    assert len(nrb) >= 3
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 1e-5)], ids=["fp64", "fp32"])
+def test_batch_fixed_iterations_vs_oracle(bte, ensemble, prec, tol):
+    probs, plans, batch = ensemble
+    k = 6
+    T = np.zeros(sum(p.n_cells for p in probs))
+    rc, st, bs = batch.solve(T, precision=prec, tol=0.0, max_iter=k)
+    assert bs["instances"] == len(probs) and bs["max_iterations"] == k
+    for i, p in enumerate(probs):
+        ref = oracle.solve(p, max_iter=k, tol=0.0)
+        Ti = T[batch.offsets[i]:batch.offsets[i + 1]]
+        assert st[i]["iterations"] == k
+        assert rel(Ti, ref["T"]) < tol, (i, p.name)
+
+
+def test_batch_equals_single_plan_solves(bte, ensemble):
+    """Same kernels, same tile: the batched FP32 result is bitwise the one-plan
+    result, per instance."""
+    probs, plans, batch = ensemble
+    k = 9
+    T = np.zeros(sum(p.n_cells for p in probs))
+    rc, st, bs = batch.solve(T, precision=0, tol=0.0, max_iter=k)
+    for i, (p, pl) in enumerate(zip(probs, plans)):
+        Ts = np.zeros(p.n_cells)
+        pl.solve(Ts, precision=0, tol=0.0, max_iter=k, tile_kind=3, dirs_per_lane=st[i]["dirs_per_lane"],
+                 dirs_per_cta=st[i]["dirs_per_cta"])
+        np.testing.assert_array_equal(T[batch.offsets[i]:batch.offsets[i + 1]], Ts)
+
+
+def test_batch_per_instance_convergence(bte):
+    """Each instance stops on its own eps_T test: iteration counts and T equal
+    the one-plan FP64 solves (bitwise), differ across the batch, and the
+    smallest instances match the oracle's converged runs."""
+    probs = [p.copy(C=p.C[:4], v=p.v[:4], tau=p.tau[:4])
+             for p in bi.ensemble_2d(n_instances=8, n_min=12, n_max=72, L_min=1e-7, L_max=1e-6)]
+    plans = [bte.Plan(p) for p in probs]
+    batch = bte.Batch(plans)
+    T = torch.zeros(sum(p.n_cells for p in probs), dtype=torch.float64, device="cuda")
+    rc, st, bs = batch.solve(T, precision=1, tol=1e-7, max_iter=100000)
+    assert bs["converged"] == len(probs)
+    its = [s["iterations"] for s in st]
+    assert len(set(its)) > 1 and bs["max_iterations"] == max(its)
+    Th = T.cpu().numpy()
+    for i, (p, pl) in enumerate(zip(probs, plans)):
+        Ts = np.zeros(p.n_cells)
+        rc, s1 = pl.solve(Ts, precision=1, tol=1e-7, max_iter=100000, tile_kind=3,
+                          dirs_per_lane=st[i]["dirs_per_lane"], dirs_per_cta=st[i]["dirs_per_cta"])
+        assert s1["iterations"] == its[i], (i, p.name)
+        np.testing.assert_array_equal(Th[batch.offsets[i]:batch.offsets[i + 1]], Ts)
+    for i in sorted(range(len(probs)), key=lambda i: probs[i].n_cells)[:2]:
+        ref = oracle.solve(probs[i], max_iter=100000, tol=1e-7)
+        assert its[i] == ref["iters"]
+        assert rel(Th[batch.offsets[i]:batch.offsets[i + 1]], ref["T"]) < 1e-12
+
+
+def test_batch_rejects_bad_inputs(bte):
+    from paper_2503_23657_gb300.binding import BTEError
+    p1 = bi.tiny(2, n=(6, 5, 1), B=2, diffuse=(2,))
+    p2 = bi.tiny(2, n=(7, 6, 1), B=3, diffuse=(2,))
+    pm = bi.tiny(2, n=(7, 6, 1), B=2, masked=True, diffuse=(2,))
+    a, b, c = bte.Plan(p1), bte.Plan(p2), bte.Plan(pm)
+    for plans in ([a, b], [a, c], [a, a]):
+        with pytest.raises(BTEError) as ei:
+            bte.Batch(plans)
+        assert ei.value.code == -1
