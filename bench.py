@@ -1,7 +1,7 @@
 """Benchmark: cell x band x direction updates/s and time-to-converge of the
 steady nongray phonon-BTE hot path on one GB300 (or N replicas).
 
-Workload (one "step"): the 2D nongray square -- 128 x 128 cells on
+Default workload (one "step"): the 2D nongray square -- 128 x 128 cells on
 2 um x 2 um, 15 synthetic silicon-like bands, 64 directions (8 Gauss-Legendre
 polar x 8 azimuths), left wall 310 K, right wall 300 K, top/bottom diffuse --
 solved from T = 300 K to eps_T < 1e-6 with FP32 sweeps and FP64 reductions
@@ -9,7 +9,13 @@ solved from T = 300 K to eps_T < 1e-6 with FP32 sweeps and FP64 reductions
 (64 seeded probes) to a relative change of 1e-6.  ``value`` counts the
 updates of every forward and adjoint source iteration.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Other workloads (--workload): ``slab`` (1D gray slab, 200 cells, FP64 to
+1e-10), ``hotspot`` (3D cube 64^3, 15 bands x 128 directions, Gaussian
+source, forward to 1e-6), ``finfet`` (masked 160x80x64 FinFET, forward +
+adjoint to 1e-6), ``ensemble`` (256 uneven 2D squares solved as one batch,
+forward to 1e-6 per instance).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 
 With torchrun (N > 1) every rank solves its own replica of the workload (the
 single-instance path does not shard; "replicas only").
@@ -29,9 +35,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "square2d_128x128_B15_D64_fwd+adj_eps1e-6"
 METRIC = "cell*band*direction updates/s (fwd+adj to eps_T<1e-6, FP32 sweeps)"
-TOL = 1e-6
+
+# workload -> (problem maker, name, tol, FP64?, adjoint?)
+WORKLOADS = {
+    "square": (lambda bi: bi.square_2d(), "square2d_128x128_B15_D64_fwd+adj_eps1e-6", 1e-6, False, True),
+    "slab": (lambda bi: bi.gray_slab(), "slab1d_200_B1_D16_fwd_eps1e-10_fp64", 1e-10, True, False),
+    "hotspot": (lambda bi: bi.hotspot_3d(), "hotspot3d_64^3_B15_D128_fwd_eps1e-6", 1e-6, False, False),
+    "finfet": (lambda bi: bi.finfet_3d(), "finfet3d_160x80x64_B15_D128_fwd+adj_eps1e-6", 1e-6, False, True),
+    "ensemble": (lambda bi: bi.ensemble_2d(), "ensemble2d_256x(32..160)^2_B15_D64_fwd_eps1e-6", 1e-6, False, False),
+}
 L2_FLUSH_BYTES = 512 << 20
 TIME_EVERY = 8   # sweeps timed with CUDA events: one in every TIME_EVERY iterations
 
@@ -100,10 +113,7 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
 # since the capture has no entry)
-NCU_TRAFFIC = {
-    # profiles/sweep2dp_square128.md: 177.9 KB read + 0.8 KB written (128 x 128 square, tile 3:4:4)
-    ("sweep2dp_kernel<float, 4, 8, 0, 0>", "3:4:4"): 178688,
-}
+NCU_TRAFFIC = {}
 
 
 def measured_hbm_peak():
@@ -128,27 +138,36 @@ def sweep_kernel_name(p, st):
     """The sweep kernel a solve ran (forward and adjoint share it), as ncu
     names it."""
     dw = st["dirs_per_lane"]
+    phi = 0 if p.phi is None or p.Q_amp == 0.0 else 1
     if st["tile_kind"] == 3:
-        return f"sweep2dp_kernel<float, {dw}, 8, 0, 0>"
+        return f"sweep2dp_kernel<float, {dw}, 8, {phi}, 0, {st['source_staged']}>"
     if st["tile_kind"] == 2:
         rb = next(r for r in (1, 2, 3, 4, 5) if 32 * r >= p.n[1])
         return f"sweep2d_kernel<float, {dw}, {rb}, false>"
-    return f"sweep_kernel<float, {dw}, 1, false, false>"
+    return f"sweep_kernel<float, {dw}, lz, {int(p.dim == 3)}, 0>"
 
 
-def cpu_baseline_oracle(iters: int = 20):
+def oracle_iters(units_per_iter, seconds=15.0, rate=4e7):
+    """Source iterations of the oracle that take about `seconds` on one core."""
+    return max(1, int(round(seconds * rate / max(units_per_iter, 1))))
+
+
+def cpu_baseline_oracle(probs, iters):
     """The FP64 oracle (single thread) on a bounded sample of the workload:
-    `iters` forward source iterations of the full 128x128 square."""
-    import bte_inputs as bi
+    `iters` forward source iterations of (the first instances of) it."""
     import oracle
-    p = bi.square_2d()
+    oracle.build()
     t0 = time.perf_counter()
-    oracle.solve(p, max_iter=iters, tol=0.0)
+    units = 0
+    for p in probs:
+        oracle.solve(p, max_iter=iters, tol=0.0)
+        units += iters * p.n_active * p.B * p.D
+        if time.perf_counter() - t0 > 20.0:
+            break
     dt = time.perf_counter() - t0
-    units = iters * p.n_active * p.B * p.D
     return {"value": units / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} forward source iterations of the full 128x128x15x64 square "
-                      f"({units:.3g} updates, {dt:.1f} s, FP64, 1 thread)"}
+            "sample": f"{iters} forward source iterations of {len(probs) if len(probs) == 1 else 'the first'} "
+                      f"instance(s) of the workload ({units:.3g} updates, {dt:.1f} s, FP64, 1 thread)"}
 
 
 def run_reference(args, ws, rank):
@@ -158,8 +177,11 @@ def run_reference(args, ws, rank):
     import bte_inputs as bi
     import oracle
     oracle.build()
-    p = bi.square_2d()
-    k_iter = 2
+    make, name, tol, fp64, adj = WORKLOADS[args.workload]
+    probs = make(bi)
+    probs = probs if isinstance(probs, list) else [probs]
+    p = probs[0]
+    k_iter = oracle_iters(p.n_active * p.B * p.D, seconds=3.0)
     units_step = k_iter * p.n_active * p.B * p.D
     for _ in range(args.warmup):
         oracle.solve(p, max_iter=1, tol=0.0)
@@ -173,15 +195,39 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (oracle/bte_oracle.c), 1 thread",
-                   "step": f"{k_iter} forward source iterations (bounded sample)"},
+        "config": {"workload": name, "reference": "FP64 CPU oracle (oracle/bte_oracle.c), 1 thread",
+                   "step": f"{k_iter} forward source iterations of {p.name} (bounded sample)"},
         "cpu_baseline": {"value": val, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps x {k_iter} source iterations of the full square"},
+                         "sample": f"{args.steps} steps x {k_iter} source iterations of {p.name}"},
         "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def roofline_object(kernel, tile, sweep_ms, updates_per_launch, B, D, extra):
+    """The sweep's HBM-equivalent rate: algorithmic bytes per launch (one FP32
+    e write per update + T, S, q per cell) over the measured launch time."""
+    import torch
+    bytes_per_update = 4.0 + 40.0 / (B * D)
+    achieved = bytes_per_update * updates_per_launch / (sweep_ms * 1e-3) / 1e9
+    peak_hbm, peak_src = measured_hbm_peak()
+    flops_per_update = 7.0   # 3 FMA + 1 MUL per update (upwind update + weighted sum)
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    smax = 2070.0
+    peak_fp32 = sm_count * 128 * 2 * smax * 1e6 / 1e12
+    alu_achieved = flops_per_update * updates_per_launch / (sweep_ms * 1e-3) / 1e12
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
+         "traffic": NCU_TRAFFIC.get((kernel, tile)), "kernel": kernel, "tile": tile, "peak_source": peak_src,
+         "algorithmic": f"{bytes_per_update:.4f} B x {updates_per_launch} cell*band*direction updates per launch "
+                        f"(e write per update + per-cell T, S, q); the kernel keeps e on chip (e is regenerated "
+                        f"once after convergence), so DRAM traffic is far lower",
+         "sweep_ms": sweep_ms,
+         "alu": {"achieved": alu_achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": alu_achieved / peak_fp32,
+                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz"}}
+    r.update(extra)
+    return r
 
 
 def main():
@@ -190,8 +236,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--workload", default="square", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations of the CPU baseline (0 = ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     ap.add_argument("--store-e-every-iter", action="store_true")
     ap.add_argument("--tile", default="0:0:0",
                     help="sweep tile kind:dirs_per_lane:dirs_per_cta (0:0:0 = autotuned); profiling runs pin "
@@ -209,22 +257,93 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if ws > 1:
-            dist.barrier()
+    import bte_inputs as bi
+    make, name, tol, fp64, with_adj = WORKLOADS[args.workload]
+    probs = make(bi)
+    probs = probs if isinstance(probs, list) else [probs]
 
     # the CPU baseline runs before any GPU work (no fork after CUDA init)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_oracle(args.cpu_iters)
+        p0 = probs[0]
+        cpu = cpu_baseline_oracle(probs, args.cpu_iters or oracle_iters(p0.n_active * p0.B * p0.D))
 
     import __graft_entry__
     __graft_entry__.build()
-    import bte_inputs as bi
     import paper_2503_23657_gb300 as m
 
-    p = bi.square_2d()
-    probes, T_obs = probes_and_obs(p)
+    ctx = dict(args=args, ws=ws, rank=rank, dist=dist, torch=torch, m=m, name=name, tol=tol, fp64=fp64,
+               with_adj=with_adj, cpu=cpu)
+    if args.workload == "ensemble":
+        line = run_ensemble(probs, ctx)
+    else:
+        line = run_single(probs[0], ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def timed_steps(ctx, step, flush):
+    """W untimed steps, then exactly K steps between barriers + syncs; returns
+    per-step device times (ms), step results, clocks."""
+    torch, args, ws, dist = ctx["torch"], ctx["args"], ctx["ws"], ctx["dist"]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    torch.cuda.nvtx.range_push("bench_timed")   # lets a profiler select the timed steps
+    times, res = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)   # evict the previous step's working set from L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if ws > 1:
+        dist.barrier()
+    return times, res, clocks.stop()
+
+
+def aggregate(ctx, units, t_total):
+    torch, ws, dist = ctx["torch"], ctx["ws"], ctx["dist"]
+    if ws > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        uu = torch.tensor([units], dtype=torch.float64, device="cuda")
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        return float(uu), float(tt)
+    return units, t_total
+
+
+def base_line(ctx, value, t_max, dtype, config):
+    args = ctx["args"]
+    return {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ctx["ws"], "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+
+
+def run_single(p, ctx):
+    torch, m, args, tol = ctx["torch"], ctx["m"], ctx["args"], ctx["tol"]
+    prec = m.BTE_FP64 if ctx["fp64"] else m.BTE_FP32
+    if ctx["with_adj"]:
+        if getattr(p, "probes", None) is not None and p.T_obs is not None:
+            probes, T_obs = np.asarray(p.probes), np.asarray(p.T_obs)
+        else:
+            probes, T_obs = probes_and_obs(p)
+    else:
+        probes, T_obs = np.zeros(0, dtype=np.int64), np.zeros(0)
     probes_d = torch.as_tensor(probes, device="cuda")
     T_obs_d = torch.as_tensor(T_obs, device="cuda")
     plan = m.Plan(p)
@@ -234,154 +353,178 @@ def main():
     g = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     per_update = p.n_active * p.B * p.D
-
     tile_kind, tile_dw, tile_cw = (int(x) for x in args.tile.split(":"))
 
-    def step(T, g):
-        rc, sf = plan.solve(T, precision=m.BTE_FP32, tol=TOL, max_iter=100000, stream=sp,
+    def step():
+        rc, sf = plan.solve(T, precision=prec, tol=tol, max_iter=100000, stream=sp,
                             store_e_every_iter=args.store_e_every_iter, tile_kind=tile_kind,
                             dirs_per_lane=tile_dw, dirs_per_cta=tile_cw)
-        g.zero_()
-        g[probes_d] = T[probes_d] - T_obs_d
-        rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g, tol=TOL, max_iter=100000)
+        sa = None
+        if ctx["with_adj"]:
+            g.zero_()
+            g[probes_d] = T[probes_d] - T_obs_d
+            rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g, tol=tol, max_iter=100000)
         return sf, sa
 
-    # the sweep of every 8th iteration of the timed steps is bracketed by CUDA
-    # events on its stream (inside the captured graphs): the dominant kernel's
-    # mean duration, sampled over the whole timed region
+    # the sweep of every TIME_EVERY-th iteration of the timed steps is bracketed
+    # by CUDA events on its stream (inside the captured graphs): the dominant
+    # kernel's mean duration, sampled over the whole timed region
     plan.set_sweep_timing(TIME_EVERY)
-    for _ in range(args.warmup):
-        step(T, g)
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(torch.cuda.current_device())
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    torch.cuda.nvtx.range_push("bench_timed")   # lets a profiler select the timed steps
-    times, fstats, astats = [], [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)   # evict the previous step's working set from L2
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sf, sa = step(T, g)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        fstats.append(sf)
-        astats.append(sa)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    barrier()
-    clk = clocks.stop()
-
-    units = sum((f["iterations"] + a["iterations"]) * per_update for f, a in zip(fstats, astats))
+    times, res, clk = timed_steps(ctx, step, flush)
+    plan.set_sweep_timing(0)
+    fstats = [r[0] for r in res]
+    astats = [r[1] for r in res if r[1] is not None]
+    units = sum(f["iterations"] * per_update for f in fstats) + sum(a["iterations"] * per_update for a in astats)
     t_total = sum(times) / 1e3
-    t_max = t_total
-    units_all = units
-    if ws > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        uu = torch.tensor([units], dtype=torch.float64, device="cuda")
-        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
-        t_max, units_all = float(tt), float(uu)
+    units_all, t_max = aggregate(ctx, units, t_total)
     value = units_all / t_max
-    launches = sum(f["kernel_launches"] + a["kernel_launches"] for f, a in zip(fstats, astats))
+    launches = sum(f["kernel_launches"] for f in fstats) + sum(a["kernel_launches"] for a in astats)
 
-    # forward-only and FP64 comparison (not part of the timed region)
     fwd_ups = statistics.median(f["updates_per_s"] for f in fstats)
     fwd_ms = statistics.median(f["seconds"] for f in fstats) * 1e3
-    T64 = torch.zeros_like(T)
-    plan.solve(T64, precision=m.BTE_FP64, tol=TOL, max_iter=100000, stream=sp)
-    rc, s64 = plan.solve(T64, precision=m.BTE_FP64, tol=TOL, max_iter=100000, stream=sp)
-    dT_fp64 = float((T - T64).abs().max() / T64.abs().max())
+    extra = {}
+    if not ctx["fp64"] and not args.no_fp64:
+        # forward in FP64 on the GPU (not part of the timed region)
+        T64 = torch.zeros_like(T)
+        plan.solve(T64, precision=m.BTE_FP64, tol=tol, max_iter=100000, stream=sp)
+        rc, s64 = plan.solve(T64, precision=m.BTE_FP64, tol=tol, max_iter=100000, stream=sp)
+        extra = {"fp64_fwd_updates_per_s": s64["updates_per_s"], "fp64_fwd_time_to_converge_ms": s64["seconds"] * 1e3,
+                 "fp64_fwd_iterations": s64["iterations"], "speedup_fp32_vs_fp64_fwd": fwd_ups / s64["updates_per_s"],
+                 "T_fp32_vs_fp64_rel": float((T - T64).abs().max() / T64.abs().max())}
 
-    plan.set_sweep_timing(0)
     # dominant kernel: the sweep (forward and adjoint launches of the same
     # kernel), its mean launch duration from the CUDA events of the timed steps
     fwd_sweep_s = sum(f["sweep_seconds"] for f in fstats)
     fwd_sweeps = sum(f["sweep_launches"] for f in fstats)
     adj_sweep_s = sum(a["sweep_seconds"] for a in astats)
     adj_sweeps = sum(a["sweep_launches"] for a in astats)
-    sweep_ms = (fwd_sweep_s + adj_sweep_s) / (fwd_sweeps + adj_sweeps) * 1e3
+    sweep_ms = (fwd_sweep_s + adj_sweep_s) / max(fwd_sweeps + adj_sweeps, 1) * 1e3
     dw = fstats[-1]["dirs_per_lane"]
-    kernel = sweep_kernel_name(p, fstats[-1])
-    # algorithmic HBM bytes per cell x band x direction update: one FP32
-    # write of e, plus per cell the T read (8 B) and S, q writes (32 B)
-    # shared by its B x D updates
-    bytes_per_update = 4.0 + 40.0 / (p.B * p.D)
-    sweep_bytes = bytes_per_update * per_update
-    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
-    peak_hbm, peak_src = measured_hbm_peak()
     tile = f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}"
-    traffic = NCU_TRAFFIC.get((kernel, tile))
-    flops_per_update = 7.0   # 3 FMA + 1 MUL per update (upwind update + weighted sum)
-    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
-    smax = 2070.0
-    peak_fp32 = sm_count * 128 * 2 * smax * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes at max SM clock
-    alu_achieved = flops_per_update * per_update / (sweep_ms * 1e-3) / 1e12
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
-                "frac": achieved / peak_hbm, "traffic": traffic,
-                "kernel": kernel, "tile": tile, "peak_source": peak_src,
-                "algorithmic": f"{bytes_per_update:.4f} B x {per_update} cell*band*direction updates per launch "
-                               f"(e write per update + per-cell T, S, q); the kernel itself keeps e on chip "
-                               f"(e is regenerated once after convergence), so DRAM traffic is far lower",
-                "sweep_ms": sweep_ms, "sweep_launches_timed": fwd_sweeps + adj_sweeps,
-                "fwd_sweep_ms": fwd_sweep_s / max(fwd_sweeps, 1) * 1e3,
-                "adj_sweep_ms": adj_sweep_s / max(adj_sweeps, 1) * 1e3,
-                "sweep_share_of_step": (fwd_sweep_s * timed_sweep_scale(fstats) +
-                                        adj_sweep_s * timed_sweep_scale(astats)) / t_total,
-                "alu": {"achieved": alu_achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                        "frac": alu_achieved / peak_fp32,
-                        "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz"}}
+    kernel = sweep_kernel_name(p, fstats[-1])
+    roofline = roofline_object(kernel, tile, sweep_ms, per_update, p.B, p.D, {
+        "sweep_launches_timed": fwd_sweeps + adj_sweeps,
+        "fwd_sweep_ms": fwd_sweep_s / max(fwd_sweeps, 1) * 1e3,
+        "adj_sweep_ms": adj_sweep_s / max(adj_sweeps, 1) * 1e3 if astats else None,
+        "sweep_share_of_step": (fwd_sweep_s * timed_sweep_scale(fstats) +
+                                (adj_sweep_s * timed_sweep_scale(astats) if astats else 0.0)) / t_total})
 
     # end to end through the C ABI with host buffers (pinned), copies inside
-    T_init_h = torch.full((p.n_cells,), 300.0, dtype=torch.float64).pin_memory()
+    T_init_h = torch.full((p.n_cells,), float(p.T_init), dtype=torch.float64).pin_memory()
     T_h = torch.zeros(p.n_cells, dtype=torch.float64).pin_memory()
     g_h = torch.zeros(p.n_cells, dtype=torch.float64).pin_memory()
+    T_obs_t = torch.as_tensor(T_obs)
     e2e_units, e2e_t = 0, 0.0
-    for i in range(max(2, args.steps)):
+    for i in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rc, sf = plan.solve(T_h, T_init=T_init_h, precision=m.BTE_FP32, tol=TOL, max_iter=100000, stream=sp,
+        rc, sf = plan.solve(T_h, T_init=T_init_h, precision=prec, tol=tol, max_iter=100000, stream=sp,
                             tile_kind=tile_kind, dirs_per_lane=tile_dw, dirs_per_cta=tile_cw)
-        g_h.zero_()
-        g_h[probes] = T_h[probes] - torch.as_tensor(T_obs)
-        rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g_h, tol=TOL, max_iter=100000)
+        u = sf["iterations"] * per_update
+        if ctx["with_adj"]:
+            g_h.zero_()
+            g_h[probes] = T_h[probes] - T_obs_t
+            rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g_h, tol=tol, max_iter=100000)
+            u += sa["iterations"] * per_update
         t1 = time.perf_counter()
         if i > 0:
-            e2e_units += (sf["iterations"] + sa["iterations"]) * per_update
+            e2e_units += u
             e2e_t += t1 - t0
-    e2e_value = e2e_units / e2e_t * (ws if ws > 1 else 1)
+    e2e_value = e2e_units / e2e_t * (ctx["ws"] if ctx["ws"] > 1 else 1)
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": p.n_cells, "bands": p.B, "directions": p.D,
-                       "tol_eps_T": TOL, "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)",
-                       "parallelism": "replicas" if ws > 1 else "single",
-                       "store_e_every_iter": bool(args.store_e_every_iter),
-                       "tile": f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}"},
-            "fwd_iterations": fstats[-1]["iterations"], "adj_iterations": astats[-1]["iterations"],
-            "fwd_time_to_converge_ms": fwd_ms, "fwd_updates_per_s": fwd_ups,
-            "fwd_adj_ms_per_step": statistics.median(times),
-            "fp64_fwd_updates_per_s": s64["updates_per_s"], "fp64_fwd_time_to_converge_ms": s64["seconds"] * 1e3,
-            "fp64_fwd_iterations": s64["iterations"], "speedup_fp32_vs_fp64_fwd": fwd_ups / s64["updates_per_s"],
-            "T_fp32_vs_fp64_rel": dT_fp64,
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "updates/s",
-                    "h2d_bytes_per_step": 2 * 8 * p.n_cells, "d2h_bytes_per_step": 8 * p.n_cells + 8 * (p.B + 7)},
-            "gpu_launches": launches,
-            "clocks": clk,
-        }
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
-    return 0
+    config = {"workload": ctx["name"], "cells": p.n_cells, "solid_cells": p.n_active, "bands": p.B,
+              "directions": p.D, "tol_eps_T": tol,
+              "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)",
+              "parallelism": "replicas" if ctx["ws"] > 1 else "single",
+              "store_e_every_iter": bool(args.store_e_every_iter), "tile": tile}
+    line = base_line(ctx, value, t_max, "f64" if ctx["fp64"] else "f32", config)
+    line.update({"fwd_iterations": fstats[-1]["iterations"],
+                 "adj_iterations": astats[-1]["iterations"] if astats else None,
+                 "fwd_time_to_converge_ms": fwd_ms, "fwd_updates_per_s": fwd_ups,
+                 "step_ms_median": statistics.median(times)})
+    line.update(extra)
+    line.update({
+        "roofline": roofline, "cpu_baseline": ctx["cpu"],
+        "e2e": {"value": e2e_value, "unit": "updates/s",
+                "h2d_bytes_per_step": (2 if ctx["with_adj"] else 1) * 8 * p.n_cells,
+                "d2h_bytes_per_step": 8 * p.n_cells + (8 * (p.B + 7) if ctx["with_adj"] else 0)},
+        "gpu_launches": launches, "clocks": clk})
+    return line
+
+
+def run_ensemble(probs, ctx):
+    torch, m, args, tol = ctx["torch"], ctx["m"], ctx["args"], ctx["tol"]
+    plans = [m.Plan(p) for p in probs]
+    batch = m.Batch(plans)
+    n = sum(p.n_cells for p in probs)
+    T = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    per_iter = [p.n_active * p.B * p.D for p in probs]
+
+    def step():
+        rc, st, bs = batch.solve(T, precision=m.BTE_FP32, tol=tol, max_iter=100000)
+        return st, bs
+
+    times, res, clk = timed_steps(ctx, step, flush)
+    units = sum(sum(s["iterations"] * u for s, u in zip(st, per_iter)) for st, bs in res)
+    t_total = sum(times) / 1e3
+    units_all, t_max = aggregate(ctx, units, t_total)
+    value = units_all / t_max
+    launches = sum(bs["kernel_launches"] for st, bs in res)
+    st, bs = res[-1]
+    its = sorted(s["iterations"] for s in st)
+
+    # FP64 batch (not timed above) and the FP32 error against it
+    extra = {}
+    if not args.no_fp64:
+        T64 = torch.zeros_like(T)
+        batch.solve(T64, precision=m.BTE_FP64, tol=tol, max_iter=100000)
+        rc, st64, bs64 = batch.solve(T64, precision=m.BTE_FP64, tol=tol, max_iter=100000)
+        errs = [float((T[batch.offsets[i]:batch.offsets[i + 1]] - T64[batch.offsets[i]:batch.offsets[i + 1]]).abs().max()
+                      / T64[batch.offsets[i]:batch.offsets[i + 1]].abs().max()) for i in range(len(probs))]
+        extra = {"fp64_time_to_converge_ms": bs64["seconds"] * 1e3, "fp64_updates_per_s": bs64["updates_per_s"],
+                 "speedup_fp32_vs_fp64": bs64["seconds"] / bs["seconds"],
+                 "T_fp32_vs_fp64_rel_max": max(errs),
+                 "iterations_equal_fp32_fp64": sum(int(a["iterations"] == b["iterations"]) for a, b in zip(st, st64))}
+
+    # the batched sweep phase (all size classes, fork to join) with every
+    # instance active: fixed iterations with the sweep phase event-timed
+    batch.set_sweep_timing(True)
+    Tz = torch.zeros_like(T)
+    rc, stz, bsz = batch.solve(Tz, precision=m.BTE_FP32, tol=0.0, max_iter=256)
+    batch.set_sweep_timing(False)
+    sweep_ms = bsz["sweep_seconds"] / max(bsz["sweep_iterations"], 1) * 1e3
+    tiles = sorted({f"3:{s['dirs_per_lane']}:{s['dirs_per_cta']}" for s in stz})
+    roofline = roofline_object("sweep2dp_batch_kernel (all size classes, concurrent)", ",".join(tiles), sweep_ms,
+                               sum(per_iter), probs[0].B, probs[0].D,
+                               {"sweep_phases_timed": bsz["sweep_iterations"],
+                                "timing": "sweep phase of the first iteration of each 32-iteration graph, "
+                                          "fixed-iteration run with every instance active"})
+
+    # end to end with a host output buffer (pinned), copy inside
+    T_h = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e_units, e2e_t = 0, 0.0
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st2, bs2 = batch.solve(T_h, precision=m.BTE_FP32, tol=tol, max_iter=100000)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_units += sum(s["iterations"] * u for s, u in zip(st2, per_iter))
+            e2e_t += t1 - t0
+    config = {"workload": ctx["name"], "instances": len(probs), "cells": n, "bands": probs[0].B,
+              "directions": probs[0].D, "tol_eps_T": tol, "size_classes": bs["classes"],
+              "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)",
+              "parallelism": "replicas" if ctx["ws"] > 1 else "single", "tiles": ",".join(tiles)}
+    line = base_line(ctx, value, t_max, "f32", config)
+    line.update({"time_to_converge_ms": bs["seconds"] * 1e3, "iterations_min_median_max": [its[0], its[len(its) // 2], its[-1]],
+                 "converged": bs["converged"]})
+    line.update(extra)
+    line.update({"roofline": roofline, "cpu_baseline": ctx["cpu"],
+                 "e2e": {"value": e2e_units / e2e_t, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 8 * n},
+                 "gpu_launches": launches, "clocks": clk})
+    return line
 
 
 if __name__ == "__main__":

@@ -153,6 +153,8 @@ typedef struct {
                                time of the call's timed source-iteration sweep launches,
                                each bracketed by CUDA events on its stream; else 0 */
     long long sweep_launches; /* number of sweep launches summed in sweep_seconds */
+    int source_staged;      /* row-pipeline tile: 1 = per-cell source staged in shared memory,
+                               0 = read ahead from global memory (other kernels: 1) */
 } bte_stats;
 
 /* Fill opts with defaults: FP32, tol 1e-6, max_iter 100000, T_init 300 K,
@@ -251,12 +253,19 @@ typedef struct {
     double updates_per_s;    /* updates / seconds */
     long long kernel_launches; /* kernels launched by the iteration loop */
     int classes;             /* size classes (concurrent sweep launches per iteration) */
+    double sweep_seconds;    /* with sweep timing on: summed device time of the timed sweep phases */
+    long long sweep_iterations; /* number of sweep phases timed */
 } bte_batch_stats;
 
 int bte_batch_create(int n, bte_plan *const *plans, bte_batch **out);
 int bte_batch_solve(bte_batch *b, const bte_solve_opts *o, double *T_out, bte_stats *st, bte_batch_stats *bs);
 void bte_batch_destroy(bte_batch *b);
 const char *bte_batch_last_error(const bte_batch *b);
+/* bte_batch_set_sweep_timing -- on != 0: the sweep phase (all size classes,
+ * fork to join) of the first iteration of every poll interval is bracketed by
+ * CUDA events; bte_batch_stats reports the summed time and count.  Returns
+ * BTE_OK, BTE_EINVAL or BTE_ECUDA. */
+int bte_batch_set_sweep_timing(bte_batch *b, int on);
 
 /* Copy the eps_T history of the last bte_solve (one value per iteration,
  * at most n, the first 65536 iterations) into out (host).  Returns the

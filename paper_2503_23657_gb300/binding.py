@@ -35,7 +35,7 @@ ERROR_NAMES = {
 EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_error",
            "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep",
            "bte_set_sweep_timing", "bte_eps_T_noalloc", "bte_batch_create", "bte_batch_solve",
-           "bte_batch_destroy", "bte_batch_last_error"]
+           "bte_batch_destroy", "bte_batch_last_error", "bte_batch_set_sweep_timing"]
 
 
 class Grid(ctypes.Structure):
@@ -70,7 +70,7 @@ class Stats(ctypes.Structure):
                 ("updates_per_s", ctypes.c_double), ("dirs_per_lane", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong), ("tile_kind", ctypes.c_int),
                 ("dirs_per_cta", ctypes.c_int), ("sweep_seconds", ctypes.c_double),
-                ("sweep_launches", ctypes.c_longlong)]
+                ("sweep_launches", ctypes.c_longlong), ("source_staged", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -82,7 +82,8 @@ _lib = None
 class BatchStats(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int), ("converged", ctypes.c_int), ("max_iterations", ctypes.c_int),
                 ("seconds", ctypes.c_double), ("updates", ctypes.c_double), ("updates_per_s", ctypes.c_double),
-                ("kernel_launches", ctypes.c_longlong), ("classes", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_longlong), ("classes", ctypes.c_int),
+                ("sweep_seconds", ctypes.c_double), ("sweep_iterations", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -126,6 +127,8 @@ def load(path: str = LIB_PATH):
     lib.bte_batch_destroy.restype = None
     lib.bte_batch_last_error.argtypes = [vp]
     lib.bte_batch_last_error.restype = ctypes.c_char_p
+    lib.bte_batch_set_sweep_timing.argtypes = [vp, ip]
+    lib.bte_batch_set_sweep_timing.restype = ip
     lib.bte_eps_T_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp]
     lib.bte_eps_T_noalloc.restype = ip
     _lib = lib
@@ -312,6 +315,11 @@ class Batch:
 
     def error(self) -> str:
         return self._lib.bte_batch_last_error(self._h).decode()
+
+    def set_sweep_timing(self, on=True):
+        rc = self._lib.bte_batch_set_sweep_timing(self._h, 1 if on else 0)
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
 
     def solve(self, T_out, precision=BTE_FP32, tol=1e-6, max_iter=100000, T_init_uniform=300.0, Q_amp=0.0,
               tau=None, stream=None, poll_every=32, dirs_per_lane=0, dirs_per_cta=0, check=True):

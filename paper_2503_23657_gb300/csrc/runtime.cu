@@ -176,6 +176,8 @@ struct bte_batch {
     std::vector<cudaStream_t> side; // one capture stream per class
     std::vector<cudaEvent_t> join;  // one per class
     cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t tev[2] = {nullptr, nullptr};  // sweep-phase timing (first iteration of a replay)
+    bool time_sweeps = false;
     BatchState<float> bs32;
     BatchState<double> bs64;
     std::string err;
@@ -186,6 +188,8 @@ struct bte_batch {
         if (fork) cudaEventDestroy(fork);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        for (cudaEvent_t e : tev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -925,6 +929,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         st->kernel_launches = launches;
         st->sweep_seconds = sweep_ms * 1e-3;
         st->sweep_launches = n_timed;
+        st->source_staged = tile_of(tid).kind == 4 ? 0 : 1;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the temperature update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "max_iter reached before eps_T < tol");
@@ -1142,6 +1147,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         st->kernel_launches = launches + 3;  // final sweep + update + gradient reduction
         st->sweep_seconds = sweep_ms * 1e-3;
         st->sweep_launches = n_timed;
+        st->source_staged = tile_of(dw).kind == 4 ? 0 : 1;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the adjoint update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "adjoint: max_iter reached before tol");
@@ -1417,8 +1423,9 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
 // joined back into `stream`), then one update launch over every instance.
 template <typename real>
 cudaError_t batch_enqueue(bte_batch *bt, BatchState<real> &bs, const std::vector<int> &tiles, int parity,
-                          cudaStream_t stream) {
-    cudaError_t e = cudaEventRecord(bt->fork, stream);
+                          cudaStream_t stream, bool timed = false) {
+    cudaError_t e = timed ? record_timing_event(bt->tev[0], stream) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaEventRecord(bt->fork, stream);
     for (size_t c = 0; c < bt->classes.size() && e == cudaSuccess; ++c) {
         cudaStream_t s = bt->side[c];
         e = cudaStreamWaitEvent(s, bt->fork, 0);
@@ -1428,6 +1435,7 @@ cudaError_t batch_enqueue(bte_batch *bt, BatchState<real> &bs, const std::vector
         if (e == cudaSuccess) e = cudaEventRecord(bt->join[c], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, bt->join[c], 0);
     }
+    if (e == cudaSuccess && timed) e = record_timing_event(bt->tev[1], stream);
     if (e != cudaSuccess) return e;
     return launch_update_batch<real>(bs.update[parity].template as<UpdateParams<real>>(), bt->d_table.as<int2>(),
                                      bt->upd_blocks, stream);
@@ -1520,6 +1528,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
     poll = std::max(2, poll + (poll & 1));
     std::vector<int> key = tiles;
     key.push_back(poll);
+    key.push_back(bt->time_sweeps ? 1 : 0);
     key.push_back((int)(tol * 1e15 > 2e9 ? 2e9 : tol * 1e15));
     if (!bs.graph || bs.graph_key != key) {
         if (bs.graph) {
@@ -1539,7 +1548,8 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
         BCK(bt, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g;
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        for (int i = 0; i < poll && ce == cudaSuccess; ++i) ce = batch_enqueue<real>(bt, bs, tiles, i & 1, cs);
+        for (int i = 0; i < poll && ce == cudaSuccess; ++i)
+            ce = batch_enqueue<real>(bt, bs, tiles, i & 1, cs, bt->time_sweeps && i == 0);
         cudaError_t ce2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
         if (ce != cudaSuccess) return bfail(bt, BTE_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce));
@@ -1555,18 +1565,27 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
     const int max_iter = o->max_iter;
     int enq = 0;
     long long launches = 0;
+    double sweep_ms = 0.0;
+    long long n_timed = 0;
     BCK(bt, cudaEventRecord(bt->ev0, stream));
     while (enq < max_iter) {
         const int k = std::min(poll, max_iter - enq);
         if (k == poll) {
             BCK(bt, cudaGraphLaunch(bs.graph, stream));
         } else {
-            for (int i = 0; i < k; ++i) BCK(bt, batch_enqueue<real>(bt, bs, tiles, (enq + i) & 1, stream));
+            for (int i = 0; i < k; ++i)
+                BCK(bt, batch_enqueue<real>(bt, bs, tiles, (enq + i) & 1, stream, bt->time_sweeps && i == 0));
         }
         enq += k;
         launches += (long long)k * (long long)(bt->classes.size() + 1);
         BCK(bt, cudaMemcpyAsync(bt->h_done, bt->d_done.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
         BCK(bt, cudaStreamSynchronize(stream));
+        if (bt->time_sweeps) {
+            float t = 0.f;
+            BCK(bt, cudaEventElapsedTime(&t, bt->tev[0], bt->tev[1]));
+            sweep_ms += t;
+            n_timed += 1;
+        }
         if (*bt->h_done >= bt->n) break;
     }
     BCK(bt, cudaEventRecord(bt->ev1, stream));
@@ -1606,6 +1625,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
             s.dirs_per_lane = tile_of(tiles[ci]).dw;
             s.dirs_per_cta = tile_of(tiles[ci]).cw;
             s.tile_kind = 3;
+            s.source_staged = tile_of(tiles[ci]).kind == 4 ? 0 : 1;
         }
     }
     BCK(bt, cudaStreamSynchronize(stream));
@@ -1619,6 +1639,8 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
         bst->updates_per_s = ms > 0 ? updates / (ms * 1e-3) : 0.0;
         bst->kernel_launches = launches;
         bst->classes = (int)bt->classes.size();
+        bst->sweep_seconds = sweep_ms * 1e-3;
+        bst->sweep_iterations = n_timed;
     }
     for (int i = 0; i < bt->n; ++i)
         if (hs[i].status == 2) return bfail(bt, BTE_ETIMEOUT, "a bounded device wait expired in a batched sweep");
@@ -1812,6 +1834,19 @@ int bte_batch_solve(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_s
     if (o->precision == BTE_FP32) return batch_solve_t<float>(bt, o, T_out, st, bs);
     if (o->precision == BTE_FP64) return batch_solve_t<double>(bt, o, T_out, st, bs);
     return bfail(bt, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+}
+
+int bte_batch_set_sweep_timing(bte_batch *bt, int on) {
+    if (!bt) return bfail(nullptr, BTE_EINVAL, "batch is null");
+    if (on) {
+        for (cudaEvent_t &e : bt->tev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return bfail(bt, BTE_ECUDA, "bte_batch_set_sweep_timing: cudaEventCreate failed");
+            }
+    }
+    bt->time_sweeps = on != 0;
+    return BTE_OK;
 }
 
 void bte_batch_destroy(bte_batch *bt) { delete bt; }
