@@ -324,7 +324,7 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
     for (int c : p->groups_cnt) gmax = std::max(gmax, c);
     if (kind_req == 0 || kind_req == 3) {
         for (int stage : {1, 0}) {
-            for (int dw : {1, 2, 4}) {
+            for (int dw : {1, 2, 4, 8}) {
                 if (dw_req && dw != dw_req) continue;
                 for (int groups : {1, 2, 4, 8, 16}) {
                     if (groups > 1 && dw * groups > gmax) break;

@@ -144,7 +144,7 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
     const int set = s * G + g;
     const int d0 = ch.d0 + g * DW;
     const int ndir = max(0, min(DW, ch.cnt - g * DW));
-    real ax[DW], ay[DW], w[DW], invd[DW], wsx[DW], wsy[DW];
+    real ax[DW], ay[DW], w[DW], invd[DW];
 #pragma unroll
     for (int dd = 0; dd < DW; ++dd) {
         if (dd < ndir) {
@@ -152,14 +152,18 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
             ax[dd] = cf[0];
             ay[dd] = cf[1];
             w[dd] = cf[3];
-            // face-sum weights: forward w |s_a| (energy leaving), adjoint a_a w (nu = mu / w)
-            wsx[dd] = adj ? cf[0] * cf[3] : cf[4];
-            wsy[dd] = adj ? cf[1] * cf[3] : cf[5];
             invd[dd] = P.invdiag[(long long)b * P.D + d0 + dd];
         } else {
-            ax[dd] = ay[dd] = w[dd] = invd[dd] = wsx[dd] = wsy[dd] = real(0);
+            ax[dd] = ay[dd] = w[dd] = invd[dd] = real(0);
         }
     }
+    // face-sum weights (used after the sweep): forward w |s_a| (energy
+    // leaving), adjoint a_a w (nu = mu / w)
+    auto face_weight = [&](int dd, int axis) -> real {
+        if (dd >= ndir) return real(0);
+        const real *cf = P.coef + ((long long)b * P.D + d0 + dd) * 8;
+        return adj ? cf[axis] * cf[3] : cf[4 + axis];
+    };
     const real srck = P.srck[b];
     const real qb = PHI ? P.qb[b] : real(0);
     const int j = 32 * R + lane;  // row in traversal order
@@ -292,12 +296,15 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
     if (in) {
         real fs = real(0);
 #pragma unroll
-        for (int dd = 0; dd < DW; ++dd) fs = fma(wsx[dd], old[dd], fs);
+        for (int dd = 0; dd < DW; ++dd) fs = fma(face_weight(dd, 0), old[dd], fs);
         fsx[Y] = fs;
     }
     // downwind y-wall sums from the top row, which the last warp fed
     if (R + 1 == NRB) {
         __syncwarp();
+        real wsy[DW];
+#pragma unroll
+        for (int dd = 0; dd < DW; ++dd) wsy[dd] = face_weight(dd, 1);
         for (int i = lane; i < nx; i += 32) {
             real fs = real(0);
 #pragma unroll

@@ -7,6 +7,7 @@ cudaError_t launch_sweep2dp<float>(const Sweep2DParams<float> &p, int dw, cudaSt
     if (dw == 1) return launch_sweep2dp_t<float, 1, 8>(p, st);
     if (dw == 2) return launch_sweep2dp_t<float, 2, 8>(p, st);
     if (dw == 4) return launch_sweep2dp_t<float, 4, 8>(p, st);
+    if (dw == 8) return launch_sweep2dp_t<float, 8, 8>(p, st);
     return cudaErrorInvalidConfiguration;
 }
 
@@ -15,6 +16,7 @@ cudaError_t launch_sweep2dp_batch<float>(const Sweep2DBatch<float> &bt, int dw, 
     if (dw == 1) return launch_sweep2dp_batch_t<float, 1, 8>(bt, st);
     if (dw == 2) return launch_sweep2dp_batch_t<float, 2, 8>(bt, st);
     if (dw == 4) return launch_sweep2dp_batch_t<float, 4, 8>(bt, st);
+    if (dw == 8) return launch_sweep2dp_batch_t<float, 8, 8>(bt, st);
     return cudaErrorInvalidConfiguration;
 }
 
