@@ -113,7 +113,10 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
 # since the capture has no entry)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/sweep2dp_square128.md: 179.7 KB read + 1.0 KB written (128 x 128 square, tile 3:4:4:1)
+    ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 180736,
+}
 
 
 def measured_hbm_peak():
@@ -237,13 +240,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="square", choices=sorted(WORKLOADS))
+    ap.add_argument("--instances", type=int, default=256, help="ensemble: number of instances (a profiler "
+                                                                  "capture uses a small batch)")
     ap.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations of the CPU baseline (0 = ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     ap.add_argument("--store-e-every-iter", action="store_true")
-    ap.add_argument("--tile", default="0:0:0",
-                    help="sweep tile kind:dirs_per_lane:dirs_per_cta (0:0:0 = autotuned); profiling runs pin "
-                         "the tile the autotuner chose, since timings under a profiler are not representative")
+    ap.add_argument("--tile", default="0:0:0:0",
+                    help="sweep tile kind:dirs_per_lane:dirs_per_cta:source_staging (0:0:0:0 = autotuned); "
+                         "profiling runs pin the tile the autotuner chose, since timings under a profiler are "
+                         "not representative")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -259,8 +265,10 @@ def main():
 
     import bte_inputs as bi
     make, name, tol, fp64, with_adj = WORKLOADS[args.workload]
-    probs = make(bi)
+    probs = bi.ensemble_2d(n_instances=args.instances) if args.workload == "ensemble" else make(bi)
     probs = probs if isinstance(probs, list) else [probs]
+    if args.workload == "ensemble" and args.instances != 256:
+        name = name.replace("256x", f"{args.instances}x")
 
     # the CPU baseline runs before any GPU work (no fork after CUDA init)
     cpu = None
@@ -353,12 +361,12 @@ def run_single(p, ctx):
     g = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     per_update = p.n_active * p.B * p.D
-    tile_kind, tile_dw, tile_cw = (int(x) for x in args.tile.split(":"))
+    tile_kind, tile_dw, tile_cw, tile_st = ((int(x) for x in (args.tile + ":0:0:0:0").split(":")[:4]))
 
     def step():
         rc, sf = plan.solve(T, precision=prec, tol=tol, max_iter=100000, stream=sp,
                             store_e_every_iter=args.store_e_every_iter, tile_kind=tile_kind,
-                            dirs_per_lane=tile_dw, dirs_per_cta=tile_cw)
+                            dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st)
         sa = None
         if ctx["with_adj"]:
             g.zero_()
@@ -400,7 +408,7 @@ def run_single(p, ctx):
     adj_sweeps = sum(a["sweep_launches"] for a in astats)
     sweep_ms = (fwd_sweep_s + adj_sweep_s) / max(fwd_sweeps + adj_sweeps, 1) * 1e3
     dw = fstats[-1]["dirs_per_lane"]
-    tile = f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}"
+    tile = f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}:{2 - fstats[-1]['source_staged']}"
     kernel = sweep_kernel_name(p, fstats[-1])
     roofline = roofline_object(kernel, tile, sweep_ms, per_update, p.B, p.D, {
         "sweep_launches_timed": fwd_sweeps + adj_sweeps,
@@ -419,7 +427,7 @@ def run_single(p, ctx):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc, sf = plan.solve(T_h, T_init=T_init_h, precision=prec, tol=tol, max_iter=100000, stream=sp,
-                            tile_kind=tile_kind, dirs_per_lane=tile_dw, dirs_per_cta=tile_cw)
+                            tile_kind=tile_kind, dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st)
         u = sf["iterations"] * per_update
         if ctx["with_adj"]:
             g_h.zero_()

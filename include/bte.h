@@ -136,6 +136,8 @@ typedef struct {
                                2 = row-block kernel (unmasked 1D/2D, one region);
                                3 = row-pipeline kernel (unmasked 1D/2D, one region) */
     int dirs_per_cta;       /* row kernels: directions per CTA (0 = autotuned) */
+    int source_staging;     /* row-pipeline kernel: 0 = autotuned, 1 = per-cell source staged in
+                               shared memory, 2 = read ahead from global memory */
 } bte_solve_opts;
 
 typedef struct {

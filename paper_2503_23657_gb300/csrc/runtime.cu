@@ -307,7 +307,7 @@ bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw, int stage
 // Candidate tiles for a precision; kind_req 0 = any, 1 = general only,
 // 2 = row-block only, 3 = row-pipeline only.
 std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req = 0, int dw_req = 0,
-                                 int cw_req = 0) {
+                                 int cw_req = 0, int staging_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
     if (lz != 0 && (kind_req == 0 || kind_req == 1)) {
@@ -324,6 +324,7 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
     for (int c : p->groups_cnt) gmax = std::max(gmax, c);
     if (kind_req == 0 || kind_req == 3) {
         for (int stage : {1, 0}) {
+            if ((staging_req == 1 && !stage) || (staging_req == 2 && stage)) continue;
             for (int dw : {1, 2, 4, 8}) {
                 if (dw_req && dw != dw_req) continue;
                 for (int groups : {1, 2, 4, 8, 16}) {
@@ -356,12 +357,34 @@ Workspace<float> &ws_of<float>(bte_plan *p) { return p->ws32; }
 template <>
 Workspace<double> &ws_of<double>(bte_plan *p) { return p->ws64; }
 
+// Cell partial sets a tile writes (direct row-block tiles: one per warp).
+int cell_sets(int tid, int chunks) {
+    const Tile tl = tile_of(tid);
+    return (tl.kind == 1 || is_rowpipe(tl.kind)) ? chunks * (tl.cw / tl.dw) : chunks;
+}
+
 template <typename real>
 int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
     if (ws.dsub.count(tid)) return BTE_OK;
     const int cw = tile_of(tid).cw;  // directions per CTA (general kernel: cw == dw)
     auto f = make_subsets(p, cw, false);
     auto a = make_subsets(p, cw, true);
+    // partial sets and face sums of this tile; a buffer that moves invalidates
+    // the captured graphs (their kernel parameters hold the old address)
+    {
+        const size_t N = (size_t)p->N, B = p->B, F = std::max(p->F, 1);
+        const size_t chunks = f.size();
+        const size_t Spad = ((size_t)cell_sets(tid, (int)chunks) + 3) & ~(size_t)3;
+        void *part0 = ws.part.p, *fsum0 = ws.fsum.p;
+        CK(p, ws.part.ensure(sizeof(real) * Spad * B * N));
+        CK(p, ws.fsum.ensure(sizeof(real) * chunks * B * F));
+        if (ws.part.p != part0 || ws.fsum.p != fsum0) {
+            if (ws.graph) cudaGraphExecDestroy(ws.graph);
+            if (ws.agraph) cudaGraphExecDestroy(ws.agraph);
+            ws.graph = nullptr;
+            ws.agraph = nullptr;
+        }
+    }
     ws.subsets[tid] = {f, a};
     ws.subbufs.emplace_back(new DevBuf());
     DevBuf *bf = ws.subbufs.back().get();
@@ -373,25 +396,6 @@ int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
     return BTE_OK;
 }
 
-// Partial sets a tile can produce at most (general tiles >= 4 directions per
-// set; the row-block kernel down to 1 direction per set).
-int max_subsets(const bte_plan *p) {
-    int dummy = 0;
-    const bool rb = rowblock_ok(p, 4, &dummy) || rowblock_ok(p, 8, &dummy) || rowpipe_ok(p, 4, 1, 1) ||
-                    rowpipe_ok(p, 8, 1, 1);
-    const int per = rb ? 1 : 4;  // row kernels: one set per warp / group of >= 1 direction
-    int s = 0;
-    for (size_t g = 0; g < p->groups_cnt.size(); ++g) s += (p->groups_cnt[g] + per - 1) / per;
-    // a partly filled chunk still has all its warps' / groups' sets
-    if (rb) s += 32 * (int)p->groups_cnt.size();
-    return s;
-}
-
-// Cell partial sets a tile writes (direct row-block tiles: one per warp).
-int cell_sets(int tid, int chunks) {
-    const Tile tl = tile_of(tid);
-    return (tl.kind == 1 || is_rowpipe(tl.kind)) ? chunks * (tl.cw / tl.dw) : chunks;
-}
 
 // Per-solve tables (depend on tau overrides, wall temperatures, Q_amp, T_ref).
 template <typename real>
@@ -480,15 +484,12 @@ template <typename real>
 int ensure_workspace(bte_plan *p, Workspace<real> &ws) {
     if (ws.init) return BTE_OK;
     const size_t N = (size_t)p->N, B = p->B, F = std::max(p->F, 1);
-    const size_t S = max_subsets(p);
     for (int i = 0; i < 2; ++i) {
         CK(p, ws.tdev[i].ensure(sizeof(real) * (N + 16)));
         CK(p, ws.ein[i].ensure(sizeof(real) * B * F));
         CK(p, ws.T[i].ensure(sizeof(double) * N));
     }
-    const size_t Spad = (S + 3) & ~(size_t)3;
-    CK(p, ws.part.ensure(sizeof(real) * Spad * B * N));
-    CK(p, ws.fsum.ensure(sizeof(real) * S * B * F));
+    // the partial sets are sized by the tiles in use (ensure_subsets)
     std::vector<real> ph(N + 16, (real)0);
     for (size_t c = 0; c < N && !p->phi.empty(); ++c) ph[c] = (real)p->phi[c];
     CK(p, upload(ws.phi, ph));
@@ -796,10 +797,11 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     if ((rc = upload_tables(p, ws))) return rc;
     // tile: the caller's restriction, then the autotuned choice (cached)
     if (o->tile_kind < 0 || o->tile_kind > 3) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1, 2 or 3");
-    std::vector<int> cand =
-        tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane, o->dirs_per_cta);
+    if (o->source_staging < 0 || o->source_staging > 2) return fail(p, BTE_EINVAL, "source_staging must be 0, 1 or 2");
+    std::vector<int> cand = tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane, o->dirs_per_cta,
+                                            o->source_staging);
     if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
-    const int tkey = (o->tile_kind * 100 + o->dirs_per_lane) * 1000 + o->dirs_per_cta;
+    const int tkey = ((o->source_staging * 10 + o->tile_kind) * 100 + o->dirs_per_lane) * 1000 + o->dirs_per_cta;
     int tid;
     if (ws.tuned.count(tkey)) {
         tid = ws.tuned[tkey];
@@ -993,7 +995,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     if (int rc2 = ensure_subsets(p, ws, gtile)) return rc2;
     const long long N = p->N;
     const int B = p->B, F = std::max(p->F, 1);
-    const size_t S = max_subsets(p);
+    const size_t S = ws.subsets.at(gtile).first.size();  // the gradient pass: one set per chunk
     for (int i = 0; i < 2; ++i) {
         CK(p, ws.thdev[i].ensure(sizeof(real) * (N + 16)));
         CK(p, ws.mein[i].ensure(sizeof(real) * (size_t)B * F));
@@ -1350,7 +1352,14 @@ BatchState<double> &bstate_of<double>(bte_batch *bt) { return bt->bs64; }
 // instance needs the most shared memory).
 std::vector<int> batch_class_candidates(bte_batch *bt, const bte_batch::Cls &c, int real_bytes, int dw_req,
                                         int cw_req) {
-    return tile_candidates(bt->plans[bt->inst[c.begin]], real_bytes, 3, dw_req, cw_req);
+    std::vector<int> all = tile_candidates(bt->plans[bt->inst[c.begin]], real_bytes, 3, dw_req, cw_req);
+    if (dw_req) return all;
+    // one direction per warp is never the fastest with this much parallelism
+    // and needs the most partial sets per instance
+    std::vector<int> out;
+    for (int tid : all)
+        if (tile_of(tid).dw > 1) out.push_back(tid);
+    return out.empty() ? all : out;
 }
 
 template <typename real>
