@@ -50,7 +50,7 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
     real *s_srck = s_invd + P.R * DW;                                    // [R]
     const int nwarps = P.WY * P.WZ;
     real *s_y = s_srck + ((P.R + 1) & ~1);                               // [2][nwarps][LZ][DW]
-    real *s_z = s_y + 2 * nwarps * LZ * DW;                              // [2][nwarps][32][DW]
+    real *s_z = s_y + 2 * nwarps * LZ * DW;                              // [2][nwarps][DW][32] (lane fastest)
     real *s_ein = s_z + (Z ? 2 * nwarps * 32 * DW : 0);                  // [F] (ein_smem)
 
     const int s = blockIdx.x;
@@ -153,7 +153,7 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
                 real vz = real(0);
                 if (Z) {
                     if (l > 0) vz = old[l - 1][dd];
-                    else if (wz > 0) vz = s_z[((rb * nwarps + warp - P.WY) * 32 + lane) * DW + dd];
+                    else if (wz > 0) vz = s_z[((rb * nwarps + warp - P.WY) * DW + dd) * 32 + lane];
                 }
                 if (ADJ) {
                     vx = bx ? Ex * w[dd] : vx;
@@ -234,7 +234,7 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
         }
         if (Z) {
 #pragma unroll
-            for (int dd = 0; dd < DW; ++dd) s_z[((wb * nwarps + warp) * 32 + lane) * DW + dd] = old[LZ - 1][dd];
+            for (int dd = 0; dd < DW; ++dd) s_z[((wb * nwarps + warp) * DW + dd) * 32 + lane] = old[LZ - 1][dd];
         }
         __syncthreads();
     }
