@@ -113,10 +113,7 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
 # since the capture has no entry)
-NCU_TRAFFIC = {
-    # profiles/sweep2dp_square128.md: 179.7 KB read + 1.0 KB written (128 x 128 square, tile 3:4:4:1)
-    ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 180736,
-}
+NCU_TRAFFIC = {}
 
 
 def measured_hbm_peak():

@@ -64,6 +64,24 @@ struct SweepParams {
 // Parameters of the row-block sweep for unmasked 1D/2D grids with one region
 // (sweep2d.cuh).  One CTA per (direction chunk, band); a chunk holds up to
 // warps_per_cta * DW directions of one quadrant, DW per warp.
+//
+// Convergence bookkeeping of one source iteration (eps_T from the update's
+// block partials, iteration counter, history, flags).  With deferred
+// finalization the update only writes the block partials and sets *pending;
+// the next row-pipeline sweep (or the finalize kernel that closes a graph
+// replay) reduces them, records eps_T and decides whether to stop.
+struct FinalizeParams {
+    const double *blockpart;          // [nblocks] x {sum of squares, max}
+    int nblocks;
+    long long n_active;
+    double tol;
+    int *done, *iter, *status, *pending;
+    double *last;                     // {eps, xmax, ss}
+    double *eps_hist;                 // [max_hist] or null
+    int max_hist;
+    int *batch_done;                  // batched solves: instances converged so far (or null)
+};
+
 template <typename real>
 struct Sweep2DParams {
     int nx, ny;
@@ -92,6 +110,8 @@ struct Sweep2DParams {
     int stage;                        // stage per-cell inputs in shared memory (TMA bulk copy)
     int groups;                       // row-pipeline kernel: direction groups per CTA
     int adj;                          // row-pipeline kernel: 1 = adjoint sweep
+    FinalizeParams fin;               // row-pipeline kernel: finalize the previous iteration
+                                      // (fin.pending null: nothing to finalize)
 };
 
 template <typename real>
@@ -154,7 +174,14 @@ struct UpdateParams {
     int max_hist;
     int ignore_done;                  // final replay passes
     int *batch_done;                  // batched solves: instances converged so far (or null)
+    int defer;                        // 1: write the block partials, set *fin.pending, no ticket
+    FinalizeParams fin;               // (defer) where the partials go
 };
+
+// Finalize the pending iteration of one problem / every instance of a batch
+// (one warp each); used to close a graph replay under deferred finalization.
+template <typename real>
+cudaError_t launch_finalize(const UpdateParams<real> *params, int n, cudaStream_t st);
 
 // Launchers (sweep_*.cu / update.cu).  launch_sweep returns
 // cudaErrorInvalidConfiguration for a (dirs_per_lane, layers_per_lane, 3D)

@@ -63,7 +63,7 @@ struct Status {
     int done;
     int iter;
     int status;
-    int pad;
+    int pending;   // deferred finalization: the last update's residual is not yet reduced
     double last[3];
 };
 
@@ -81,6 +81,7 @@ struct Workspace {
     std::vector<std::unique_ptr<DevBuf>> subbufs;
     std::map<int, int> tuned;  // tile request -> chosen tile
     DevBuf wall;  // [6][wall_stride] face index of each wall position (-1: none)
+    DevBuf fin_fwd, fin_adj;  // UpdateParams<real> read by the finalize kernel (forward / adjoint)
     DevBuf gradpart;  // gradient reduction block partials
     // graph cache
     cudaGraphExec_t graph = nullptr;
@@ -536,6 +537,25 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int tid, bool a
     return sp;
 }
 
+// Convergence bookkeeping of the plan's solve (forward: with eps history).
+FinalizeParams fin_params(bte_plan *p, double tol, bool adj) {
+    FinalizeParams f{};
+    Status *st = p->d_status.as<Status>();
+    f.blockpart = p->d_blockpart.as<double>();
+    f.nblocks = (int)((p->N + 31) / 32);  // the update's cell blocks (32 cells each)
+    f.n_active = p->n_active;
+    f.tol = tol;
+    f.done = &st->done;
+    f.iter = &st->iter;
+    f.status = &st->status;
+    f.pending = &st->pending;
+    f.last = st->last;
+    f.eps_hist = adj ? nullptr : p->d_hist.as<double>();
+    f.max_hist = p->hist_cap;
+    f.batch_done = nullptr;
+    return f;
+}
+
 template <typename real>
 UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool adj, double tol) {
     UpdateParams<real> u{};
@@ -572,6 +592,9 @@ UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool
     u.max_hist = p->hist_cap;
     u.tol = tol;
     u.n_active = p->n_active;
+    // row-pipeline tiles finalize each iteration in the next sweep's prologue
+    u.defer = is_rowpipe(tile_of(tid).kind) ? 1 : 0;
+    u.fin = fin_params(p, tol, adj);
     return u;
 }
 
@@ -616,7 +639,8 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
 // One sweep (all bands x directions x cells) with the given tile.
 template <typename real>
 cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool adj, const real *tsrc,
-                              const real *ein, bool store_e, bool use_done, cudaStream_t stream) {
+                              const real *ein, bool store_e, bool use_done, cudaStream_t stream,
+                              const FinalizeParams *fin = nullptr) {
     const Tile tl = tile_of(tid);
     if (tl.kind >= 1) {
         Sweep2DParams<real> sp = sweep2d_params(p, ws, tid, adj);
@@ -625,6 +649,7 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
         sp.store_e = store_e ? 1 : 0;
         sp.e = ws.e.template as<real>();
         if (!use_done) sp.done = nullptr;
+        if (use_done && fin && is_rowpipe(tl.kind)) sp.fin = *fin;  // finalize the previous iteration
         if (is_rowpipe(tl.kind)) return launch_sweep2dp<real>(sp, tl.dw, stream);
         return launch_sweep2d<real>(sp, tl.dw, rowblock_rb(p), adj, stream);
     }
@@ -651,9 +676,10 @@ template <typename real>
 cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int tid, int parity, double tol, bool store_e,
                             bool replay, cudaStream_t stream, cudaEvent_t ta = nullptr, cudaEvent_t tb = nullptr) {
     cudaError_t e = ta ? record_timing_event(ta, stream) : cudaSuccess;
+    const FinalizeParams fin = fin_params(p, tol, false);
     if (e == cudaSuccess)
         e = launch_tile_sweep(p, ws, tid, false, ws.tdev[parity].template as<real>(), ws.ein[parity].template as<real>(),
-                              store_e, !replay, stream);
+                              store_e, !replay, stream, &fin);
     if (e == cudaSuccess && tb) e = record_timing_event(tb, stream);
     if (e != cudaSuccess || replay) return e;
     UpdateParams<real> u = update_params(p, ws, tid, false, tol);
@@ -826,6 +852,14 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     if (p->time_every) CK(p, ensure_timing_events(p, poll));
     // graph of `poll` iterations (even, so every replay starts at parity 0)
     auto key = std::make_tuple(dw, poll, tol, (store_every ? 1 : 0) | (p->time_every << 1));
+    // the finalize kernel that closes every replay / eager chunk (a no-op
+    // unless the tile defers finalization)
+    {
+        const UpdateParams<real> uf = update_params(p, ws, dw, false, tol);
+        CK(p, ws.fin_fwd.ensure(sizeof(UpdateParams<real>)));
+        CK(p, cudaMemcpy(ws.fin_fwd.p, &uf, sizeof(UpdateParams<real>), cudaMemcpyHostToDevice));
+    }
+    const UpdateParams<real> *fin_fwd = ws.fin_fwd.template as<UpdateParams<real>>();
     if (!ws.graph || ws.graph_key != key) {
         if (ws.graph) {
             cudaGraphExecDestroy(ws.graph);
@@ -837,6 +871,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         for (int i = 0; i < poll && ce == cudaSuccess; ++i)
             ce = enqueue_forward(p, ws, dw, i & 1, tol, store_every, false, cs, tev_a(p, i), tev_b(p, i));
+        if (ce == cudaSuccess) ce = launch_finalize<real>(fin_fwd, 1, cs);
         cudaError_t ce2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
         if (ce != cudaSuccess) return fail(p, BTE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -862,9 +897,10 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         } else {
             for (int i = 0; i < k; ++i)
                 CK(p, enqueue_forward(p, ws, dw, (enq + i) & 1, tol, store_every, false, stream, tev_a(p, i), tev_b(p, i)));
+            CK(p, launch_finalize<real>(fin_fwd, 1, stream));
         }
         enq += k;
-        launches += 2LL * k;
+        launches += 2LL * k + 1;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
         CK(p, cudaStreamSynchronize(stream));
         if (p->time_every) CK(p, sum_timing_events(p, k, &sweep_ms, &n_timed));
@@ -946,9 +982,10 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
                             cudaStream_t stream, cudaEvent_t ta = nullptr, cudaEvent_t tb = nullptr) {
     if (!final_pass) {
         cudaError_t e = ta ? record_timing_event(ta, stream) : cudaSuccess;
+        const FinalizeParams fin = fin_params(p, tol, true);
         if (e == cudaSuccess)
             e = launch_tile_sweep(p, ws, dw, true, ws.thdev[parity].template as<real>(), ws.mein[parity].template as<real>(),
-                                  false, true, stream);
+                                  false, true, stream, &fin);
         if (e == cudaSuccess && tb) e = record_timing_event(tb, stream);
         if (e != cudaSuccess) return e;
         UpdateParams<real> u = update_params(p, ws, dw, true, tol);
@@ -977,6 +1014,7 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
     u.ein_out = ws.mein[parity ^ 1].template as<real>();
     if (final_pass) {
         u.ignore_done = 1;
+        u.defer = 0;
         u.fsum_total = ws.msum.template as<double>();
     }
     return launch_update<real>(u, stream);
@@ -1046,6 +1084,12 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
     const int poll = 32;
     if (p->time_every) CK(p, ensure_timing_events(p, poll));
+    {
+        const UpdateParams<real> uf = update_params(p, ws, dw, true, tol);
+        CK(p, ws.fin_adj.ensure(sizeof(UpdateParams<real>)));
+        CK(p, cudaMemcpy(ws.fin_adj.p, &uf, sizeof(UpdateParams<real>), cudaMemcpyHostToDevice));
+    }
+    const UpdateParams<real> *fin_adj = ws.fin_adj.template as<UpdateParams<real>>();
     auto key = std::make_tuple(dw, poll, tol, p->time_every << 1);
     if (!ws.agraph || ws.agraph_key != key) {
         if (ws.agraph) {
@@ -1058,6 +1102,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         for (int i = 0; i < poll && ce == cudaSuccess; ++i)
             ce = enqueue_adjoint(p, ws, dw, i & 1, tol, false, cs, tev_a(p, i), tev_b(p, i));
+        if (ce == cudaSuccess) ce = launch_finalize<real>(fin_adj, 1, cs);
         cudaError_t ce2 = cudaStreamEndCapture(cs, &gr);
         cudaStreamDestroy(cs);
         if (ce != cudaSuccess || ce2 != cudaSuccess)
@@ -1077,12 +1122,13 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     CK(p, cudaEventRecord(p->ev0, stream));
     while (enq < max_iter) {
         const int k = std::min(poll, max_iter - enq);
-        launches += 2LL * k;
+        launches += 2LL * k + 1;
         if (k == poll) {
             CK(p, cudaGraphLaunch(ws.agraph, stream));
         } else {
             for (int i = 0; i < k; ++i)
                 CK(p, enqueue_adjoint(p, ws, dw, (enq + i) & 1, tol, false, stream, tev_a(p, i), tev_b(p, i)));
+            CK(p, launch_finalize<real>(fin_adj, 1, stream));
         }
         enq += k;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
@@ -1406,6 +1452,14 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 sp.e = nullptr;
                 sp.done = &st_all[i].done;
                 sp.status = &st_all[i].status;
+                FinalizeParams fin = fin_params(p, tol, false);
+                fin.done = &st_all[i].done;
+                fin.iter = &st_all[i].iter;
+                fin.status = &st_all[i].status;
+                fin.pending = &st_all[i].pending;
+                fin.last = st_all[i].last;
+                fin.batch_done = bt->d_done.as<int>();
+                sp.fin = fin;
                 sw[i] = sp;
                 UpdateParams<real> u = update_params(p, ws, tid, false, tol);
                 u.x_in = ws.T[par].template as<double>();
@@ -1417,6 +1471,8 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 u.status = &st_all[i].status;
                 u.last = st_all[i].last;
                 u.batch_done = bt->d_done.as<int>();
+                u.fin = sp.fin;
+                u.defer = 1;
                 up[i] = u;
             }
         }
@@ -1559,6 +1615,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         for (int i = 0; i < poll && ce == cudaSuccess; ++i)
             ce = batch_enqueue<real>(bt, bs, tiles, i & 1, cs, bt->time_sweeps && i == 0);
+        if (ce == cudaSuccess) ce = launch_finalize<real>(bs.update[0].template as<UpdateParams<real>>(), bt->n, cs);
         cudaError_t ce2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
         if (ce != cudaSuccess) return bfail(bt, BTE_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce));
@@ -1584,9 +1641,10 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
         } else {
             for (int i = 0; i < k; ++i)
                 BCK(bt, batch_enqueue<real>(bt, bs, tiles, (enq + i) & 1, stream, bt->time_sweeps && i == 0));
+            BCK(bt, launch_finalize<real>(bs.update[0].template as<UpdateParams<real>>(), bt->n, stream));
         }
         enq += k;
-        launches += (long long)k * (long long)(bt->classes.size() + 1);
+        launches += (long long)k * (long long)(bt->classes.size() + 1) + 1;
         BCK(bt, cudaMemcpyAsync(bt->h_done, bt->d_done.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
         BCK(bt, cudaStreamSynchronize(stream));
         if (bt->time_sweeps) {

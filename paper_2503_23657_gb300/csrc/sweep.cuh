@@ -43,7 +43,13 @@ struct SweepTile {
 template <typename real, int DW, int LZ, bool Z, bool ADJ>
 __global__ void __launch_bounds__(SweepTile<DW, LZ, Z>::kMaxThreads)
 sweep_kernel(const __grid_constant__ SweepParams<real> P) {
-    if (P.done != nullptr && *((volatile const int *)P.done) != 0) return;
+    {
+        // one thread reads the stop flag: every warp of the CTA decides alike
+        __shared__ int s_done;
+        if (threadIdx.x == 0) s_done = (P.done != nullptr && *((volatile const int *)P.done) != 0) ? 1 : 0;
+        __syncthreads();
+        if (s_done) return;
+    }
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *s_invd = reinterpret_cast<real *>(smem_raw);                 // [R][DW]

@@ -142,7 +142,13 @@ struct RowSweep {
 template <typename real, int DW, int RB, bool ADJ>
 __global__ void __launch_bounds__(Sweep2DTile<DW, RB>::kMaxThreads)
 sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
-    if (P.done != nullptr && *((volatile const int *)P.done) != 0) return;
+    {
+        // one thread reads the stop flag: every warp of the CTA decides alike
+        __shared__ int s_done;
+        if (threadIdx.x == 0) s_done = (P.done != nullptr && *((volatile const int *)P.done) != 0) ? 1 : 0;
+        __syncthreads();
+        if (s_done) return;
+    }
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     const int N = P.nx * P.ny;

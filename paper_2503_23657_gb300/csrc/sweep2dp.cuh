@@ -44,6 +44,7 @@
 #include <stdint.h>
 
 #include "bte_internal.cuh"
+#include "finalize.cuh"
 #include "tma.cuh"
 
 namespace bte {
@@ -66,10 +67,10 @@ constexpr int kPipeMaxThreads = 512;
 // One CTA's work: direction chunk s of band b of the problem P.
 template <typename real, int DW, int K, bool PHI, bool STORE_E, bool STAGE>
 __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, const int s, const int b) {
-    if (P.done != nullptr && *((volatile const int *)P.done) != 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_abort;
+    __shared__ int s_stop;
     const int nx = P.nx, ny = P.ny;
     const int N = nx * ny;
     const int Npad = (N + 15) & ~15;
@@ -96,12 +97,19 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
     const int X0 = negx ? nx - 1 : 0;
 
     // ---- prologue: TMA bulk copy of the per-cell inputs, wall values ----
+    // the stop flag may be set while this kernel runs (deferred finalization
+    // in CTA (0, 0)): one thread reads it, so every warp of the CTA takes
+    // the same decision (a warp that left early would stall the pipeline)
     if (threadIdx.x == 0) {
-        mbar_init(&s_bar, 1);
-        mbar_fence_init();
         s_abort = 0;
+        s_stop = (P.done != nullptr && *((volatile const int *)P.done) != 0) ? 1 : 0;
+        if (!s_stop) {
+            mbar_init(&s_bar, 1);
+            mbar_fence_init();
+        }
     }
     __syncthreads();
+    if (s_stop) return;
     if (STAGE && threadIdx.x == 0) {
         const uint32_t bytes = (uint32_t)(Npad * sizeof(real));
         mbar_arrive_expect_tx(&s_bar, PHI ? 2 * bytes : bytes);
@@ -187,6 +195,17 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
     const long long eoff = (long long)b * P.D + d0;
     const int BD = P.B * P.D;
 
+    // deferred finalization of the previous iteration: CTA (0, 0) records
+    // eps_T and the stop decision; its last pipeline warp does it, since that
+    // warp waits longest for its first columns anyway.  Nothing in this
+    // kernel waits for it: a stop found here ends the solve at the update
+    // that follows (which sees the flag), one sweep later.
+    if (s == 0 && b == 0 && warp == G * NRB - 1 && P.fin.pending != nullptr &&
+        *((volatile const int *)P.fin.pending) != 0) {
+        double eps, tmx, tss;
+        fin_reduce(P.fin, eps, tmx, tss);
+        if (lane == 0) fin_record(P.fin, eps, tmx, tss);
+    }
     // before its row enters the grid a lane holds the x-upwind wall value
     real old[DW];
     {

@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include "bte_internal.cuh"
+#include "finalize.cuh"
 
 namespace bte {
 
@@ -189,6 +190,16 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
         }
     }
     warp_reduce2(ss, mx);
+    if (P.defer) {
+        // deferred finalization: the block partials and the pending mark;
+        // the next row-pipeline sweep (or the finalize kernel) reduces them
+        if (tx == 0) {
+            P.blockpart[2 * cb] = ss;
+            P.blockpart[2 * cb + 1] = mx;
+            if (cb == 0) *P.fin.pending = 1;
+        }
+        return;
+    }
     if (tx == 0) {
         P.blockpart[2 * cb] = ss;
         P.blockpart[2 * cb + 1] = mx;
@@ -249,6 +260,24 @@ __global__ void __launch_bounds__(kUpdThreads, 4)
 update_batch_kernel(const UpdateParams<real> *__restrict__ params, const int2 *__restrict__ table) {
     const int2 e = table[blockIdx.x];
     update_body<real>(params[e.x], e.y);
+}
+
+// Close a graph replay / an eager chunk under deferred finalization: one
+// warp per problem reduces the pending block partials and records them.
+template <typename real>
+__global__ void __launch_bounds__(32) finalize_kernel(const UpdateParams<real> *__restrict__ params) {
+    const UpdateParams<real> &P = params[blockIdx.x];
+    if (!P.defer || P.fin.pending == nullptr || *((volatile const int *)P.fin.pending) == 0) return;
+    double eps, tmx, tss;
+    fin_reduce(P.fin, eps, tmx, tss);
+    if (threadIdx.x == 0) fin_record(P.fin, eps, tmx, tss);
+}
+
+template <typename real>
+cudaError_t launch_finalize(const UpdateParams<real> *params, int n, cudaStream_t st) {
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    finalize_kernel<real><<<n, 32, 0, st>>>(params);
+    return cudaGetLastError();
 }
 
 template <typename real>
@@ -419,6 +448,8 @@ cudaError_t launch_grad(const GradParams<real> &g, cudaStream_t st) {
 template cudaError_t launch_update<float>(const UpdateParams<float> &, cudaStream_t);
 template cudaError_t launch_update<double>(const UpdateParams<double> &, cudaStream_t);
 template cudaError_t launch_update_batch<float>(const UpdateParams<float> *, const int2 *, int, cudaStream_t);
+template cudaError_t launch_finalize<float>(const UpdateParams<float> *, int, cudaStream_t);
+template cudaError_t launch_finalize<double>(const UpdateParams<double> *, int, cudaStream_t);
 template cudaError_t launch_update_batch<double>(const UpdateParams<double> *, const int2 *, int, cudaStream_t);
 template cudaError_t launch_flux<float>(long long, int, int, const int2 *, const float *, const double *,
                                         const double *, double *, cudaStream_t);
