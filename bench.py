@@ -113,7 +113,10 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
 # since the capture has no entry)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/sweep2dp_square128.md: 202.2 KB read + 1.0 KB written (128 x 128 square, tile 3:4:4:1)
+    ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 203264,
+}
 
 
 def measured_hbm_peak():
