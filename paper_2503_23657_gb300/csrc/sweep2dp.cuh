@@ -97,6 +97,10 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
     const int X0 = negx ? nx - 1 : 0;
 
     // ---- prologue: TMA bulk copy of the per-cell inputs, wall values ----
+    // the next kernel may be launched now (it waits for this grid to finish);
+    // everything below reads what the previous kernel wrote
+    pdl_launch_dependents();
+    pdl_wait();
     // the stop flag may be set while this kernel runs (deferred finalization
     // in CTA (0, 0)): one thread reads it, so every warp of the CTA takes
     // the same decision (a warp that left early would stall the pipeline)
@@ -383,8 +387,7 @@ cudaError_t launch_sweep2dp_v(const Sweep2DParams<real> &p, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<dim3(p.S, p.B), threads, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(p.S, p.B), dim3(threads), smem, st, p);
 }
 
 template <typename real, int DW, int K, bool PHI, bool STAGE>

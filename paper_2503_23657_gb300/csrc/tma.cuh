@@ -55,4 +55,11 @@ __device__ __forceinline__ int ld_acquire_cta(const int *p) {
     return v;
 }
 
+// Programmatic dependent launch (sm_90+): let the next kernel in the stream
+// be launched while this one runs; wait until the previous kernel has
+// completed and its memory is visible.  Both are no-ops for a kernel launched
+// without programmatic serialization.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace bte

@@ -19,6 +19,7 @@
 
 #include "bte_internal.cuh"
 #include "finalize.cuh"
+#include "tma.cuh"
 
 namespace bte {
 
@@ -94,6 +95,9 @@ template <typename real>
 __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const int blk) {
     __shared__ double sband[kBandSlots][kCellsPerBlock];
     __shared__ int is_last;
+    // the next kernel may be launched now; wait for the sweep's results
+    pdl_launch_dependents();
+    pdl_wait();
     const int face_blocks = update_face_blocks(P.F, P.B);
     const int cell_blocks = update_cell_blocks(P.N);
     if (blk < face_blocks) {
@@ -283,8 +287,7 @@ cudaError_t launch_finalize(const UpdateParams<real> *params, int n, cudaStream_
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st) {
     const int blocks = update_face_blocks(p.F, p.B) + update_cell_blocks(p.N);
-    update_kernel<real><<<blocks, kUpdThreads, 0, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(update_kernel<real>, dim3(blocks), dim3(kUpdThreads), 0, st, p);
 }
 
 template <typename real>
