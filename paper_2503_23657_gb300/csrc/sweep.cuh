@@ -125,12 +125,17 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
             const bool inr = ((unsigned)x < (unsigned)P.nx) && (j < P.ny) && (k < P.nz);
             long long c = 0;
             int2 ci = make_int2(0, 0);
+            real tsv = real(0), phv = real(0);
             if (inr) {
                 const int X = nx_ ? P.nx - 1 - x : x;
                 const int Y = ny_ ? P.ny - 1 - j : j;
                 const int Zc = nz_ ? P.nz - 1 - k : k;
                 c = X + (long long)P.nx * (Y + (long long)P.ny * Zc);
+                // independent loads issued together (the source does not wait
+                // for the cell record)
                 ci = P.cell[c];
+                tsv = ldg(P.tsrc + c);
+                if (!ADJ && P.phi != nullptr) phv = ldg(P.phi + c);
             }
             const int region = ci.y & kRegionMask;
             const bool act = inr && (region != 0);
@@ -145,9 +150,9 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
             real base = real(0);
             real thc = real(0);
             if (act) {
-                thc = P.tsrc[c];
+                thc = tsv;
                 base = thc * s_srck[region - 1];
-                if (!ADJ && P.phi != nullptr) base += P.phi[c] * qb;
+                if (!ADJ && P.phi != nullptr) base += phv * qb;
             }
             const real *invd = s_invd + (act ? region - 1 : 0) * DW;
             real acc = real(0);
