@@ -95,3 +95,29 @@ def test_single_cell(bte, dim):
     rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=1e-13, max_iter=100000)
     assert st["iterations"] == ref["iters"]
     assert rel(T, ref["T"]) < 1e-12
+
+
+def test_finfet_reduced_adjoint_vs_oracle(bte):
+    """The inverse problem's gradients (config 5 geometry at 1/8 scale: two
+    regions, mask, source, 16 directions): GPU adjoint against the oracle's
+    own FP64 adjoint of the same converged state, FP64 and FP32 sweeps."""
+    p = bi.finfet_3d(scale=8, n_polar=2, n_az=8)
+    ref = oracle.solve(p, max_iter=100000, tol=1e-12)
+    rng = np.random.default_rng(5)
+    probes = np.asarray(p.probes)
+    T_obs = ref["T"][probes] + rng.uniform(-0.5, 0.5, probes.size)
+    g = np.zeros(p.n_cells)
+    np.add.at(g, probes, ref["T"][probes] - T_obs)
+    adj = oracle.adjoint(p, ref["e"], ref["T"], g, max_iter=100000, tol=1e-12)
+    plan = bte.Plan(p)
+    T = np.zeros(p.n_cells)
+    rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=1e-12, max_iter=100000)
+    rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g, tol=1e-12, max_iter=100000)
+    np.testing.assert_allclose(g_tau, adj["g_tau"], rtol=1e-8, atol=1e-8 * np.abs(adj["g_tau"]).max())
+    np.testing.assert_allclose(g_Tw, adj["g_Tw"], rtol=1e-8, atol=1e-8 * np.abs(adj["g_Tw"]).max())
+    assert g_Q == pytest.approx(adj["g_Q"], rel=1e-8)
+    rc, st = plan.solve(T, precision=bte.BTE_FP32, tol=1e-9, max_iter=100000, check=False)
+    rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g, tol=1e-9, max_iter=100000, check=False)
+    np.testing.assert_allclose(g_tau, adj["g_tau"], rtol=1e-3, atol=1e-3 * np.abs(adj["g_tau"]).max())
+    np.testing.assert_allclose(g_Tw, adj["g_Tw"], rtol=1e-3, atol=1e-3 * np.abs(adj["g_Tw"]).max())
+    assert g_Q == pytest.approx(adj["g_Q"], rel=1e-3)
