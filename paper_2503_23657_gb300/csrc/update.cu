@@ -25,31 +25,6 @@ namespace bte {
 
 constexpr int kUpdThreads = 256;
 
-__device__ __forceinline__ void block_reduce2(double &a, double &m, double *sh) {
-    // sum of a, max of m over the block (kUpdThreads threads)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        sh[2 * warp] = a;
-        sh[2 * warp + 1] = m;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        a = lane < nw ? sh[2 * lane] : 0.0;
-        m = lane < nw ? sh[2 * lane + 1] : -INFINITY;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-        }
-    }
-}
-
 // Sum of the S partial sets of one (band, cell); sets are N apart
 // ([B][Spad][N] layout), so a warp's loads of one set are coalesced; eight
 // independent loads are in flight, summed in a fixed order in the sweep
@@ -64,15 +39,6 @@ __device__ __forceinline__ real sum_sets(const real *pp, int S, long long N) {
     }
     for (int q = 0; s < S; ++s, ++q) a[q] += pp[(long long)s * N];
     return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-}
-
-// Sum and max over one warp (fixed shuffle tree: deterministic).
-__device__ __forceinline__ void warp_reduce2(double &a, double &m) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    }
 }
 
 // Face blocks come first (they start with the cell blocks instead of after
@@ -193,7 +159,7 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
             P.xdev_out[c] = (real)0;
         }
     }
-    warp_reduce2(ss, mx);
+    fin_warp_reduce(ss, mx);
     if (P.defer) {
         // deferred finalization: the block partials and the pending mark;
         // the next row-pipeline sweep (or the finalize kernel) reduces them
@@ -214,28 +180,12 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
     __syncwarp();
     if (!is_last) return;
     __threadfence();
-    // last cell block, warp 0: every lane sums a fixed, strided slice of the
-    // block partials (loads issued sixteen at a time, summed in slice order),
-    // then the fixed shuffle tree -> deterministic result
-    double tss = 0.0, tmx = -INFINITY;
-    for (int i0 = tx; i0 < cell_blocks; i0 += 32 * 16) {
-        double2 v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int i = i0 + 32 * q;
-            v[q] = i < cell_blocks ? __ldcg(reinterpret_cast<const double2 *>(P.blockpart) + i)
-                                   : make_double2(0.0, -INFINITY);
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            tss += v[q].x;
-            tmx = fmax(tmx, v[q].y);
-        }
-    }
-    warp_reduce2(tss, tmx);
+    // last cell block, warp 0: the deterministic reduction of the block
+    // partials (fixed slices, fixed shuffle tree)
+    double eps, tmx, tss;
+    fin_reduce(P.fin, eps, tmx, tss);
     if (tx == 0) {
         *P.counter = 0u;
-        const double eps = (tmx > 0.0) ? sqrt(tss / (double)P.n_active) / tmx : 0.0;
         const int it = it_prev;
         if (P.eps_hist && it < P.max_hist) P.eps_hist[it] = eps;
         P.last[0] = eps;
