@@ -325,11 +325,14 @@ def timed_steps(ctx, step, flush):
 
 
 def aggregate(ctx, units, t_total):
+    """Whole-job numbers over the replicas: units summed over ranks, time the
+    slowest rank's."""
     torch, ws, dist = ctx["torch"], ctx["ws"], ctx["dist"]
     if ws > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        uu = torch.tensor([units], dtype=torch.float64, device="cuda")
+        uu = torch.tensor([units], dtype=torch.float64, device=dev)
         dist.all_reduce(uu, op=dist.ReduceOp.SUM)
         return float(uu), float(tt)
     return units, t_total
