@@ -114,8 +114,8 @@ class ClockSampler:
 # capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
 # since the capture has no entry)
 NCU_TRAFFIC = {
-    # profiles/sweep2dp_square128.md: 202.2 KB read + 1.0 KB written (128 x 128 square, tile 3:4:4:1)
-    ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 203264,
+    # profiles/sweep2dp_square128.md: 202.2 KB read + 1.5 KB written (128 x 128 square, tile 3:4:4:1)
+    ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 203776,
 }
 
 
@@ -142,6 +142,8 @@ def sweep_kernel_name(p, st):
     names it."""
     dw = st["dirs_per_lane"]
     phi = 0 if p.phi is None or p.Q_amp == 0.0 else 1
+    if st["tile_kind"] == 3 and p.dim == 3:
+        return f"sweep3dp_kernel<float, {dw}, {phi}, 0>"
     if st["tile_kind"] == 3:
         return f"sweep2dp_kernel<float, {dw}, 8, {phi}, 0, {st['source_staged']}>"
     if st["tile_kind"] == 2:
@@ -247,7 +249,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     ap.add_argument("--store-e-every-iter", action="store_true")
     ap.add_argument("--tile", default="0:0:0:0",
-                    help="sweep tile kind:dirs_per_lane:dirs_per_cta:source_staging (0:0:0:0 = autotuned); "
+                    help="sweep tile kind:dirs_per_lane:dirs_per_cta:source_staging[:warps_z] "
+                         "(0:0:0:0 = autotuned; warps_z: the 3D plane-pipeline kernel's warps along z); "
                          "profiling runs pin the tile the autotuner chose, since timings under a profiler are "
                          "not representative")
     args = ap.parse_args()
@@ -364,12 +367,13 @@ def run_single(p, ctx):
     g = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     per_update = p.n_active * p.B * p.D
-    tile_kind, tile_dw, tile_cw, tile_st = ((int(x) for x in (args.tile + ":0:0:0:0").split(":")[:4]))
+    tile_kind, tile_dw, tile_cw, tile_st, tile_wz = ((int(x) for x in (args.tile + ":0:0:0:0:0").split(":")[:5]))
 
     def step():
         rc, sf = plan.solve(T, precision=prec, tol=tol, max_iter=100000, stream=sp,
                             store_e_every_iter=args.store_e_every_iter, tile_kind=tile_kind,
-                            dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st)
+                            dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st,
+                            warps_z=tile_wz)
         sa = None
         if ctx["with_adj"]:
             g.zero_()
@@ -412,6 +416,8 @@ def run_single(p, ctx):
     sweep_ms = (fwd_sweep_s + adj_sweep_s) / max(fwd_sweeps + adj_sweeps, 1) * 1e3
     dw = fstats[-1]["dirs_per_lane"]
     tile = f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}:{2 - fstats[-1]['source_staged']}"
+    if fstats[-1]["warps_z"]:
+        tile += f":{fstats[-1]['warps_z']}"
     kernel = sweep_kernel_name(p, fstats[-1])
     roofline = roofline_object(kernel, tile, sweep_ms, per_update, p.B, p.D, {
         "sweep_launches_timed": fwd_sweeps + adj_sweeps,
@@ -430,7 +436,8 @@ def run_single(p, ctx):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc, sf = plan.solve(T_h, T_init=T_init_h, precision=prec, tol=tol, max_iter=100000, stream=sp,
-                            tile_kind=tile_kind, dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st)
+                            tile_kind=tile_kind, dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st,
+                            warps_z=tile_wz)
         u = sf["iterations"] * per_update
         if ctx["with_adj"]:
             g_h.zero_()

@@ -134,10 +134,14 @@ typedef struct {
     int store_e_every_iter; /* 1: write e to HBM on every sweep; 0: only the final one */
     int tile_kind;          /* 0 = autotuned; 1 = general wavefront kernel (any grid);
                                2 = row-block kernel (unmasked 1D/2D, one region);
-                               3 = row-pipeline kernel (unmasked 1D/2D, one region) */
+                               3 = row-pipeline kernel (unmasked 1D/2D, one region; on 3D
+                                   grids the plane-pipeline kernel: masks and several
+                                   regions allowed, FP32 only) */
     int dirs_per_cta;       /* row kernels: directions per CTA (0 = autotuned) */
     int source_staging;     /* row-pipeline kernel: 0 = autotuned, 1 = per-cell source staged in
                                shared memory, 2 = read ahead from global memory */
+    int warps_z;            /* 3D plane-pipeline kernel: warps along z per CTA (planes in
+                               flight per pass); 0 = autotuned */
 } bte_solve_opts;
 
 typedef struct {
@@ -157,6 +161,7 @@ typedef struct {
     long long sweep_launches; /* number of sweep launches summed in sweep_seconds */
     int source_staged;      /* row-pipeline tile: 1 = per-cell source staged in shared memory,
                                0 = read ahead from global memory (other kernels: 1) */
+    int warps_z;            /* 3D plane-pipeline tile: warps along z per CTA (other kernels: 0) */
 } bte_stats;
 
 /* Fill opts with defaults: FP32, tol 1e-6, max_iter 100000, T_init 300 K,

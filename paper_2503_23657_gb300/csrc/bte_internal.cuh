@@ -43,6 +43,25 @@ __host__ __device__ inline int face_of(int base, int flags, int side) {
     return base + __builtin_popcount(bm & ((1u << side) - 1u));
 }
 
+// Diagonal-skewed copy of a per-cell field (plane-pipeline 3D sweep).  A warp
+// of that sweep updates, at one step, one cell of each of its 32 rows, on a
+// diagonal of the (x, y) plane whose direction depends on the octant: X + Y
+// constant when the sweep runs along x and y in the same sense, X - Y
+// constant otherwise.  Family 0 keys a cell (X, Y, Z) by X + Y, family 1 by
+// X + (ny - 1 - Y); rows are innermost, so those 32 cells are 32 consecutive
+// entries of one family.  Entries that are no cell (X outside the grid)
+// hold zero.
+struct SkewLayout {
+    int nx, ny;
+    int nd;          // nx + ny - 1 diagonals per plane
+    int nyp;         // entries per diagonal (ny rounded up to 32)
+    long long fam;   // entries of one family (nz * nd * nyp)
+};
+__host__ __device__ inline long long skew_index(const SkewLayout &L, int f, int X, int Y, int Z) {
+    const int key = f ? X + (L.ny - 1 - Y) : X + Y;
+    return f * L.fam + ((long long)Z * L.nd + key) * L.nyp + Y;
+}
+
 // A subset of directions that share one sweep orientation (the signs of the
 // resolved components of s), processed by one CTA per band.
 struct Subset {
@@ -156,6 +175,42 @@ template <typename real>
 cudaError_t launch_sweep2dp_batch(const Sweep2DBatch<real> &bt, int dirs_per_warp, cudaStream_t st);
 size_t sweep2dp_smem(int nx, int ny, int with_phi, int groups, int dw, int stage, int real_bytes);
 
+// Parameters of the plane-pipeline 3D sweep (sweep3dp.cuh): masked grids,
+// any number of regions.  One CTA per (direction subset, band); WY warps
+// along y (32 rows each) times H warps along z, every warp one plane of a
+// pass of H planes.
+template <typename real>
+struct Sweep3DParams {
+    int nx, ny, nz;
+    int B, D, F, S, R;                // S = direction subsets (cell and face-sum sets)
+    int Spad;                         // S rounded up to a multiple of 4
+    int WY, H;                        // warps along y, warps along z
+    long long N;
+    SkewLayout skew;                  // layout of the three skewed per-cell inputs
+    const int2 *__restrict__ cell;    // skewed {face base, flags}
+    const real *__restrict__ tsrc;    // skewed fwd: T - T_ref; adj: Theta
+    const real *__restrict__ phi;     // skewed fwd source profile, or null
+    const real *__restrict__ ein;     // [B][F] boundary values
+    real *__restrict__ part;          // [B][Spad][N]
+    real *__restrict__ fsum;          // [S][B][F]
+    real *__restrict__ e;             // [N][B][D] (store_e)
+    real *__restrict__ wrap;          // [S][B][nx][WY*32][DW] top plane of a pass, read by the next pass
+    const Subset *__restrict__ sub;   // [S]
+    const real *__restrict__ coef;    // [B][D][8]
+    const real *__restrict__ invdiag; // [R][B][D]
+    const real *__restrict__ srck;    // [R][B] fwd C_b/(4 pi tau_rb); adj 1/tau_rb
+    const real *__restrict__ qb;      // [B]
+    const int *__restrict__ done;
+    int store_e;
+    int adj;                          // 1: adjoint sweep (carries nu = mu / w)
+    FinalizeParams fin;               // finalize the previous iteration (fin.pending null: nothing)
+};
+
+template <typename real>
+cudaError_t launch_sweep3dp(const Sweep3DParams<real> &p, int dirs_per_lane, cudaStream_t st);
+size_t sweep3dp_smem(int R, int WY, int H, int dw, int real_bytes);
+constexpr int kPipe3Chunk = 4;        // steps between the CTA barriers of the 3D pipeline
+
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.
 template <typename real>
 struct UpdateParams {
@@ -172,6 +227,8 @@ struct UpdateParams {
     const double *__restrict__ x_in;  // fwd T_old / adj Theta_old [N]
     double *__restrict__ x_out;       // [N]
     real *__restrict__ xdev_out;      // fwd T - T_ref / adj Theta, as real [N]
+    real *__restrict__ xskew_out;     // the same in the skewed layout (both families), or null
+    SkewLayout skew;
     const double *__restrict__ g;     // adj: dJ/dT [N]
     const double *__restrict__ wgt;   // [R][B] fwd 1/tau_rb ; adj C_b/(4 pi tau_rb)
     const double *__restrict__ Kinv;  // [R]   1 / sum_b C_b/tau_rb
@@ -216,6 +273,9 @@ int sweep_max_threads(int dirs_per_lane, int layers_per_lane, bool three_d);
 
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st);
+// natural-order per-cell field -> skewed layout (both families)
+template <typename T>
+cudaError_t launch_skew(long long N, const SkewLayout &L, const T *src, T *dst, cudaStream_t st);
 // batched update: table[i] = {instance, block of that instance}, `blocks` entries
 template <typename real>
 cudaError_t launch_update_batch(const UpdateParams<real> *params, const int2 *table, int blocks, cudaStream_t st);

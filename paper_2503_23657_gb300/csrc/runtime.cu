@@ -83,6 +83,12 @@ struct Workspace {
     DevBuf wall;  // [6][wall_stride] face index of each wall position (-1: none)
     DevBuf fin_fwd, fin_adj;  // UpdateParams<real> read by the finalize kernel (forward / adjoint)
     DevBuf gradpart;  // gradient reduction block partials
+    DevBuf wrap;      // plane-pipeline 3D sweep: last plane of a pass, per CTA
+    // plane-pipeline 3D sweep: skewed copies of the cell records, the source
+    // profile and the forward / adjoint sweep sources (both parities)
+    DevBuf skc, skphi, skt[2], ska[2];
+    SkewLayout skew{};
+    bool skew_ready = false;
     // graph cache
     cudaGraphExec_t graph = nullptr;
     std::tuple<int, int, double, int> graph_key{-1, -1, 0.0, -1};
@@ -238,7 +244,8 @@ long long cell_index(const bte_plan *p, int i, int j, int k) { return i + (long 
 // kernel with one partial set per direction group and the per-cell source
 // staged in shared memory, 4 = the same kernel reading the source ahead from
 // global memory), directions per lane/warp (dw) and directions per CTA chunk
-// (cw).
+// (cw).  Kind 5 is the plane-pipeline 3D kernel (masked grids): one subset
+// of dw directions per CTA, and the cw field holds its warps along z.
 struct Tile {
     int kind, dw, cw;
 };
@@ -247,6 +254,12 @@ inline Tile tile_of(int id) { return Tile{id / 100000, id % 100, (id / 100) % 10
 // the bte_solve_opts.tile_kind value of an internal kernel kind
 inline int abi_kind(int kind) { return kind == 0 ? 1 : (kind >= 3 ? 3 : 2); }
 inline bool is_rowpipe(int kind) { return kind == 3 || kind == 4; }
+inline bool is_pipe3(int kind) { return kind == 5; }
+// kernels that finalize each iteration in the next sweep's prologue
+inline bool defers_finalize(int kind) { return is_rowpipe(kind) || is_pipe3(kind); }
+// directions one CTA handles
+inline int tile_cta_dirs(const Tile &t) { return is_pipe3(t.kind) ? t.dw : t.cw; }
+inline int source_staged_kind(int kind) { return (kind == 4 || kind == 5) ? 0 : 1; }
 
 // Directions of one orientation group split into subsets of at most dw.
 std::vector<Subset> make_subsets(const bte_plan *p, int dw, bool flip) {
@@ -305,10 +318,48 @@ bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw, int stage
     return sweep2dp_smem(p->nx, p->ny, p->phi.empty() ? 0 : 1, groups, dw, stage, real_bytes) <= 200 * 1024;
 }
 
+// Plane-pipeline 3D kernel: 3D grid (masks and regions allowed), FP32,
+// ceil(ny / 32) warps along y times H along z (at most 16 warps); a grid of
+// more than H planes streams in passes, which needs two warps along z and
+// nx >= 4 H + 2 (the next pass reads the last plane of the previous one two
+// steps ahead, a chunk after it was written).
+bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H) {
+    if (p->dim != 3 || real_bytes != 4 || H < 1) return false;
+    if (p->N >= (1LL << 31) - 1) return false;
+    const long long skew_entries = 2LL * p->nz * (p->nx + p->ny - 1) * (((p->ny + 31) / 32) * 32);
+    if (skew_entries >= (1LL << 31) - 1) return false;
+    const int WY = (p->ny + 31) / 32;
+    if (WY * H > 16 || H > p->nz) return false;
+    const int M = (p->nz + H - 1) / H;
+    if (M > 1 && (H < 2 || p->nx < kPipe3Chunk * H + 2)) return false;
+    return sweep3dp_smem(p->R, WY, H, dw, real_bytes) <= 225 * 1024;
+}
+
+// Warps along z offered for the plane-pipeline kernel: the most that fit,
+// and about half of that (two CTAs per SM).
+std::vector<int> pipe3_heights(const bte_plan *p, int real_bytes, int dw) {
+    std::vector<int> out;
+    const int WY = (p->ny + 31) / 32;
+    int hmax = 0;
+    for (int H = std::min(16 / std::max(WY, 1), p->nz); H >= 1; --H)
+        if (pipe3_ok(p, real_bytes, dw, H)) {
+            hmax = H;
+            break;
+        }
+    if (hmax == 0) return out;
+    out.push_back(hmax);
+    for (int H = (hmax + 1) / 2; H >= 1 && H < hmax; --H)
+        if (pipe3_ok(p, real_bytes, dw, H)) {
+            out.push_back(H);
+            break;
+        }
+    return out;
+}
+
 // Candidate tiles for a precision; kind_req 0 = any, 1 = general only,
 // 2 = row-block only, 3 = row-pipeline only.
 std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req = 0, int dw_req = 0,
-                                 int cw_req = 0, int staging_req = 0) {
+                                 int cw_req = 0, int staging_req = 0, int wz_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
     if (lz != 0 && (kind_req == 0 || kind_req == 1)) {
@@ -335,6 +386,16 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
                     out.push_back(tile_id(stage ? 3 : 4, dw, dw * groups));
                 }
             }
+        }
+    }
+    if ((kind_req == 0 || kind_req == 3) && staging_req != 1) {
+        for (int dw : {2, 4, 8}) {
+            if ((dw_req && dw != dw_req) || (cw_req && dw != cw_req)) continue;
+            if (wz_req) {
+                if (pipe3_ok(p, real_bytes, dw, wz_req)) out.push_back(tile_id(5, dw, wz_req));
+                continue;
+            }
+            for (int H : pipe3_heights(p, real_bytes, dw)) out.push_back(tile_id(5, dw, H));
         }
     }
     if ((kind_req == 0 || kind_req == 2) && rowblock_ok(p, real_bytes, &stage)) {
@@ -364,10 +425,54 @@ int cell_sets(int tid, int chunks) {
     return (tl.kind == 1 || is_rowpipe(tl.kind)) ? chunks * (tl.cw / tl.dw) : chunks;
 }
 
+// Skewed per-cell inputs of the plane-pipeline 3D sweep (built once per plan
+// and precision; the sweep sources follow every update).
+template <typename real>
+int ensure_skew(bte_plan *p, Workspace<real> &ws) {
+    if (ws.skew_ready) return BTE_OK;
+    SkewLayout L{};
+    L.nx = p->nx;
+    L.ny = p->ny;
+    L.nd = p->nx + p->ny - 1;
+    L.nyp = ((p->ny + 31) / 32) * 32;
+    L.fam = (long long)p->nz * L.nd * L.nyp;
+    const size_t n = 2 * (size_t)L.fam;
+    CK(p, ws.skc.ensure(sizeof(int2) * n));
+    CK(p, cudaMemset(ws.skc.p, 0, sizeof(int2) * n));
+    CK(p, ws.skphi.ensure(sizeof(real) * n));
+    CK(p, cudaMemset(ws.skphi.p, 0, sizeof(real) * n));
+    for (int i = 0; i < 2; ++i) {
+        CK(p, ws.skt[i].ensure(sizeof(real) * n));
+        CK(p, cudaMemset(ws.skt[i].p, 0, sizeof(real) * n));
+        CK(p, ws.ska[i].ensure(sizeof(real) * n));
+        CK(p, cudaMemset(ws.ska[i].p, 0, sizeof(real) * n));
+    }
+    CK(p, launch_skew<int2>(p->N, L, p->d_cell.as<int2>(), ws.skc.template as<int2>(), 0));
+    CK(p, launch_skew<real>(p->N, L, ws.phi.template as<real>(), ws.skphi.template as<real>(), 0));
+    for (int i = 0; i < 2; ++i)
+        CK(p, launch_skew<real>(p->N, L, ws.tdev[i].template as<real>(), ws.skt[i].template as<real>(), 0));
+    CK(p, cudaDeviceSynchronize());
+    ws.skew = L;
+    ws.skew_ready = true;
+    return BTE_OK;
+}
+
+// skewed copy of a natural-order sweep source of the workspace
+template <typename real>
+const real *skewed_source(Workspace<real> &ws, const real *tsrc) {
+    for (int i = 0; i < 2; ++i) {
+        if (tsrc == ws.tdev[i].template as<real>()) return ws.skt[i].template as<real>();
+        if (tsrc == ws.thdev[i].template as<real>()) return ws.ska[i].template as<real>();
+    }
+    return nullptr;
+}
+
 template <typename real>
 int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
     if (ws.dsub.count(tid)) return BTE_OK;
-    const int cw = tile_of(tid).cw;  // directions per CTA (general kernel: cw == dw)
+    if (is_pipe3(tile_of(tid).kind))
+        if (int rc = ensure_skew(p, ws)) return rc;
+    const int cw = tile_cta_dirs(tile_of(tid));  // directions per CTA (general kernel: cw == dw)
     auto f = make_subsets(p, cw, false);
     auto a = make_subsets(p, cw, true);
     // partial sets and face sums of this tile; a buffer that moves invalidates
@@ -376,10 +481,15 @@ int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
         const size_t N = (size_t)p->N, B = p->B, F = std::max(p->F, 1);
         const size_t chunks = f.size();
         const size_t Spad = ((size_t)cell_sets(tid, (int)chunks) + 3) & ~(size_t)3;
-        void *part0 = ws.part.p, *fsum0 = ws.fsum.p;
+        void *part0 = ws.part.p, *fsum0 = ws.fsum.p, *wrap0 = ws.wrap.p;
         CK(p, ws.part.ensure(sizeof(real) * Spad * B * N));
         CK(p, ws.fsum.ensure(sizeof(real) * chunks * B * F));
-        if (ws.part.p != part0 || ws.fsum.p != fsum0) {
+        const Tile tl = tile_of(tid);
+        if (is_pipe3(tl.kind) && (p->nz + tl.cw - 1) / tl.cw > 1) {
+            const size_t ld = (size_t)((p->ny + 31) / 32) * 32;
+            CK(p, ws.wrap.ensure(sizeof(real) * chunks * B * (size_t)p->nx * ld * tl.dw));
+        }
+        if (ws.part.p != part0 || ws.fsum.p != fsum0 || ws.wrap.p != wrap0) {
             if (ws.graph) cudaGraphExecDestroy(ws.graph);
             if (ws.agraph) cudaGraphExecDestroy(ws.agraph);
             ws.graph = nullptr;
@@ -593,7 +703,8 @@ UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool
     u.tol = tol;
     u.n_active = p->n_active;
     // row-pipeline tiles finalize each iteration in the next sweep's prologue
-    u.defer = is_rowpipe(tile_of(tid).kind) ? 1 : 0;
+    u.defer = defers_finalize(tile_of(tid).kind) ? 1 : 0;
+    u.skew = ws.skew;
     u.fin = fin_params(p, tol, adj);
     return u;
 }
@@ -636,12 +747,56 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     return sp;
 }
 
+template <typename real>
+Sweep3DParams<real> sweep3d_params(bte_plan *p, Workspace<real> &ws, int tid, bool adj) {
+    const Tile tl = tile_of(tid);
+    Sweep3DParams<real> sp{};
+    sp.nx = p->nx;
+    sp.ny = p->ny;
+    sp.nz = p->nz;
+    sp.B = p->B;
+    sp.D = p->D;
+    sp.F = std::max(p->F, 1);
+    sp.S = (int)ws.subsets.at(tid).first.size();
+    sp.R = p->R;
+    sp.Spad = (cell_sets(tid, sp.S) + 3) & ~3;
+    sp.WY = (p->ny + 31) / 32;
+    sp.H = tl.cw;
+    sp.N = p->N;
+    sp.skew = ws.skew;
+    sp.cell = ws.skc.template as<int2>();
+    sp.phi = p->phi.empty() ? nullptr : ws.skphi.template as<real>();
+    sp.part = ws.part.template as<real>();
+    sp.fsum = ws.fsum.template as<real>();
+    sp.e = ws.e.template as<real>();
+    sp.wrap = ws.wrap.template as<real>();
+    auto pr = ws.dsub.at(tid);
+    sp.sub = (adj ? pr.second : pr.first)->template as<Subset>();
+    sp.coef = ws.coef.template as<real>();
+    sp.invdiag = ws.invdiag.template as<real>();
+    sp.srck = adj ? ws.srck_a.template as<real>() : ws.srck_f.template as<real>();
+    sp.qb = ws.qb.template as<real>();
+    sp.done = p->d_status.as<int>();
+    sp.adj = adj ? 1 : 0;
+    return sp;
+}
+
 // One sweep (all bands x directions x cells) with the given tile.
 template <typename real>
 cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool adj, const real *tsrc,
                               const real *ein, bool store_e, bool use_done, cudaStream_t stream,
                               const FinalizeParams *fin = nullptr) {
     const Tile tl = tile_of(tid);
+    if (is_pipe3(tl.kind)) {
+        Sweep3DParams<real> sp = sweep3d_params(p, ws, tid, adj);
+        sp.tsrc = skewed_source(ws, tsrc);
+        if (!sp.tsrc) return cudaErrorInvalidValue;
+        sp.ein = ein;
+        sp.store_e = store_e ? 1 : 0;
+        if (!use_done) sp.done = nullptr;
+        if (use_done && fin) sp.fin = *fin;  // finalize the previous iteration
+        return launch_sweep3dp<real>(sp, tl.dw, stream);
+    }
     if (tl.kind >= 1) {
         Sweep2DParams<real> sp = sweep2d_params(p, ws, tid, adj);
         sp.tsrc = tsrc;
@@ -686,6 +841,7 @@ cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int tid, int parit
     u.x_in = ws.T[parity].template as<double>();
     u.x_out = ws.T[parity ^ 1].template as<double>();
     u.xdev_out = ws.tdev[parity ^ 1].template as<real>();
+    if (is_pipe3(tile_of(tid).kind)) u.xskew_out = ws.skt[parity ^ 1].template as<real>();
     u.ein_out = ws.ein[parity ^ 1].template as<real>();
     return launch_update<real>(u, stream);
 }
@@ -731,6 +887,8 @@ int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaS
     }
     CK(p, cudaMemcpyAsync(ws.T[0].p, T0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemcpyAsync(ws.tdev[0].p, td.data(), sizeof(real) * N, cudaMemcpyHostToDevice, stream));
+    if (ws.skew_ready)
+        CK(p, launch_skew<real>(N, ws.skew, ws.tdev[0].template as<real>(), ws.skt[0].template as<real>(), stream));
     CK(p, cudaMemcpyAsync(ws.ein[0].p, e0.data(), sizeof(real) * e0.size(), cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
@@ -824,10 +982,12 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     // tile: the caller's restriction, then the autotuned choice (cached)
     if (o->tile_kind < 0 || o->tile_kind > 3) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1, 2 or 3");
     if (o->source_staging < 0 || o->source_staging > 2) return fail(p, BTE_EINVAL, "source_staging must be 0, 1 or 2");
+    if (o->warps_z < 0 || o->warps_z > 16) return fail(p, BTE_EINVAL, "warps_z must be in 0..16");
     std::vector<int> cand = tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane, o->dirs_per_cta,
-                                            o->source_staging);
+                                            o->source_staging, o->warps_z);
     if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
-    const int tkey = ((o->source_staging * 10 + o->tile_kind) * 100 + o->dirs_per_lane) * 1000 + o->dirs_per_cta;
+    const int tkey =
+        (((o->warps_z * 10 + o->source_staging) * 10 + o->tile_kind) * 100 + o->dirs_per_lane) * 1000 + o->dirs_per_cta;
     int tid;
     if (ws.tuned.count(tkey)) {
         tid = ws.tuned[tkey];
@@ -963,11 +1123,12 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         st->updates_per_s = st->seconds > 0 ? (double)n * p->n_active * p->B * p->D / st->seconds : 0.0;
         st->dirs_per_lane = tile_of(tid).dw;
         st->tile_kind = abi_kind(tile_of(tid).kind);
-        st->dirs_per_cta = tile_of(tid).cw;
+        st->dirs_per_cta = tile_cta_dirs(tile_of(tid));
         st->kernel_launches = launches;
         st->sweep_seconds = sweep_ms * 1e-3;
         st->sweep_launches = n_timed;
-        st->source_staged = tile_of(tid).kind == 4 ? 0 : 1;
+        st->source_staged = source_staged_kind(tile_of(tid).kind);
+        st->warps_z = is_pipe3(tile_of(tid).kind) ? tile_of(tid).cw : 0;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the temperature update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "max_iter reached before eps_T < tol");
@@ -993,6 +1154,7 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
         u.x_in = ws.theta[parity].template as<double>();
         u.x_out = ws.theta[parity ^ 1].template as<double>();
         u.xdev_out = ws.thdev[parity ^ 1].template as<real>();
+        if (is_pipe3(tile_of(dw).kind)) u.xskew_out = ws.ska[parity ^ 1].template as<real>();
         u.ein_out = ws.mein[parity ^ 1].template as<real>();
         return launch_update<real>(u, stream);
     }
@@ -1071,6 +1233,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     CK(p, cudaMemcpyAsync(ws.g.p, g.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemcpyAsync(ws.theta[0].p, th.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemcpyAsync(ws.thdev[0].p, thr.data(), sizeof(real) * N, cudaMemcpyHostToDevice, stream));
+    if (ws.skew_ready)
+        CK(p, launch_skew<real>(N, ws.skew, ws.thdev[0].template as<real>(), ws.ska[0].template as<real>(), stream));
     CK(p, cudaMemsetAsync(ws.mein[0].p, 0, sizeof(real) * (size_t)B * F, stream));
     CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
@@ -1191,11 +1355,12 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         st->updates_per_s = st->seconds > 0 ? (double)(n + 1) * p->n_active * p->B * p->D / st->seconds : 0.0;
         st->dirs_per_lane = tile_of(dw).dw;
         st->tile_kind = abi_kind(tile_of(dw).kind);
-        st->dirs_per_cta = tile_of(dw).cw;
+        st->dirs_per_cta = tile_cta_dirs(tile_of(dw));
         st->kernel_launches = launches + 3;  // final sweep + update + gradient reduction
         st->sweep_seconds = sweep_ms * 1e-3;
         st->sweep_launches = n_timed;
-        st->source_staged = tile_of(dw).kind == 4 ? 0 : 1;
+        st->source_staged = source_staged_kind(tile_of(dw).kind);
+        st->warps_z = is_pipe3(tile_of(dw).kind) ? tile_of(dw).cw : 0;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the adjoint update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "adjoint: max_iter reached before tol");

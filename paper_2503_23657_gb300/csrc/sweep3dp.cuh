@@ -1,0 +1,453 @@
+// Plane-pipeline wavefront sweep for 3D grids (masked, any number of regions).
+//
+// Same discrete equations as sweep.cuh (Eq. fvm-1 with step upwind faces,
+// the lower-triangular matrix A of Eq. A_matrix in the sweep order of the
+// direction's octant), with the work of one (band, direction subset) spread
+// over a CTA as a pipeline of warps:
+//
+//   * one CTA per (direction subset of DW directions sharing an octant,
+//     band); WY = ceil(ny / 32) warps along y (lane = row) times H warps
+//     along z.  Warp (wy, h) owns rows 32 wy .. 32 wy + 31 of the planes
+//     h, h + H, h + 2H, ... (one pass of H planes after the other); every
+//     lane carries the DW directions in registers;
+//   * in canonical (octant-mirrored) coordinates lane l of a warp handles the
+//     virtual column u = tau - l at its local step tau, u = m nx + i meaning
+//     column i of the warp's plane in pass m, so a lane streams through its
+//     rows of all passes without a gap.  The x-upwind value is the lane's
+//     own register from the previous step, the y-upwind value comes from
+//     lane l - 1 by a shuffle (lane 0: from lane 31 of the warp below
+//     through a shared-memory ring), the z-upwind value from the same lane
+//     of the warp below in z through a shared-memory ring (the first warp
+//     of a pass: from the last plane of the previous pass, which the last
+//     warp left in a global buffer);
+//   * the warps run in lockstep chunks of K steps with one CTA barrier per
+//     chunk; warp (wy, h) runs (32 + K) wy + K h steps behind warp (0, 0),
+//     so every value a warp reads was written in an earlier chunk, and the
+//     rings are deep enough that no slot is rewritten before it is read;
+//   * boundary values come from the per-cell record (face base and the
+//     sides that are boundary faces: domain walls and faces next to void
+//     cells), read four steps ahead; the source, the boundary face values
+//     and the previous pass's plane are read two steps ahead, so the step
+//     itself only waits on on-chip data.  The per-cell record, source and
+//     source profile are read from diagonal-skewed copies (SkewLayout), in
+//     which the 32 cells of a warp's step are consecutive: one coalesced
+//     segment per warp and array instead of 32 scattered rows;
+//   * forward and adjoint run the same recurrence: the adjoint unknown mu_d
+//     of the transposed system (Eq. adjoint) scaled by 1 / w_d obeys the
+//     forward recurrence with the adjoint source and boundary values, and
+//     sum_d mu_d = sum_d w_d nu_d; only the face-sum weights differ
+//     (forward w_d |s_d,a|, adjoint a_d w_d);
+//   * the per-cell weighted sums of a step sit on a diagonal; each warp
+//     parks them for 32 steps in a shared-memory tile [row][33] and writes
+//     them row by row (32 consecutive cells of a row).
+#pragma once
+
+#include <stdint.h>
+
+#include "bte_internal.cuh"
+#include "finalize.cuh"
+#include "tma.cuh"
+
+namespace bte {
+
+constexpr int kP3MaxThreads = 512;
+constexpr int kP3RZ = 2 * kPipe3Chunk;  // z-ring depth (virtual columns)
+constexpr int kP3RY = 4 * kPipe3Chunk;  // y-ring depth
+
+__host__ __device__ constexpr int p3_round4(int n) { return (n + 3) & ~3; }
+
+// DW consecutive values (16-byte aligned groups of 4, 8-byte aligned pairs)
+// to and from registers; CG = through L2 only (data written in this launch)
+template <bool CG>
+__device__ __forceinline__ void p3_ld4(const float *p, float *v) {
+    const float4 x = CG ? __ldcg(reinterpret_cast<const float4 *>(p)) : *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+}
+template <bool CG>
+__device__ __forceinline__ void p3_ld4(const double *p, double *v) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 x = CG ? __ldcg(q) : q[0];
+    const double2 y = CG ? __ldcg(q + 1) : q[1];
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = y.x;
+    v[3] = y.y;
+}
+template <bool CG>
+__device__ __forceinline__ void p3_ld2(const float *p, float *v) {
+    const float2 x = CG ? __ldcg(reinterpret_cast<const float2 *>(p)) : *reinterpret_cast<const float2 *>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+}
+template <bool CG>
+__device__ __forceinline__ void p3_ld2(const double *p, double *v) {
+    const double2 x = CG ? __ldcg(reinterpret_cast<const double2 *>(p)) : *reinterpret_cast<const double2 *>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+}
+template <int DW, bool CG = false, typename real>
+__device__ __forceinline__ void p3_load(const real *p, real (&v)[DW]) {
+    if constexpr (DW % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < DW; q += 4) p3_ld4<CG>(p + q, v + q);
+    } else if constexpr (DW == 2) {
+        p3_ld2<CG>(p, v);
+    } else {
+        v[0] = CG ? __ldcg(p) : p[0];
+    }
+}
+__device__ __forceinline__ void p3_st4(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void p3_st4(double *p, const double *v) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void p3_st2(float *p, const float *v) { *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]); }
+__device__ __forceinline__ void p3_st2(double *p, const double *v) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+template <int DW, typename real>
+__device__ __forceinline__ void p3_store(real *p, const real (&v)[DW]) {
+    if constexpr (DW % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < DW; q += 4) p3_st4(p + q, v + q);
+    } else if constexpr (DW == 2) {
+        p3_st2(p, v);
+    } else {
+        p[0] = v[0];
+    }
+}
+
+// Shared-memory carve-up, in elements of real.
+struct P3Smem {
+    int invd, srck, fw, zr, yr, tile, total;
+};
+__host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW) {
+    const int NW = WY * H;
+    P3Smem s;
+    s.invd = 0;                                        // [R][DW] 1 / diagonal
+    s.srck = s.invd + p3_round4(R * DW);               // [R] source factor
+    s.fw = s.srck + p3_round4(R);                      // [3][DW] face-sum weights
+    s.zr = s.fw + p3_round4(3 * DW);                   // [NW][RZ][32][DW] z rings
+    s.yr = s.zr + NW * kP3RZ * 32 * DW;                // [NW][RY][DW] y rings
+    s.tile = s.yr + NW * kP3RY * DW;                   // [NW][32][33] partial-sum tiles
+    s.total = s.tile + NW * 32 * 33;
+    return s;
+}
+
+template <typename real, int DW, bool PHI, bool STORE_E>
+__global__ void __launch_bounds__(kP3MaxThreads, 1)
+sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
+    constexpr int K = kPipe3Chunk, RZ = kP3RZ, RY = kP3RY;
+    static_assert(K == 4, "the prefetch slots assume four steps per chunk");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_stop;
+
+    const int s = blockIdx.x;
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int WY = P.WY, H = P.H;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, R = P.R;
+    const P3Smem L = p3_smem(R, WY, H, DW);
+    real *sm = reinterpret_cast<real *>(smem_raw);
+    real *s_invd = sm + L.invd;
+    real *s_srck = sm + L.srck;
+    real *s_fw = sm + L.fw;
+
+    // the next kernel may be launched now (it waits for this grid); all
+    // reads below see what the previous kernel wrote
+    pdl_launch_dependents();
+    pdl_wait();
+    // one thread reads the stop flag, so every warp of the CTA decides alike
+    if (threadIdx.x == 0) s_stop = (P.done != nullptr && *((volatile const int *)P.done) != 0) ? 1 : 0;
+    __syncthreads();
+    if (s_stop) return;
+
+    const Subset sub = P.sub[s];
+    const int d0 = sub.d0;
+    const int ndir = min(DW, sub.cnt);
+    const bool adj = P.adj != 0;
+    for (int q = threadIdx.x; q < R * DW; q += blockDim.x) {
+        const int r = q / DW, dd = q - r * DW;
+        s_invd[q] = dd < ndir ? P.invdiag[((long long)r * P.B + b) * P.D + d0 + dd] : real(0);
+    }
+    for (int r = threadIdx.x; r < R; r += blockDim.x) s_srck[r] = P.srck[r * P.B + b];
+    for (int q = threadIdx.x; q < 3 * DW; q += blockDim.x) {
+        const int a = q / DW, dd = q - a * DW;
+        real v = real(0);
+        if (dd < ndir) {
+            const real *cf = P.coef + ((long long)b * P.D + d0 + dd) * 8;
+            // forward: w |s_a| (energy leaving); adjoint: a_a w (nu = mu / w)
+            v = adj ? cf[a] * cf[3] : cf[4 + a];
+        }
+        s_fw[q] = v;
+    }
+    // deferred finalization of the previous iteration (CTA (0, 0)); nothing
+    // in this kernel depends on it: a stop found here ends the solve at the
+    // update that follows
+    if (s == 0 && b == 0 && warp == 0 && P.fin.pending != nullptr && *((volatile const int *)P.fin.pending) != 0) {
+        double eps, tmx, tss;
+        fin_reduce(P.fin, eps, tmx, tss);
+        if (lane == 0) fin_record(P.fin, eps, tmx, tss);
+    }
+    __syncthreads();
+
+    // ---- this warp: rows 32 wy .. 32 wy + 31 of planes h + H m ----
+    const int wy = warp % WY;
+    const int h = warp / WY;
+    const bool negx = sub.neg & 1, negy = (sub.neg >> 1) & 1, negz = (sub.neg >> 2) & 1;
+    const int up_x = negx ? 1 : 0, up_y = negy ? 3 : 2, up_z = negz ? 5 : 4;
+    const unsigned dn_mask = (1u << (up_x ^ 1)) | (1u << (up_y ^ 1)) | (1u << (up_z ^ 1));
+    real ax[DW], ay[DW], az[DW], w[DW];
+#pragma unroll
+    for (int dd = 0; dd < DW; ++dd) {
+        if (dd < ndir) {
+            const real *cf = P.coef + ((long long)b * P.D + d0 + dd) * 8;
+            ax[dd] = cf[0];
+            ay[dd] = cf[1];
+            az[dd] = cf[2];
+            w[dd] = cf[3];
+        } else {
+            ax[dd] = ay[dd] = az[dd] = w[dd] = real(0);
+        }
+    }
+    const real qb = PHI ? P.qb[b] : real(0);
+    const real *einb = P.ein + (long long)b * P.F;
+    const int j = 32 * wy + lane;
+    const bool rowv = j < ny;
+    const int Y = negy ? ny - 1 - j : j;
+    const int M = (nz + H - 1) / H;        // passes
+    const int U = M * nx;                  // virtual columns of a lane
+    const int n_loc = (U + 31 + 31) & ~31; // local steps (whole 32-step tiles)
+    constexpr int Ly = 32 + K, Lz = K;     // lag of the next warp along y / z
+    const int delta = wy * Ly + h * Lz;
+    const int T = (WY - 1) * Ly + (H - 1) * Lz + n_loc;
+    const int nxny = nx * ny;
+    const int ld_wrap = WY * 32;
+    // skewed inputs: the family of this octant (X + Y or X - Y constant
+    // along a step) and its plane / diagonal strides
+    const int fam = (negx != negy) ? 1 : 0;
+    const int sk_nd = P.skew.nd, sk_nyp = P.skew.nyp;
+    const int sk_base = fam ? (int)P.skew.fam : 0;
+    const bool wrap_rd = (h == 0) && M > 1;       // reads the previous pass's last plane
+    const bool wrap_wr = (h == H - 1) && M > 1;   // writes this pass's last plane
+    const bool feed_y = wy + 1 < WY;
+    const bool feed_z = h + 1 < H;
+    real *const part_b = P.part + ((long long)b * P.Spad + s) * P.N;
+    real *const fs_sb = P.fsum + ((long long)s * P.B + b) * P.F;
+    real *const wrap_c = (M > 1) ? P.wrap + ((long long)s * P.B + b) * (long long)nx * ld_wrap * DW : nullptr;
+    real *const tile = sm + L.tile + warp * 32 * 33;
+    real *const zr_out = sm + L.zr + warp * RZ * 32 * DW;
+    const real *const zr_in = sm + L.zr + (warp - WY) * RZ * 32 * DW;   // h > 0
+    real *const yr_out = sm + L.yr + warp * RY * DW;
+    const real *const yr_in = sm + L.yr + (warp - 1) * RY * DW;         // wy > 0
+
+    // cell of virtual column (i, m) of this lane: skewed index, or -1
+    // outside the grid; its natural index (e stores only); iw = column of the
+    // wrap buffer this warp reads / writes there, or -1
+    auto locate = [&](int i, int m, int &sk, int &c, int &iw) {
+        const int k = h + H * m;
+        const bool v = rowv && i >= 0 && m < M && k < nz;
+        const int X = negx ? nx - 1 - i : i;
+        const int Z = negz ? nz - 1 - k : k;
+        const int key = fam ? X + (ny - 1 - Y) : X + Y;
+        sk = v ? sk_base + (Z * sk_nd + key) * sk_nyp + Y : -1;
+        c = (STORE_E && v) ? X + nx * Y + nxny * Z : -1;
+        iw = (v && ((wrap_rd && m >= 1) || (wrap_wr && m + 1 < M))) ? i : -1;
+    };
+
+    // record slots (local step mod 4) and data slots (local step mod 2)
+    int rs[4], rc[STORE_E ? 4 : 1], rx[4], ry[4], riw[4];
+    real dt[2], dp[2], dex[2], dey[2], dez[2], dwz[2][DW];
+    // tracker of the record read next: virtual column (ui, um) of local step tau + 4
+    int ui = -lane, um = 0;
+    auto fetch_record = [&](int q) {
+        int sk, c, iw;
+        locate(ui, um, sk, c, iw);
+        rs[q] = sk;
+        if (STORE_E) rc[STORE_E ? q : 0] = c;
+        riw[q] = iw;
+        int2 ci = make_int2(0, 0);
+        if (sk >= 0) ci = __ldg(P.cell + sk);
+        rx[q] = ci.x;
+        ry[q] = ci.y;
+        ++ui;
+        if (ui == nx) {
+            ui = 0;
+            ++um;
+        }
+    };
+    // source, boundary values and wrapped plane of the cell in record slot q
+    auto fetch_data = [&](int q, int slot) {
+        const int sk = rs[q];
+        const int fb = rx[q], fl = ry[q], iw = riw[q];
+        const bool v = sk >= 0;
+        const unsigned bm = ((unsigned)fl >> kSideShift) & 63u;
+        dt[slot] = v ? __ldg(P.tsrc + sk) : real(0);
+        if (PHI) dp[slot] = v ? __ldg(P.phi + sk) : real(0);
+        dex[slot] = (v && ((bm >> up_x) & 1u)) ? __ldg(einb + face_of(fb, fl, up_x)) : real(0);
+        dey[slot] = (v && ((bm >> up_y) & 1u)) ? __ldg(einb + face_of(fb, fl, up_y)) : real(0);
+        dez[slot] = (v && ((bm >> up_z) & 1u)) ? __ldg(einb + face_of(fb, fl, up_z)) : real(0);
+        if (wrap_rd && iw >= 0) {
+            // written by this CTA earlier in this launch: read through L2
+            p3_load<DW, true>(wrap_c + ((long long)iw * ld_wrap + j) * DW, dwz[slot]);
+        } else {
+#pragma unroll
+            for (int dd = 0; dd < DW; ++dd) dwz[slot][dd] = real(0);
+        }
+    };
+    // before its rows enter the grid a lane's registers hold zeros; the first
+    // cell of every row has its x-upwind side marked as a boundary
+    real old[DW];
+#pragma unroll
+    for (int dd = 0; dd < DW; ++dd) old[dd] = real(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) fetch_record(q);
+    fetch_data(0, 0);
+    fetch_data(1, 1);
+
+    for (int t0 = 0; t0 < T; t0 += K) {
+        const int tau0 = t0 - delta;
+        if (tau0 >= 0 && tau0 < n_loc) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int tau = tau0 + k;
+                const int u = tau - lane;
+                // this step's cell (record read four steps ago, data two)
+                const bool inside = rs[k] >= 0;
+                const int c = STORE_E ? rc[STORE_E ? k : 0] : -1;
+                const int fb = rx[k], fl = ry[k], iw = riw[k];
+                const real tsv = dt[k & 1];
+                const real phv = PHI ? dp[k & 1] : real(0);
+                const real Ex = dex[k & 1], Ey = dey[k & 1], Ez = dez[k & 1];
+                real zin[DW];
+#pragma unroll
+                for (int dd = 0; dd < DW; ++dd) zin[dd] = dwz[k & 1][dd];
+                // reads for later steps
+                fetch_record(k);
+                fetch_data((k + 2) & 3, k & 1);
+
+                const int region = fl & kRegionMask;
+                const bool act = inside && region != 0;
+                const unsigned bm = ((unsigned)fl >> kSideShift) & 63u;
+                const bool bx = (bm >> up_x) & 1u;
+                const bool by = (bm >> up_y) & 1u;
+                const bool bz = (bm >> up_z) & 1u;
+                const int r = act ? region - 1 : 0;
+                real base = tsv * s_srck[r];
+                if (PHI) base += phv * qb;
+                real invd[DW], yin[DW];
+                p3_load<DW>(s_invd + r * DW, invd);
+                if (h > 0) p3_load<DW>(zr_in + ((u & (RZ - 1)) * 32 + lane) * DW, zin);
+                if (wy > 0) {
+                    p3_load<DW>(yr_in + (tau & (RY - 1)) * DW, yin);  // lane 0: u == tau
+                } else {
+#pragma unroll
+                    for (int dd = 0; dd < DW; ++dd) yin[dd] = real(0);
+                }
+                real acc = real(0);
+#pragma unroll
+                for (int dd = 0; dd < DW; ++dd) {
+                    real vy = __shfl_up_sync(0xffffffffu, old[dd], 1);
+                    if (lane == 0) vy = yin[dd];
+                    real vx = old[dd];
+                    real vz = zin[dd];
+                    vx = bx ? Ex : vx;
+                    vy = by ? Ey : vy;
+                    vz = bz ? Ez : vz;
+                    real r0 = fma(ax[dd], vx, base);
+                    r0 = fma(ay[dd], vy, r0);
+                    r0 = fma(az[dd], vz, r0);
+                    const real en = r0 * invd[dd];
+                    old[dd] = act ? en : old[dd];
+                    acc = fma(w[dd], en, acc);
+                }
+                tile[lane * 33 + (tau & 31)] = acc;
+                if (feed_z) p3_store<DW>(zr_out + ((u & (RZ - 1)) * 32 + lane) * DW, old);
+                if (feed_y && lane == 31) p3_store<DW>(yr_out + (u & (RY - 1)) * DW, old);
+                if (wrap_wr && iw >= 0) p3_store<DW>(wrap_c + ((long long)iw * ld_wrap + j) * DW, old);
+                // face sums at the boundary sides the traversal leaves by
+                if (act && (bm & dn_mask)) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int dn = (a == 0 ? up_x : (a == 1 ? up_y : up_z)) ^ 1;
+                        if (!((bm >> dn) & 1u)) continue;
+                        real fs = real(0);
+#pragma unroll
+                        for (int dd = 0; dd < DW; ++dd) fs = fma(s_fw[a * DW + dd], old[dd], fs);
+                        fs_sb[face_of(fb, fl, dn)] = fs;
+                    }
+                }
+                if (STORE_E && act) {
+                    real *ep = P.e + ((long long)c * P.B + b) * P.D + d0;
+#pragma unroll
+                    for (int dd = 0; dd < DW; ++dd)
+                        if (dd < ndir) ep[dd] = adj ? old[dd] * w[dd] : old[dd];
+                }
+            }
+            if (((tau0 + K) & 31) == 0) {
+                // the last 32 steps of row r are 32 consecutive virtual columns:
+                // write them row by row (lane q: column u = tb + q - r)
+                __syncwarp();
+                const int tb = tau0 + K - 32;
+                const int u0 = tb + lane;
+                int m = u0 / nx;
+                int i = u0 - m * nx;
+                for (int rr = 0; rr < 32; ++rr) {
+                    if (rr > 0) {
+                        --i;
+                        if (i < 0) {
+                            i += nx;
+                            --m;
+                        }
+                    }
+                    const int u = u0 - rr;
+                    const int jr = 32 * wy + rr;
+                    const int k = h + H * m;
+                    if (u >= 0 && u < U && jr < ny && k < nz) {
+                        const int X = negx ? nx - 1 - i : i;
+                        const int Yr = negy ? ny - 1 - jr : jr;
+                        const int Z = negz ? nz - 1 - k : k;
+                        part_b[X + nx * Yr + nxny * Z] = tile[rr * 33 + lane];
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename real>
+size_t sweep3dp_smem_bytes(int R, int WY, int H, int dw) {
+    return (size_t)p3_smem(R, WY, H, dw).total * sizeof(real);
+}
+
+template <typename real, int DW, bool PHI, bool STORE_E>
+cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
+    const int threads = p.WY * p.H * 32;
+    if (p.H < 1 || p.WY < 1 || threads > kP3MaxThreads) return cudaErrorInvalidConfiguration;
+    const size_t smem = sweep3dp_smem_bytes<real>(p.R, p.WY, p.H, DW);
+    auto kern = sweep3dp_kernel<real, DW, PHI, STORE_E>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_pdl(kern, dim3(p.S, p.B), dim3(threads), smem, st, p);
+}
+
+// the source-profile term only in forward sweeps with a source; e only when asked
+template <typename real, int DW>
+cudaError_t launch_sweep3dp_t(const Sweep3DParams<real> &p, cudaStream_t st) {
+    const bool phi = !p.adj && p.phi != nullptr;
+    if (p.store_e)
+        return phi ? launch_sweep3dp_v<real, DW, true, true>(p, st) : launch_sweep3dp_v<real, DW, false, true>(p, st);
+    return phi ? launch_sweep3dp_v<real, DW, true, false>(p, st) : launch_sweep3dp_v<real, DW, false, false>(p, st);
+}
+
+}  // namespace bte

@@ -1,0 +1,25 @@
+// Instantiations of the plane-pipeline 3D sweep: float.
+#include "sweep3dp.cuh"
+
+namespace bte {
+template <>
+cudaError_t launch_sweep3dp<float>(const Sweep3DParams<float> &p, int dw, cudaStream_t st) {
+    if (dw == 2) return launch_sweep3dp_t<float, 2>(p, st);
+    if (dw == 4) return launch_sweep3dp_t<float, 4>(p, st);
+    if (dw == 8) return launch_sweep3dp_t<float, 8>(p, st);
+    return cudaErrorInvalidConfiguration;
+}
+
+size_t sweep3dp_smem(int R, int WY, int H, int dw, int real_bytes) {
+    return real_bytes == 4 ? sweep3dp_smem_bytes<float>(R, WY, H, dw) : sweep3dp_smem_bytes<double>(R, WY, H, dw);
+}
+}  // namespace bte
+
+namespace bte {
+// The plane-pipeline kernel runs FP32 only (candidate tiles never offer it
+// for FP64 solves).
+template <>
+cudaError_t launch_sweep3dp<double>(const Sweep3DParams<double> &, int, cudaStream_t) {
+    return cudaErrorInvalidConfiguration;
+}
+}  // namespace bte

@@ -29,6 +29,17 @@ constexpr int kUpdThreads = 256;
 // ([B][Spad][N] layout), so a warp's loads of one set are coalesced; eight
 // independent loads are in flight, summed in a fixed order in the sweep
 // precision.
+// value of cell c into both families of a skewed field
+template <typename T>
+__device__ __forceinline__ void skew_store(const SkewLayout &L, long long c, T v, T *dst) {
+    const long long row = c / L.nx;
+    const int X = (int)(c - row * L.nx);
+    const int Y = (int)(row % L.ny);
+    const int Z = (int)(row / L.ny);
+    dst[skew_index(L, 0, X, Y, Z)] = v;
+    dst[skew_index(L, 1, X, Y, Z)] = v;
+}
+
 template <typename real>
 __device__ __forceinline__ real sum_sets(const real *pp, int S, long long N) {
     real a[8] = {real(0), real(0), real(0), real(0), real(0), real(0), real(0), real(0)};
@@ -140,16 +151,19 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
 #pragma unroll
             for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
             double xn;
+            real xd;
             if (!P.adjoint) {
                 const double dev = tot * P.Kinv[r - 1];
                 xn = P.T_ref + dev;
-                P.xdev_out[c] = (real)dev;
+                xd = (real)dev;
                 mx = xn;
             } else {
                 xn = (P.g[c] + tot) * P.Kinv[r - 1];
-                P.xdev_out[c] = (real)xn;
+                xd = (real)xn;
                 mx = fabs(xn);
             }
+            P.xdev_out[c] = xd;
+            if (P.xskew_out) skew_store(P.skew, c, xd, P.xskew_out);
             const double d = xn - x_old;
             ss = d * d;
             if (!isfinite(xn)) ss = NAN;
@@ -157,6 +171,7 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
         } else {
             P.x_out[c] = 0.0;
             P.xdev_out[c] = (real)0;
+            if (P.xskew_out) skew_store(P.skew, c, (real)0, P.xskew_out);
         }
     }
     fin_warp_reduce(ss, mx);
@@ -414,5 +429,21 @@ template cudaError_t launch_permute_e<double>(long long, int, int, const int2 *,
                                               const double *, double *, cudaStream_t);
 template cudaError_t launch_grad<float>(const GradParams<float> &, cudaStream_t);
 template cudaError_t launch_grad<double>(const GradParams<double> &, cudaStream_t);
+
+template <typename T>
+__global__ void skew_kernel(long long N, SkewLayout L, const T *__restrict__ src, T *__restrict__ dst) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) skew_store(L, c, src[c], dst);
+}
+
+template <typename T>
+cudaError_t launch_skew(long long N, const SkewLayout &L, const T *src, T *dst, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    skew_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, L, src, dst);
+    return cudaGetLastError();
+}
+template cudaError_t launch_skew<float>(long long, const SkewLayout &, const float *, float *, cudaStream_t);
+template cudaError_t launch_skew<double>(long long, const SkewLayout &, const double *, double *, cudaStream_t);
+template cudaError_t launch_skew<int2>(long long, const SkewLayout &, const int2 *, int2 *, cudaStream_t);
 
 }  // namespace bte
