@@ -326,7 +326,7 @@ bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw, int stage
 bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H) {
     if (p->dim != 3 || real_bytes != 4 || H < 1) return false;
     if (p->N >= (1LL << 31) - 1) return false;
-    const long long skew_entries = 2LL * p->nz * (p->nx + p->ny - 1) * (((p->ny + 31) / 32) * 32);
+    const long long skew_entries = 2LL * p->nz * (p->nx + p->ny - 1) * (((p->ny + 31) / 32) * 32) + 32;
     if (skew_entries >= (1LL << 31) - 1) return false;
     const int WY = (p->ny + 31) / 32;
     if (WY * H > 16 || H > p->nz) return false;
@@ -436,7 +436,7 @@ int ensure_skew(bte_plan *p, Workspace<real> &ws) {
     L.nd = p->nx + p->ny - 1;
     L.nyp = ((p->ny + 31) / 32) * 32;
     L.fam = (long long)p->nz * L.nd * L.nyp;
-    const size_t n = 2 * (size_t)L.fam;
+    const size_t n = 2 * (size_t)L.fam + 32;  // both families + a zero pad entry
     CK(p, ws.skc.ensure(sizeof(int2) * n));
     CK(p, cudaMemset(ws.skc.p, 0, sizeof(int2) * n));
     CK(p, ws.skphi.ensure(sizeof(real) * n));

@@ -203,6 +203,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const bool negx = sub.neg & 1, negy = (sub.neg >> 1) & 1, negz = (sub.neg >> 2) & 1;
     const int up_x = negx ? 1 : 0, up_y = negy ? 3 : 2, up_z = negz ? 5 : 4;
     const unsigned dn_mask = (1u << (up_x ^ 1)) | (1u << (up_y ^ 1)) | (1u << (up_z ^ 1));
+    const unsigned below_x = (1u << up_x) - 1u, below_y = (1u << up_y) - 1u, below_z = (1u << up_z) - 1u;
     real ax[DW], ay[DW], az[DW], w[DW];
 #pragma unroll
     for (int dd = 0; dd < DW; ++dd) {
@@ -222,6 +223,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const bool rowv = j < ny;
     const int Y = negy ? ny - 1 - j : j;
     const int M = (nz + H - 1) / H;        // passes
+    const int Mh = (nz - h + H - 1) / H;   // passes in which this warp's plane lies in the grid
     const int U = M * nx;                  // virtual columns of a lane
     const int n_loc = (U + 31 + 31) & ~31; // local steps (whole 32-step tiles)
     constexpr int Ly = 32 + K, Lz = K;     // lag of the next warp along y / z
@@ -229,11 +231,22 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const int T = (WY - 1) * Ly + (H - 1) * Lz + n_loc;
     const int nxny = nx * ny;
     const int ld_wrap = WY * 32;
+    const int sx = negx ? -1 : 1;          // dX / di
+    const int sz = negz ? -1 : 1;          // dZ / dk
+    const float inv_nx = 1.0f / (float)nx;
     // skewed inputs: the family of this octant (X + Y or X - Y constant
-    // along a step) and its plane / diagonal strides
+    // along a step); index of column i of pass m of this lane:
+    //   sk0 + sx nyp i + sz H nd nyp m  (within a pass; see SkewLayout)
+    // and a zero pad entry (2 fam) for the cells outside the grid
     const int fam = (negx != negy) ? 1 : 0;
     const int sk_nd = P.skew.nd, sk_nyp = P.skew.nyp;
-    const int sk_base = fam ? (int)P.skew.fam : 0;
+    const int sk_pad = 2 * (int)P.skew.fam;
+    const int X0 = negx ? nx - 1 : 0;
+    const int Zh = negz ? nz - 1 - h : h;
+    const int key0 = fam ? X0 + (ny - 1 - Y) : X0 + Y;
+    const int sk0 = (fam ? (int)P.skew.fam : 0) + (Zh * sk_nd + key0) * sk_nyp + Y;
+    const int dsk = sx * sk_nyp;                                   // next column
+    const int dsk_pass = (sz * H * sk_nd - sx * (nx - 1)) * sk_nyp; // column 0 of the next pass
     const bool wrap_rd = (h == 0) && M > 1;       // reads the previous pass's last plane
     const bool wrap_wr = (h == H - 1) && M > 1;   // writes this pass's last plane
     const bool feed_y = wy + 1 < WY;
@@ -247,65 +260,67 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     real *const yr_out = sm + L.yr + warp * RY * DW;
     const real *const yr_in = sm + L.yr + (warp - 1) * RY * DW;         // wy > 0
 
-    // cell of virtual column (i, m) of this lane: skewed index, or -1
-    // outside the grid; its natural index (e stores only); iw = column of the
-    // wrap buffer this warp reads / writes there, or -1
-    auto locate = [&](int i, int m, int &sk, int &c, int &iw) {
-        const int k = h + H * m;
-        const bool v = rowv && i >= 0 && m < M && k < nz;
-        const int X = negx ? nx - 1 - i : i;
-        const int Z = negz ? nz - 1 - k : k;
-        const int key = fam ? X + (ny - 1 - Y) : X + Y;
-        sk = v ? sk_base + (Z * sk_nd + key) * sk_nyp + Y : -1;
-        c = (STORE_E && v) ? X + nx * Y + nxny * Z : -1;
-        iw = (v && ((wrap_rd && m >= 1) || (wrap_wr && m + 1 < M))) ? i : -1;
-    };
-
     // record slots (local step mod 4) and data slots (local step mod 2)
     int rs[4], rc[STORE_E ? 4 : 1], rx[4], ry[4], riw[4];
     real dt[2], dp[2], dex[2], dey[2], dez[2], dwz[2][DW];
-    // tracker of the record read next: virtual column (ui, um) of local step tau + 4
+    // tracker of the record read next (local step tau + 4): column ui of
+    // pass um and its skewed index (valid once ui >= 0)
     int ui = -lane, um = 0;
+    int sk_t = sk0 - lane * dsk;
     auto fetch_record = [&](int q) {
-        int sk, c, iw;
-        locate(ui, um, sk, c, iw);
+        const bool v = rowv && ui >= 0 && um < Mh;
+        const int sk = v ? sk_t : sk_pad;
         rs[q] = sk;
-        if (STORE_E) rc[STORE_E ? q : 0] = c;
-        riw[q] = iw;
-        int2 ci = make_int2(0, 0);
-        if (sk >= 0) ci = __ldg(P.cell + sk);
+        if (STORE_E) {
+            const int X = negx ? nx - 1 - ui : ui;
+            const int k = h + H * um;
+            const int Z = negz ? nz - 1 - k : k;
+            rc[STORE_E ? q : 0] = v ? X + nx * Y + nxny * Z : -1;
+        }
+        // wrap buffer column: read by the first warp of a pass (the value is
+        // used only past the first pass), written by the last one
+        riw[q] = wrap_wr ? ((v && um + 1 < M) ? ui : -1) : max(ui, 0);
+        const int2 ci = __ldg(P.cell + sk);
         rx[q] = ci.x;
         ry[q] = ci.y;
         ++ui;
+        sk_t += dsk;
         if (ui == nx) {
             ui = 0;
             ++um;
+            sk_t += dsk_pass - dsk;
         }
     };
-    // source, boundary values and wrapped plane of the cell in record slot q
+    // source, boundary values and wrapped plane of the cell in record slot q;
+    // every load is unconditional (a cell without a boundary on a side reads
+    // face 0, a cell outside the grid the zero pad entry) and the step selects
     auto fetch_data = [&](int q, int slot) {
         const int sk = rs[q];
-        const int fb = rx[q], fl = ry[q], iw = riw[q];
-        const bool v = sk >= 0;
+        const int fb = rx[q], fl = ry[q];
         const unsigned bm = ((unsigned)fl >> kSideShift) & 63u;
-        dt[slot] = v ? __ldg(P.tsrc + sk) : real(0);
-        if (PHI) dp[slot] = v ? __ldg(P.phi + sk) : real(0);
-        dex[slot] = (v && ((bm >> up_x) & 1u)) ? __ldg(einb + face_of(fb, fl, up_x)) : real(0);
-        dey[slot] = (v && ((bm >> up_y) & 1u)) ? __ldg(einb + face_of(fb, fl, up_y)) : real(0);
-        dez[slot] = (v && ((bm >> up_z) & 1u)) ? __ldg(einb + face_of(fb, fl, up_z)) : real(0);
-        if (wrap_rd && iw >= 0) {
+        dt[slot] = __ldg(P.tsrc + sk);
+        if (PHI) dp[slot] = __ldg(P.phi + sk);
+        const int fx = ((bm >> up_x) & 1u) ? fb + __popc(bm & below_x) : 0;
+        const int fy = ((bm >> up_y) & 1u) ? fb + __popc(bm & below_y) : 0;
+        const int fz = ((bm >> up_z) & 1u) ? fb + __popc(bm & below_z) : 0;
+        dex[slot] = __ldg(einb + fx);
+        dey[slot] = __ldg(einb + fy);
+        dez[slot] = __ldg(einb + fz);
+        if (wrap_rd) {
             // written by this CTA earlier in this launch: read through L2
-            p3_load<DW, true>(wrap_c + ((long long)iw * ld_wrap + j) * DW, dwz[slot]);
-        } else {
-#pragma unroll
-            for (int dd = 0; dd < DW; ++dd) dwz[slot][dd] = real(0);
+            p3_load<DW, true>(wrap_c + ((long long)riw[q] * ld_wrap + j) * DW, dwz[slot]);
         }
     };
     // before its rows enter the grid a lane's registers hold zeros; the first
-    // cell of every row has its x-upwind side marked as a boundary
+    // cell of every row has its x-upwind side marked as a boundary, and a cell
+    // next to a void or outside cell reads the boundary value instead of it
     real old[DW];
 #pragma unroll
     for (int dd = 0; dd < DW; ++dd) old[dd] = real(0);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int dd = 0; dd < DW; ++dd) dwz[q][dd] = real(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) fetch_record(q);
     fetch_data(0, 0);
@@ -319,7 +334,6 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 const int tau = tau0 + k;
                 const int u = tau - lane;
                 // this step's cell (record read four steps ago, data two)
-                const bool inside = rs[k] >= 0;
                 const int c = STORE_E ? rc[STORE_E ? k : 0] : -1;
                 const int fb = rx[k], fl = ry[k], iw = riw[k];
                 const real tsv = dt[k & 1];
@@ -333,7 +347,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 fetch_data((k + 2) & 3, k & 1);
 
                 const int region = fl & kRegionMask;
-                const bool act = inside && region != 0;
+                const bool act = region != 0;   // solid cell of the grid
                 const unsigned bm = ((unsigned)fl >> kSideShift) & 63u;
                 const bool bx = (bm >> up_x) & 1u;
                 const bool by = (bm >> up_y) & 1u;
@@ -350,21 +364,22 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
 #pragma unroll
                     for (int dd = 0; dd < DW; ++dd) yin[dd] = real(0);
                 }
+                // cells that are not solid cells of the grid update garbage
+                // that no solid cell reads (their downwind neighbours take
+                // boundary values) and that the update kernel ignores
                 real acc = real(0);
 #pragma unroll
                 for (int dd = 0; dd < DW; ++dd) {
                     real vy = __shfl_up_sync(0xffffffffu, old[dd], 1);
                     if (lane == 0) vy = yin[dd];
-                    real vx = old[dd];
-                    real vz = zin[dd];
-                    vx = bx ? Ex : vx;
+                    const real vx = bx ? Ex : old[dd];
                     vy = by ? Ey : vy;
-                    vz = bz ? Ez : vz;
+                    const real vz = bz ? Ez : zin[dd];
                     real r0 = fma(ax[dd], vx, base);
                     r0 = fma(ay[dd], vy, r0);
                     r0 = fma(az[dd], vz, r0);
                     const real en = r0 * invd[dd];
-                    old[dd] = act ? en : old[dd];
+                    old[dd] = en;
                     acc = fma(w[dd], en, acc);
                 }
                 tile[lane * 33 + (tau & 31)] = acc;
@@ -390,27 +405,34 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                         if (dd < ndir) ep[dd] = adj ? old[dd] * w[dd] : old[dd];
                 }
             }
-            if (((tau0 + K) & 31) == 0) {
-                // the last 32 steps of row r are 32 consecutive virtual columns:
-                // write them row by row (lane q: column u = tb + q - r)
+            {
+                // write 4 of the 32 rows of the sum tile (rows 4 g .. 4 g + 3,
+                // g = this chunk's index mod 8): every row is written once per
+                // 32 steps, covering its last 32 steps = 32 consecutive virtual
+                // columns, and every warp does the same work in every chunk.
+                // Lane q writes the column of the step whose tile slot is q.
                 __syncwarp();
-                const int tb = tau0 + K - 32;
-                const int u0 = tb + lane;
-                int m = u0 / nx;
-                int i = u0 - m * nx;
-                for (int rr = 0; rr < 32; ++rr) {
-                    if (rr > 0) {
-                        --i;
-                        if (i < 0) {
-                            i += nx;
-                            --m;
-                        }
+                const int te = tau0 + K - 1;
+                const int g = (te >> 2) & 7;
+                const int tq = te - ((te - lane) & 31);
+                const int u_top = tq - 4 * g;
+                // u_top / nx without an integer division (exact for the
+                // column counts of a grid that fits in memory)
+                int m = __float2int_rd(((float)u_top + 0.5f) * inv_nx);
+                m -= (m * nx > u_top) ? 1 : 0;
+                m += ((m + 1) * nx <= u_top) ? 1 : 0;
+                int i = u_top - m * nx;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int rr = 4 * g + q;
+                    if (q > 0 && --i < 0) {
+                        i += nx;
+                        --m;
                     }
-                    const int u = u0 - rr;
-                    const int jr = 32 * wy + rr;
                     const int k = h + H * m;
-                    if (u >= 0 && u < U && jr < ny && k < nz) {
+                    if (m >= 0 && k < nz && 32 * wy + rr < ny) {
                         const int X = negx ? nx - 1 - i : i;
+                        const int jr = 32 * wy + rr;
                         const int Yr = negy ? ny - 1 - jr : jr;
                         const int Z = negz ? nz - 1 - k : k;
                         part_b[X + nx * Yr + nxny * Z] = tile[rr * 33 + lane];
