@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -244,6 +245,8 @@ def main():
     ap.add_argument("--workload", default="square", choices=sorted(WORKLOADS))
     ap.add_argument("--instances", type=int, default=256, help="ensemble: number of instances (a profiler "
                                                                   "capture uses a small batch)")
+    ap.add_argument("--bands", type=int, default=0, help="keep only the first N bands (0 = all): the small "
+                                                          "case of a workload for a full profiler capture")
     ap.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations of the CPU baseline (0 = ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
@@ -272,6 +275,9 @@ def main():
     probs = probs if isinstance(probs, list) else [probs]
     if args.workload == "ensemble" and args.instances != 256:
         name = name.replace("256x", f"{args.instances}x")
+    if args.bands:
+        probs = [q.copy(C=q.C[:args.bands], v=q.v[:args.bands], tau=q.tau[:args.bands]) for q in probs]
+        name = re.sub(r"_B\d+_", f"_B{probs[0].B}_", name)
 
     # the CPU baseline runs before any GPU work (no fork after CUDA init)
     cpu = None

@@ -398,7 +398,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                         fs_sb[face_of(fb, fl, dn)] = fs;
                     }
                 }
-                if (STORE_E && act) {
+                if (STORE_E && act && c >= 0) {
                     real *ep = P.e + ((long long)c * P.B + b) * P.D + d0;
 #pragma unroll
                     for (int dd = 0; dd < DW; ++dd)
