@@ -318,13 +318,14 @@ bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw, int stage
     return sweep2dp_smem(p->nx, p->ny, p->phi.empty() ? 0 : 1, groups, dw, stage, real_bytes) <= 200 * 1024;
 }
 
-// Plane-pipeline 3D kernel: 3D grid (masks and regions allowed), FP32,
-// ceil(ny / 32) warps along y times H along z (at most 16 warps); a grid of
+// Plane-pipeline 3D kernel: 3D grid (masks and regions allowed), FP32 with
+// 2, 4 or 8 directions per lane, FP64 with 2 or 4, ceil(ny / 32) warps along
+// y times H along z (at most 16 warps); a grid of
 // more than H planes streams in passes, which needs two warps along z and
 // nx >= 4 H + 2 (the next pass reads the last plane of the previous one two
 // steps ahead, a chunk after it was written).
 bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H) {
-    if (p->dim != 3 || real_bytes != 4 || H < 1) return false;
+    if (p->dim != 3 || H < 1 || (real_bytes == 8 && dw > 4)) return false;
     if (p->N >= (1LL << 31) - 1) return false;
     const long long skew_entries = 2LL * p->nz * (p->nx + p->ny - 1) * (((p->ny + 31) / 32) * 32) + 32;
     if (skew_entries >= (1LL << 31) - 1) return false;

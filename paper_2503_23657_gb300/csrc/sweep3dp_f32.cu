@@ -14,12 +14,3 @@ size_t sweep3dp_smem(int R, int WY, int H, int dw, int real_bytes) {
     return real_bytes == 4 ? sweep3dp_smem_bytes<float>(R, WY, H, dw) : sweep3dp_smem_bytes<double>(R, WY, H, dw);
 }
 }  // namespace bte
-
-namespace bte {
-// The plane-pipeline kernel runs FP32 only (candidate tiles never offer it
-// for FP64 solves).
-template <>
-cudaError_t launch_sweep3dp<double>(const Sweep3DParams<double> &, int, cudaStream_t) {
-    return cudaErrorInvalidConfiguration;
-}
-}  // namespace bte

@@ -175,9 +175,26 @@ def test_adjoint_passes_matches_general(bte):
     assert out[1][2] == pytest.approx(out[0][2], rel=1e-4)
 
 
+@pytest.mark.parametrize("name,kw", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("dw", [2, 4])
+def test_fp64_fixed_iterations(bte, name, kw, dw):
+    """FP64 sweeps through the plane pipeline: within 1e-12 of the oracle."""
+    p = bi.tiny(3, **kw)
+    k = 7
+    ref = oracle.solve(p, max_iter=k, tol=0.0)
+    act = p.mask > 0
+    plan = bte.Plan(p)
+    for H in sorted({heights(p.n)[0], heights(p.n)[-1]}):
+        T = np.zeros(p.n_cells)
+        rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=3,
+                            warps_z=H)
+        assert st["tile_kind"] == 3 and st["warps_z"] == H
+        assert rel(T, ref["T"], act) < 1e-12
+
+
 def test_rejections(bte):
     """warps_z that the grid cannot take is refused (EINVAL), and FP64 has no
-    plane-pipeline tile."""
+    eight-direction plane-pipeline tile."""
     from paper_2503_23657_gb300 import binding
     p = bi.tiny(3, **CASES[2][1])
     plan = bte.Plan(p)
@@ -187,5 +204,5 @@ def test_rejections(bte):
     assert rc == binding.BTE_EINVAL
     rc, st = plan.solve(T, tol=0.0, max_iter=2, tile_kind=3, warps_z=17, check=False)
     assert rc == binding.BTE_EINVAL
-    rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=2, tile_kind=3, check=False)
+    rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=2, tile_kind=3, dirs_per_lane=8, check=False)
     assert rc == binding.BTE_EINVAL
