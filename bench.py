@@ -118,7 +118,7 @@ NCU_TRAFFIC = {
     # profiles/sweep2dp_square128.md: 202.2 KB read + 1.5 KB written (128 x 128 square, tile 3:4:4:1)
     ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 203776,
     # profiles/sweep3dp_hotspot64.md: 77.6 MB read + 271.2 MB written (64^3 hotspot, 15 bands, tile 3:8:8:2:4)
-    ("sweep3dp_kernel<float, 8, 1, 0>", "3:8:8:2:4"): 348800000,
+    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4"): 348800000,
 }
 
 
@@ -146,7 +146,7 @@ def sweep_kernel_name(p, st):
     dw = st["dirs_per_lane"]
     phi = 0 if p.phi is None or p.Q_amp == 0.0 else 1
     if st["tile_kind"] == 3 and p.dim == 3:
-        return f"sweep3dp_kernel<float, {dw}, {phi}, 0>"
+        return f"sweep3dp_kernel<float, {dw}, {phi}, 0, {int(st['lane_axis'] == 2)}>"
     if st["tile_kind"] == 3:
         return f"sweep2dp_kernel<float, {dw}, 8, {phi}, 0, {st['source_staged']}>"
     if st["tile_kind"] == 2:

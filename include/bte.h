@@ -140,8 +140,10 @@ typedef struct {
     int dirs_per_cta;       /* row kernels: directions per CTA (0 = autotuned) */
     int source_staging;     /* row-pipeline kernel: 0 = autotuned, 1 = per-cell source staged in
                                shared memory, 2 = read ahead from global memory */
-    int warps_z;            /* 3D plane-pipeline kernel: warps along z per CTA (planes in
-                               flight per pass); 0 = autotuned */
+    int warps_z;            /* 3D plane-pipeline kernel: warps along the plane axis per CTA
+                               (planes in flight per pass); 0 = autotuned */
+    int lane_axis;          /* 3D plane-pipeline kernel: axis of the rows its lanes hold,
+                               1 = y (planes along z), 2 = z (planes along y); 0 = autotuned */
 } bte_solve_opts;
 
 typedef struct {
@@ -161,7 +163,9 @@ typedef struct {
     long long sweep_launches; /* number of sweep launches summed in sweep_seconds */
     int source_staged;      /* row-pipeline tile: 1 = per-cell source staged in shared memory,
                                0 = read ahead from global memory (other kernels: 1) */
-    int warps_z;            /* 3D plane-pipeline tile: warps along z per CTA (other kernels: 0) */
+    int warps_z;            /* 3D plane-pipeline tile: warps along the plane axis per CTA
+                               (other kernels: 0) */
+    int lane_axis;          /* 3D plane-pipeline tile: row axis, 1 = y, 2 = z (other kernels: 0) */
 } bte_stats;
 
 /* Fill opts with defaults: FP32, tol 1e-6, max_iter 100000, T_init 300 K,

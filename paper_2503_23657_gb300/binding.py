@@ -62,7 +62,7 @@ class SolveOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("poll_every", ctypes.c_int),
                 ("dirs_per_lane", ctypes.c_int), ("store_e_every_iter", ctypes.c_int),
                 ("tile_kind", ctypes.c_int), ("dirs_per_cta", ctypes.c_int), ("source_staging", ctypes.c_int),
-                ("warps_z", ctypes.c_int)]
+                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -72,7 +72,7 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("tile_kind", ctypes.c_int),
                 ("dirs_per_cta", ctypes.c_int), ("sweep_seconds", ctypes.c_double),
                 ("sweep_launches", ctypes.c_longlong), ("source_staged", ctypes.c_int),
-                ("warps_z", ctypes.c_int)]
+                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -221,7 +221,7 @@ class Plan:
     def solve(self, T_out, q_out=None, e_out=None, precision=BTE_FP32, tol=1e-6, max_iter=100000,
               T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None,
               poll_every=32, dirs_per_lane=0, store_e_every_iter=False, tile_kind=0, dirs_per_cta=0,
-              source_staging=0, warps_z=0, check=True):
+              source_staging=0, warps_z=0, lane_axis=0, check=True):
         """Run bte_solve.  Buffers are numpy arrays (host) or torch tensors
         (host or CUDA) of the documented sizes.  Returns (rc, stats dict)."""
         p = self.problem
@@ -245,6 +245,7 @@ class Plan:
         o.dirs_per_cta = dirs_per_cta
         o.source_staging = source_staging
         o.warps_z = warps_z
+        o.lane_axis = lane_axis
         st = Stats()
         rc = self._lib.bte_solve(self._h, ctypes.byref(o), _addr(T_out), _addr(q_out), _addr(e_out),
                                  ctypes.byref(st))

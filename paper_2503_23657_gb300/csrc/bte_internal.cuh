@@ -45,21 +45,25 @@ __host__ __device__ inline int face_of(int base, int flags, int side) {
 
 // Diagonal-skewed copy of a per-cell field (plane-pipeline 3D sweep).  A warp
 // of that sweep updates, at one step, one cell of each of its 32 rows, on a
-// diagonal of the (x, y) plane whose direction depends on the octant: X + Y
-// constant when the sweep runs along x and y in the same sense, X - Y
-// constant otherwise.  Family 0 keys a cell (X, Y, Z) by X + Y, family 1 by
-// X + (ny - 1 - Y); rows are innermost, so those 32 cells are 32 consecutive
+// diagonal of the plane spanned by x and the row axis (y, or z when the
+// lanes run along z; coordinate R, extent n1, the remaining axis P being
+// the plane index) whose direction depends on the octant: X + R constant
+// when the sweep runs along x and the row axis in the same sense, X - R
+// constant otherwise.  Family 0 keys a cell by X + R, family 1 by
+// X + (n1 - 1 - R); rows are innermost, so those 32 cells are 32 consecutive
 // entries of one family.  Entries that are no cell (X outside the grid)
 // hold zero.
 struct SkewLayout {
-    int nx, ny;
-    int nd;          // nx + ny - 1 diagonals per plane
-    int nyp;         // entries per diagonal (ny rounded up to 32)
-    long long fam;   // entries of one family (nz * nd * nyp)
+    int nx, ny;      // grid (x, y extents: decode a cell index)
+    int a1;          // row axis: 1 = y, 2 = z
+    int n1;          // rows (extent of the row axis)
+    int nd;          // nx + n1 - 1 diagonals per plane
+    int nyp;         // entries per diagonal (n1 rounded up to 32)
+    long long fam;   // entries of one family (planes * nd * nyp)
 };
-__host__ __device__ inline long long skew_index(const SkewLayout &L, int f, int X, int Y, int Z) {
-    const int key = f ? X + (L.ny - 1 - Y) : X + Y;
-    return f * L.fam + ((long long)Z * L.nd + key) * L.nyp + Y;
+__host__ __device__ inline long long skew_index(const SkewLayout &L, int f, int X, int R, int P) {
+    const int key = f ? X + (L.n1 - 1 - R) : X + R;
+    return f * L.fam + ((long long)P * L.nd + key) * L.nyp + R;
 }
 
 // A subset of directions that share one sweep orientation (the signs of the
@@ -184,7 +188,8 @@ struct Sweep3DParams {
     int nx, ny, nz;
     int B, D, F, S, R;                // S = direction subsets (cell and face-sum sets)
     int Spad;                         // S rounded up to a multiple of 4
-    int WY, H;                        // warps along y, warps along z
+    int WY, H;                        // warps along the row axis, warps along the plane axis
+    int lane_axis;                    // row (lane) axis: 1 = y, 2 = z; planes along the other
     long long N;
     SkewLayout skew;                  // layout of the three skewed per-cell inputs
     const int2 *__restrict__ cell;    // skewed {face base, flags}

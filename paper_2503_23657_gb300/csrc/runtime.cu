@@ -86,9 +86,10 @@ struct Workspace {
     DevBuf wrap;      // plane-pipeline 3D sweep: last plane of a pass, per CTA
     // plane-pipeline 3D sweep: skewed copies of the cell records, the source
     // profile and the forward / adjoint sweep sources (both parities)
-    DevBuf skc, skphi, skt[2], ska[2];
-    SkewLayout skew{};
-    bool skew_ready = false;
+    // (one set per row axis: [0] rows along y, [1] rows along z)
+    DevBuf skc[2], skphi[2], skt[2][2], ska[2][2];
+    SkewLayout skew[2]{};
+    bool skew_ready[2] = {false, false};
     // graph cache
     cudaGraphExec_t graph = nullptr;
     std::tuple<int, int, double, int> graph_key{-1, -1, 0.0, -1};
@@ -260,6 +261,11 @@ inline bool defers_finalize(int kind) { return is_rowpipe(kind) || is_pipe3(kind
 // directions one CTA handles
 inline int tile_cta_dirs(const Tile &t) { return is_pipe3(t.kind) ? t.dw : t.cw; }
 inline int source_staged_kind(int kind) { return (kind == 4 || kind == 5) ? 0 : 1; }
+// plane-pipeline tiles: cw = H + 20 map, map 0 = rows along y, 1 = rows along z
+inline int pipe3_h(const Tile &t) { return t.cw % 20; }
+inline int pipe3_map(const Tile &t) { return t.cw / 20; }
+inline int pipe3_rows(const bte_plan *p, int map) { return map ? p->nz : p->ny; }
+inline int pipe3_planes(const bte_plan *p, int map) { return map ? p->ny : p->nz; }
 
 // Directions of one orientation group split into subsets of at most dw.
 std::vector<Subset> make_subsets(const bte_plan *p, int dw, bool flip) {
@@ -324,33 +330,34 @@ bool rowpipe_ok(const bte_plan *p, int real_bytes, int groups, int dw, int stage
 // more than H planes streams in passes, which needs two warps along z and
 // nx >= 4 H + 2 (the next pass reads the last plane of the previous one two
 // steps ahead, a chunk after it was written).
-bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H) {
+bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H, int map) {
     if (p->dim != 3 || H < 1 || (real_bytes == 8 && dw > 4)) return false;
     if (p->N >= (1LL << 31) - 1) return false;
-    const long long skew_entries = 2LL * p->nz * (p->nx + p->ny - 1) * (((p->ny + 31) / 32) * 32) + 32;
+    const int n1 = pipe3_rows(p, map), n2 = pipe3_planes(p, map);
+    const long long skew_entries = 2LL * n2 * (p->nx + n1 - 1) * (((n1 + 31) / 32) * 32) + 32;
     if (skew_entries >= (1LL << 31) - 1) return false;
-    const int WY = (p->ny + 31) / 32;
-    if (WY * H > 16 || H > p->nz) return false;
-    const int M = (p->nz + H - 1) / H;
+    const int WY = (n1 + 31) / 32;
+    if (WY * H > 16 || H > n2) return false;
+    const int M = (n2 + H - 1) / H;
     if (M > 1 && (H < 2 || p->nx < kPipe3Chunk * H + 2)) return false;
     return sweep3dp_smem(p->R, WY, H, dw, real_bytes) <= 225 * 1024;
 }
 
 // Warps along z offered for the plane-pipeline kernel: the most that fit,
 // and about half of that (two CTAs per SM).
-std::vector<int> pipe3_heights(const bte_plan *p, int real_bytes, int dw) {
+std::vector<int> pipe3_heights(const bte_plan *p, int real_bytes, int dw, int map) {
     std::vector<int> out;
-    const int WY = (p->ny + 31) / 32;
+    const int WY = (pipe3_rows(p, map) + 31) / 32;
     int hmax = 0;
-    for (int H = std::min(16 / std::max(WY, 1), p->nz); H >= 1; --H)
-        if (pipe3_ok(p, real_bytes, dw, H)) {
+    for (int H = std::min(16 / std::max(WY, 1), pipe3_planes(p, map)); H >= 1; --H)
+        if (pipe3_ok(p, real_bytes, dw, H, map)) {
             hmax = H;
             break;
         }
     if (hmax == 0) return out;
     out.push_back(hmax);
     for (int H = (hmax + 1) / 2; H >= 1 && H < hmax; --H)
-        if (pipe3_ok(p, real_bytes, dw, H)) {
+        if (pipe3_ok(p, real_bytes, dw, H, map)) {
             out.push_back(H);
             break;
         }
@@ -360,7 +367,7 @@ std::vector<int> pipe3_heights(const bte_plan *p, int real_bytes, int dw) {
 // Candidate tiles for a precision; kind_req 0 = any, 1 = general only,
 // 2 = row-block only, 3 = row-pipeline only.
 std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req = 0, int dw_req = 0,
-                                 int cw_req = 0, int staging_req = 0, int wz_req = 0) {
+                                 int cw_req = 0, int staging_req = 0, int wz_req = 0, int axis_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
     if (lz != 0 && (kind_req == 0 || kind_req == 1)) {
@@ -392,11 +399,16 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
     if ((kind_req == 0 || kind_req == 3) && staging_req != 1) {
         for (int dw : {2, 4, 8}) {
             if ((dw_req && dw != dw_req) || (cw_req && dw != cw_req)) continue;
-            if (wz_req) {
-                if (pipe3_ok(p, real_bytes, dw, wz_req)) out.push_back(tile_id(5, dw, wz_req));
-                continue;
+            // rows along y, and along z where that differs (a grid whose z
+            // extent fills the 32 lanes better)
+            for (int map = 0; map < 2; ++map) {
+                if (axis_req ? (map != axis_req - 1) : (map == 1 && p->nz == p->ny)) continue;
+                if (wz_req) {
+                    if (pipe3_ok(p, real_bytes, dw, wz_req, map)) out.push_back(tile_id(5, dw, wz_req + 20 * map));
+                    continue;
+                }
+                for (int H : pipe3_heights(p, real_bytes, dw, map)) out.push_back(tile_id(5, dw, H + 20 * map));
             }
-            for (int H : pipe3_heights(p, real_bytes, dw)) out.push_back(tile_id(5, dw, H));
         }
     }
     if ((kind_req == 0 || kind_req == 2) && rowblock_ok(p, real_bytes, &stage)) {
@@ -429,41 +441,43 @@ int cell_sets(int tid, int chunks) {
 // Skewed per-cell inputs of the plane-pipeline 3D sweep (built once per plan
 // and precision; the sweep sources follow every update).
 template <typename real>
-int ensure_skew(bte_plan *p, Workspace<real> &ws) {
-    if (ws.skew_ready) return BTE_OK;
+int ensure_skew(bte_plan *p, Workspace<real> &ws, int map) {
+    if (ws.skew_ready[map]) return BTE_OK;
     SkewLayout L{};
     L.nx = p->nx;
     L.ny = p->ny;
-    L.nd = p->nx + p->ny - 1;
-    L.nyp = ((p->ny + 31) / 32) * 32;
-    L.fam = (long long)p->nz * L.nd * L.nyp;
+    L.a1 = 1 + map;
+    L.n1 = pipe3_rows(p, map);
+    L.nd = p->nx + L.n1 - 1;
+    L.nyp = ((L.n1 + 31) / 32) * 32;
+    L.fam = (long long)pipe3_planes(p, map) * L.nd * L.nyp;
     const size_t n = 2 * (size_t)L.fam + 32;  // both families + a zero pad entry
-    CK(p, ws.skc.ensure(sizeof(int2) * n));
-    CK(p, cudaMemset(ws.skc.p, 0, sizeof(int2) * n));
-    CK(p, ws.skphi.ensure(sizeof(real) * n));
-    CK(p, cudaMemset(ws.skphi.p, 0, sizeof(real) * n));
+    CK(p, ws.skc[map].ensure(sizeof(int2) * n));
+    CK(p, cudaMemset(ws.skc[map].p, 0, sizeof(int2) * n));
+    CK(p, ws.skphi[map].ensure(sizeof(real) * n));
+    CK(p, cudaMemset(ws.skphi[map].p, 0, sizeof(real) * n));
     for (int i = 0; i < 2; ++i) {
-        CK(p, ws.skt[i].ensure(sizeof(real) * n));
-        CK(p, cudaMemset(ws.skt[i].p, 0, sizeof(real) * n));
-        CK(p, ws.ska[i].ensure(sizeof(real) * n));
-        CK(p, cudaMemset(ws.ska[i].p, 0, sizeof(real) * n));
+        CK(p, ws.skt[map][i].ensure(sizeof(real) * n));
+        CK(p, cudaMemset(ws.skt[map][i].p, 0, sizeof(real) * n));
+        CK(p, ws.ska[map][i].ensure(sizeof(real) * n));
+        CK(p, cudaMemset(ws.ska[map][i].p, 0, sizeof(real) * n));
     }
-    CK(p, launch_skew<int2>(p->N, L, p->d_cell.as<int2>(), ws.skc.template as<int2>(), 0));
-    CK(p, launch_skew<real>(p->N, L, ws.phi.template as<real>(), ws.skphi.template as<real>(), 0));
+    CK(p, launch_skew<int2>(p->N, L, p->d_cell.as<int2>(), ws.skc[map].template as<int2>(), 0));
+    CK(p, launch_skew<real>(p->N, L, ws.phi.template as<real>(), ws.skphi[map].template as<real>(), 0));
     for (int i = 0; i < 2; ++i)
-        CK(p, launch_skew<real>(p->N, L, ws.tdev[i].template as<real>(), ws.skt[i].template as<real>(), 0));
+        CK(p, launch_skew<real>(p->N, L, ws.tdev[i].template as<real>(), ws.skt[map][i].template as<real>(), 0));
     CK(p, cudaDeviceSynchronize());
-    ws.skew = L;
-    ws.skew_ready = true;
+    ws.skew[map] = L;
+    ws.skew_ready[map] = true;
     return BTE_OK;
 }
 
-// skewed copy of a natural-order sweep source of the workspace
+// skewed copy (row-axis map `map`) of a natural-order sweep source of the workspace
 template <typename real>
-const real *skewed_source(Workspace<real> &ws, const real *tsrc) {
+const real *skewed_source(Workspace<real> &ws, const real *tsrc, int map) {
     for (int i = 0; i < 2; ++i) {
-        if (tsrc == ws.tdev[i].template as<real>()) return ws.skt[i].template as<real>();
-        if (tsrc == ws.thdev[i].template as<real>()) return ws.ska[i].template as<real>();
+        if (tsrc == ws.tdev[i].template as<real>()) return ws.skt[map][i].template as<real>();
+        if (tsrc == ws.thdev[i].template as<real>()) return ws.ska[map][i].template as<real>();
     }
     return nullptr;
 }
@@ -472,7 +486,7 @@ template <typename real>
 int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
     if (ws.dsub.count(tid)) return BTE_OK;
     if (is_pipe3(tile_of(tid).kind))
-        if (int rc = ensure_skew(p, ws)) return rc;
+        if (int rc = ensure_skew(p, ws, pipe3_map(tile_of(tid)))) return rc;
     const int cw = tile_cta_dirs(tile_of(tid));  // directions per CTA (general kernel: cw == dw)
     auto f = make_subsets(p, cw, false);
     auto a = make_subsets(p, cw, true);
@@ -486,8 +500,8 @@ int ensure_subsets(bte_plan *p, Workspace<real> &ws, int tid) {
         CK(p, ws.part.ensure(sizeof(real) * Spad * B * N));
         CK(p, ws.fsum.ensure(sizeof(real) * chunks * B * F));
         const Tile tl = tile_of(tid);
-        if (is_pipe3(tl.kind) && (p->nz + tl.cw - 1) / tl.cw > 1) {
-            const size_t ld = (size_t)((p->ny + 31) / 32) * 32;
+        if (is_pipe3(tl.kind) && (pipe3_planes(p, pipe3_map(tl)) + pipe3_h(tl) - 1) / pipe3_h(tl) > 1) {
+            const size_t ld = (size_t)((pipe3_rows(p, pipe3_map(tl)) + 31) / 32) * 32;
             CK(p, ws.wrap.ensure(sizeof(real) * chunks * B * (size_t)p->nx * ld * tl.dw));
         }
         if (ws.part.p != part0 || ws.fsum.p != fsum0 || ws.wrap.p != wrap0) {
@@ -705,7 +719,7 @@ UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool
     u.n_active = p->n_active;
     // row-pipeline tiles finalize each iteration in the next sweep's prologue
     u.defer = defers_finalize(tile_of(tid).kind) ? 1 : 0;
-    u.skew = ws.skew;
+    if (is_pipe3(tile_of(tid).kind)) u.skew = ws.skew[pipe3_map(tile_of(tid))];
     u.fin = fin_params(p, tol, adj);
     return u;
 }
@@ -761,12 +775,14 @@ Sweep3DParams<real> sweep3d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     sp.S = (int)ws.subsets.at(tid).first.size();
     sp.R = p->R;
     sp.Spad = (cell_sets(tid, sp.S) + 3) & ~3;
-    sp.WY = (p->ny + 31) / 32;
-    sp.H = tl.cw;
+    const int map = pipe3_map(tl);
+    sp.lane_axis = 1 + map;
+    sp.WY = (pipe3_rows(p, map) + 31) / 32;
+    sp.H = pipe3_h(tl);
     sp.N = p->N;
-    sp.skew = ws.skew;
-    sp.cell = ws.skc.template as<int2>();
-    sp.phi = p->phi.empty() ? nullptr : ws.skphi.template as<real>();
+    sp.skew = ws.skew[map];
+    sp.cell = ws.skc[map].template as<int2>();
+    sp.phi = p->phi.empty() ? nullptr : ws.skphi[map].template as<real>();
     sp.part = ws.part.template as<real>();
     sp.fsum = ws.fsum.template as<real>();
     sp.e = ws.e.template as<real>();
@@ -790,7 +806,7 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
     const Tile tl = tile_of(tid);
     if (is_pipe3(tl.kind)) {
         Sweep3DParams<real> sp = sweep3d_params(p, ws, tid, adj);
-        sp.tsrc = skewed_source(ws, tsrc);
+        sp.tsrc = skewed_source(ws, tsrc, pipe3_map(tl));
         if (!sp.tsrc) return cudaErrorInvalidValue;
         sp.ein = ein;
         sp.store_e = store_e ? 1 : 0;
@@ -842,7 +858,7 @@ cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int tid, int parit
     u.x_in = ws.T[parity].template as<double>();
     u.x_out = ws.T[parity ^ 1].template as<double>();
     u.xdev_out = ws.tdev[parity ^ 1].template as<real>();
-    if (is_pipe3(tile_of(tid).kind)) u.xskew_out = ws.skt[parity ^ 1].template as<real>();
+    if (is_pipe3(tile_of(tid).kind)) u.xskew_out = ws.skt[pipe3_map(tile_of(tid))][parity ^ 1].template as<real>();
     u.ein_out = ws.ein[parity ^ 1].template as<real>();
     return launch_update<real>(u, stream);
 }
@@ -888,8 +904,10 @@ int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaS
     }
     CK(p, cudaMemcpyAsync(ws.T[0].p, T0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemcpyAsync(ws.tdev[0].p, td.data(), sizeof(real) * N, cudaMemcpyHostToDevice, stream));
-    if (ws.skew_ready)
-        CK(p, launch_skew<real>(N, ws.skew, ws.tdev[0].template as<real>(), ws.skt[0].template as<real>(), stream));
+    for (int map = 0; map < 2; ++map)
+        if (ws.skew_ready[map])
+            CK(p, launch_skew<real>(N, ws.skew[map], ws.tdev[0].template as<real>(), ws.skt[map][0].template as<real>(),
+                                    stream));
     CK(p, cudaMemcpyAsync(ws.ein[0].p, e0.data(), sizeof(real) * e0.size(), cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
@@ -984,11 +1002,14 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     if (o->tile_kind < 0 || o->tile_kind > 3) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1, 2 or 3");
     if (o->source_staging < 0 || o->source_staging > 2) return fail(p, BTE_EINVAL, "source_staging must be 0, 1 or 2");
     if (o->warps_z < 0 || o->warps_z > 16) return fail(p, BTE_EINVAL, "warps_z must be in 0..16");
+    if (o->lane_axis < 0 || o->lane_axis > 2) return fail(p, BTE_EINVAL, "lane_axis must be 0, 1 or 2");
     std::vector<int> cand = tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane, o->dirs_per_cta,
-                                            o->source_staging, o->warps_z);
+                                            o->source_staging, o->warps_z, o->lane_axis);
     if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
     const int tkey =
-        (((o->warps_z * 10 + o->source_staging) * 10 + o->tile_kind) * 100 + o->dirs_per_lane) * 1000 + o->dirs_per_cta;
+        ((((o->lane_axis * 20 + o->warps_z) * 10 + o->source_staging) * 10 + o->tile_kind) * 100 + o->dirs_per_lane) *
+            1000 +
+        o->dirs_per_cta;
     int tid;
     if (ws.tuned.count(tkey)) {
         tid = ws.tuned[tkey];
@@ -1129,7 +1150,8 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         st->sweep_seconds = sweep_ms * 1e-3;
         st->sweep_launches = n_timed;
         st->source_staged = source_staged_kind(tile_of(tid).kind);
-        st->warps_z = is_pipe3(tile_of(tid).kind) ? tile_of(tid).cw : 0;
+        st->warps_z = is_pipe3(tile_of(tid).kind) ? pipe3_h(tile_of(tid)) : 0;
+        st->lane_axis = is_pipe3(tile_of(tid).kind) ? 1 + pipe3_map(tile_of(tid)) : 0;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the temperature update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "max_iter reached before eps_T < tol");
@@ -1155,7 +1177,7 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
         u.x_in = ws.theta[parity].template as<double>();
         u.x_out = ws.theta[parity ^ 1].template as<double>();
         u.xdev_out = ws.thdev[parity ^ 1].template as<real>();
-        if (is_pipe3(tile_of(dw).kind)) u.xskew_out = ws.ska[parity ^ 1].template as<real>();
+        if (is_pipe3(tile_of(dw).kind)) u.xskew_out = ws.ska[pipe3_map(tile_of(dw))][parity ^ 1].template as<real>();
         u.ein_out = ws.mein[parity ^ 1].template as<real>();
         return launch_update<real>(u, stream);
     }
@@ -1234,8 +1256,10 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     CK(p, cudaMemcpyAsync(ws.g.p, g.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemcpyAsync(ws.theta[0].p, th.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
     CK(p, cudaMemcpyAsync(ws.thdev[0].p, thr.data(), sizeof(real) * N, cudaMemcpyHostToDevice, stream));
-    if (ws.skew_ready)
-        CK(p, launch_skew<real>(N, ws.skew, ws.thdev[0].template as<real>(), ws.ska[0].template as<real>(), stream));
+    for (int map = 0; map < 2; ++map)
+        if (ws.skew_ready[map])
+            CK(p, launch_skew<real>(N, ws.skew[map], ws.thdev[0].template as<real>(), ws.ska[map][0].template as<real>(),
+                                    stream));
     CK(p, cudaMemsetAsync(ws.mein[0].p, 0, sizeof(real) * (size_t)B * F, stream));
     CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
@@ -1361,7 +1385,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         st->sweep_seconds = sweep_ms * 1e-3;
         st->sweep_launches = n_timed;
         st->source_staged = source_staged_kind(tile_of(dw).kind);
-        st->warps_z = is_pipe3(tile_of(dw).kind) ? tile_of(dw).cw : 0;
+        st->warps_z = is_pipe3(tile_of(dw).kind) ? pipe3_h(tile_of(dw)) : 0;
+        st->lane_axis = is_pipe3(tile_of(dw).kind) ? 1 + pipe3_map(tile_of(dw)) : 0;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the adjoint update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "adjoint: max_iter reached before tol");

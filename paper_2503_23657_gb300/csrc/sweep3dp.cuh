@@ -6,10 +6,13 @@
 // over a CTA as a pipeline of warps:
 //
 //   * one CTA per (direction subset of DW directions sharing an octant,
-//     band); WY = ceil(ny / 32) warps along y (lane = row) times H warps
-//     along z.  Warp (wy, h) owns rows 32 wy .. 32 wy + 31 of the planes
-//     h, h + H, h + 2H, ... (one pass of H planes after the other); every
-//     lane carries the DW directions in registers;
+//     band).  x is marched; the lanes hold rows along the row axis (y, or z
+//     when the host picks it: lane_axis) and the planes lie along the other
+//     axis.  WY = ceil(rows / 32) warps along the row axis times H warps
+//     along the plane axis; warp (wy, h) owns rows 32 wy .. 32 wy + 31 of
+//     the planes h, h + H, h + 2H, ... (one pass of H planes after the
+//     other); every lane carries the DW directions in registers.  Below,
+//     "y" and "z" name the row and plane axes;
 //   * in canonical (octant-mirrored) coordinates lane l of a warp handles the
 //     virtual column u = tau - l at its local step tau, u = m nx + i meaning
 //     column i of the warp's plane in pass m, so a lane streams through its
@@ -139,7 +142,7 @@ __host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW) {
     return s;
 }
 
-template <typename real, int DW, bool PHI, bool STORE_E>
+template <typename real, int DW, bool PHI, bool STORE_E, bool ZROWS>
 __global__ void __launch_bounds__(kP3MaxThreads, 1)
 sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     constexpr int K = kPipe3Chunk, RZ = kP3RZ, RY = kP3RY;
@@ -152,7 +155,14 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int WY = P.WY, H = P.H;
-    const int nx = P.nx, ny = P.ny, nz = P.nz, R = P.R;
+    const int nx = P.nx, R = P.R;
+    // axis roles: x is marched; the lanes hold rows along a1 (1 = y, 2 = z),
+    // the warps along z of the CTA hold planes along a2 (the other one)
+    constexpr int a1 = ZROWS ? 2 : 1, a2 = 3 - a1;
+    const int n1 = a1 == 1 ? P.ny : P.nz;          // rows
+    const int n2 = a1 == 1 ? P.nz : P.ny;          // planes
+    const int s1 = a1 == 1 ? nx : nx * P.ny;       // cell stride of the next row
+    const int s2 = a1 == 1 ? nx * P.ny : nx;       // cell stride of the next plane
     const P3Smem L = p3_smem(R, WY, H, DW);
     real *sm = reinterpret_cast<real *>(smem_raw);
     real *s_invd = sm + L.invd;
@@ -200,18 +210,18 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     // ---- this warp: rows 32 wy .. 32 wy + 31 of planes h + H m ----
     const int wy = warp % WY;
     const int h = warp / WY;
-    const bool negx = sub.neg & 1, negy = (sub.neg >> 1) & 1, negz = (sub.neg >> 2) & 1;
-    const int up_x = negx ? 1 : 0, up_y = negy ? 3 : 2, up_z = negz ? 5 : 4;
-    const unsigned dn_mask = (1u << (up_x ^ 1)) | (1u << (up_y ^ 1)) | (1u << (up_z ^ 1));
-    const unsigned below_x = (1u << up_x) - 1u, below_y = (1u << up_y) - 1u, below_z = (1u << up_z) - 1u;
+    const bool negx = sub.neg & 1, neg1 = (sub.neg >> a1) & 1, neg2 = (sub.neg >> a2) & 1;
+    const int up_x = negx ? 1 : 0, up_1 = 2 * a1 + (neg1 ? 1 : 0), up_2 = 2 * a2 + (neg2 ? 1 : 0);
+    const unsigned dn_mask = (1u << (up_x ^ 1)) | (1u << (up_1 ^ 1)) | (1u << (up_2 ^ 1));
+    const unsigned below_x = (1u << up_x) - 1u, below_1 = (1u << up_1) - 1u, below_2 = (1u << up_2) - 1u;
     real ax[DW], ay[DW], az[DW], w[DW];
 #pragma unroll
     for (int dd = 0; dd < DW; ++dd) {
         if (dd < ndir) {
             const real *cf = P.coef + ((long long)b * P.D + d0 + dd) * 8;
             ax[dd] = cf[0];
-            ay[dd] = cf[1];
-            az[dd] = cf[2];
+            ay[dd] = cf[a1];   // coefficient of the row (lane) axis
+            az[dd] = cf[a2];   // coefficient of the plane axis
             w[dd] = cf[3];
         } else {
             ax[dd] = ay[dd] = az[dd] = w[dd] = real(0);
@@ -220,30 +230,29 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const real qb = PHI ? P.qb[b] : real(0);
     const real *einb = P.ein + (long long)b * P.F;
     const int j = 32 * wy + lane;
-    const bool rowv = j < ny;
-    const int Y = negy ? ny - 1 - j : j;
-    const int M = (nz + H - 1) / H;        // passes
-    const int Mh = (nz - h + H - 1) / H;   // passes in which this warp's plane lies in the grid
+    const bool rowv = j < n1;
+    const int Y = neg1 ? n1 - 1 - j : j;
+    const int M = (n2 + H - 1) / H;        // passes
+    const int Mh = (n2 - h + H - 1) / H;   // passes in which this warp's plane lies in the grid
     const int U = M * nx;                  // virtual columns of a lane
     const int n_loc = (U + 31 + 31) & ~31; // local steps (whole 32-step tiles)
     constexpr int Ly = 32 + K, Lz = K;     // lag of the next warp along y / z
     const int delta = wy * Ly + h * Lz;
     const int T = (WY - 1) * Ly + (H - 1) * Lz + n_loc;
-    const int nxny = nx * ny;
     const int ld_wrap = WY * 32;
     const int sx = negx ? -1 : 1;          // dX / di
-    const int sz = negz ? -1 : 1;          // dZ / dk
+    const int sz = neg2 ? -1 : 1;          // dZ / dk
     const float inv_nx = 1.0f / (float)nx;
     // skewed inputs: the family of this octant (X + Y or X - Y constant
     // along a step); index of column i of pass m of this lane:
     //   sk0 + sx nyp i + sz H nd nyp m  (within a pass; see SkewLayout)
     // and a zero pad entry (2 fam) for the cells outside the grid
-    const int fam = (negx != negy) ? 1 : 0;
+    const int fam = (negx != neg1) ? 1 : 0;
     const int sk_nd = P.skew.nd, sk_nyp = P.skew.nyp;
     const int sk_pad = 2 * (int)P.skew.fam;
     const int X0 = negx ? nx - 1 : 0;
-    const int Zh = negz ? nz - 1 - h : h;
-    const int key0 = fam ? X0 + (ny - 1 - Y) : X0 + Y;
+    const int Zh = neg2 ? n2 - 1 - h : h;
+    const int key0 = fam ? X0 + (n1 - 1 - Y) : X0 + Y;
     const int sk0 = (fam ? (int)P.skew.fam : 0) + (Zh * sk_nd + key0) * sk_nyp + Y;
     const int dsk = sx * sk_nyp;                                   // next column
     const int dsk_pass = (sz * H * sk_nd - sx * (nx - 1)) * sk_nyp; // column 0 of the next pass
@@ -274,8 +283,8 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         if (STORE_E) {
             const int X = negx ? nx - 1 - ui : ui;
             const int k = h + H * um;
-            const int Z = negz ? nz - 1 - k : k;
-            rc[STORE_E ? q : 0] = v ? X + nx * Y + nxny * Z : -1;
+            const int Z = neg2 ? n2 - 1 - k : k;
+            rc[STORE_E ? q : 0] = v ? X + s1 * Y + s2 * Z : -1;
         }
         // wrap buffer column: read by the first warp of a pass (the value is
         // used only past the first pass), written by the last one
@@ -301,8 +310,8 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         dt[slot] = __ldg(P.tsrc + sk);
         if (PHI) dp[slot] = __ldg(P.phi + sk);
         const int fx = ((bm >> up_x) & 1u) ? fb + __popc(bm & below_x) : 0;
-        const int fy = ((bm >> up_y) & 1u) ? fb + __popc(bm & below_y) : 0;
-        const int fz = ((bm >> up_z) & 1u) ? fb + __popc(bm & below_z) : 0;
+        const int fy = ((bm >> up_1) & 1u) ? fb + __popc(bm & below_1) : 0;
+        const int fz = ((bm >> up_2) & 1u) ? fb + __popc(bm & below_2) : 0;
         dex[slot] = __ldg(einb + fx);
         dey[slot] = __ldg(einb + fy);
         dez[slot] = __ldg(einb + fz);
@@ -350,8 +359,8 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 const bool act = region != 0;   // solid cell of the grid
                 const unsigned bm = ((unsigned)fl >> kSideShift) & 63u;
                 const bool bx = (bm >> up_x) & 1u;
-                const bool by = (bm >> up_y) & 1u;
-                const bool bz = (bm >> up_z) & 1u;
+                const bool by = (bm >> up_1) & 1u;
+                const bool bz = (bm >> up_2) & 1u;
                 const int r = act ? region - 1 : 0;
                 real base = tsv * s_srck[r];
                 if (PHI) base += phv * qb;
@@ -390,11 +399,12 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 if (act && (bm & dn_mask)) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        const int dn = (a == 0 ? up_x : (a == 1 ? up_y : up_z)) ^ 1;
+                        const int dn = (a == 0 ? up_x : (a == 1 ? up_1 : up_2)) ^ 1;
+                        const int pa = a == 0 ? 0 : (a == 1 ? a1 : a2);   // physical axis
                         if (!((bm >> dn) & 1u)) continue;
                         real fs = real(0);
 #pragma unroll
-                        for (int dd = 0; dd < DW; ++dd) fs = fma(s_fw[a * DW + dd], old[dd], fs);
+                        for (int dd = 0; dd < DW; ++dd) fs = fma(s_fw[pa * DW + dd], old[dd], fs);
                         fs_sb[face_of(fb, fl, dn)] = fs;
                     }
                 }
@@ -430,12 +440,12 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                         --m;
                     }
                     const int k = h + H * m;
-                    if (m >= 0 && k < nz && 32 * wy + rr < ny) {
+                    if (m >= 0 && k < n2 && 32 * wy + rr < n1) {
                         const int X = negx ? nx - 1 - i : i;
                         const int jr = 32 * wy + rr;
-                        const int Yr = negy ? ny - 1 - jr : jr;
-                        const int Z = negz ? nz - 1 - k : k;
-                        part_b[X + nx * Yr + nxny * Z] = tile[rr * 33 + lane];
+                        const int Yr = neg1 ? n1 - 1 - jr : jr;
+                        const int Z = neg2 ? n2 - 1 - k : k;
+                        part_b[X + s1 * Yr + s2 * Z] = tile[rr * 33 + lane];
                     }
                 }
                 __syncwarp();
@@ -450,12 +460,12 @@ size_t sweep3dp_smem_bytes(int R, int WY, int H, int dw) {
     return (size_t)p3_smem(R, WY, H, dw).total * sizeof(real);
 }
 
-template <typename real, int DW, bool PHI, bool STORE_E>
+template <typename real, int DW, bool PHI, bool STORE_E, bool ZROWS>
 cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
     const int threads = p.WY * p.H * 32;
     if (p.H < 1 || p.WY < 1 || threads > kP3MaxThreads) return cudaErrorInvalidConfiguration;
     const size_t smem = sweep3dp_smem_bytes<real>(p.R, p.WY, p.H, DW);
-    auto kern = sweep3dp_kernel<real, DW, PHI, STORE_E>;
+    auto kern = sweep3dp_kernel<real, DW, PHI, STORE_E, ZROWS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -464,12 +474,22 @@ cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
 }
 
 // the source-profile term only in forward sweeps with a source; e only when asked
-template <typename real, int DW>
-cudaError_t launch_sweep3dp_t(const Sweep3DParams<real> &p, cudaStream_t st) {
+template <typename real, int DW, bool ZROWS>
+cudaError_t launch_sweep3dp_z(const Sweep3DParams<real> &p, cudaStream_t st) {
     const bool phi = !p.adj && p.phi != nullptr;
     if (p.store_e)
-        return phi ? launch_sweep3dp_v<real, DW, true, true>(p, st) : launch_sweep3dp_v<real, DW, false, true>(p, st);
-    return phi ? launch_sweep3dp_v<real, DW, true, false>(p, st) : launch_sweep3dp_v<real, DW, false, false>(p, st);
+        return phi ? launch_sweep3dp_v<real, DW, true, true, ZROWS>(p, st)
+                   : launch_sweep3dp_v<real, DW, false, true, ZROWS>(p, st);
+    return phi ? launch_sweep3dp_v<real, DW, true, false, ZROWS>(p, st)
+               : launch_sweep3dp_v<real, DW, false, false, ZROWS>(p, st);
+}
+
+// rows along y or along z
+template <typename real, int DW>
+cudaError_t launch_sweep3dp_t(const Sweep3DParams<real> &p, cudaStream_t st) {
+    if (p.lane_axis == 1) return launch_sweep3dp_z<real, DW, false>(p, st);
+    if (p.lane_axis == 2) return launch_sweep3dp_z<real, DW, true>(p, st);
+    return cudaErrorInvalidConfiguration;
 }
 
 }  // namespace bte

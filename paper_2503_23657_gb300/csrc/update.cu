@@ -36,8 +36,10 @@ __device__ __forceinline__ void skew_store(const SkewLayout &L, long long c, T v
     const int X = (int)(c - row * L.nx);
     const int Y = (int)(row % L.ny);
     const int Z = (int)(row / L.ny);
-    dst[skew_index(L, 0, X, Y, Z)] = v;
-    dst[skew_index(L, 1, X, Y, Z)] = v;
+    const int R = L.a1 == 1 ? Y : Z;   // row coordinate
+    const int P = L.a1 == 1 ? Z : Y;   // plane coordinate
+    dst[skew_index(L, 0, X, R, P)] = v;
+    dst[skew_index(L, 1, X, R, P)] = v;
 }
 
 template <typename real>

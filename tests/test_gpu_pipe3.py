@@ -30,17 +30,20 @@ def bte():
     return m
 
 
-def heights(n):
-    """Warps along z the kernel accepts for an nx x ny x nz grid: at most 16
-    warps per CTA (ceil(ny / 32) along y), and a grid of several passes needs
-    two warps along z and nx >= 4 H + 2."""
+def heights(n, lane_axis=1):
+    """Warps along the plane axis the kernel accepts for an nx x ny x nz grid
+    whose lanes hold rows along y (lane_axis 1, planes along z) or z
+    (lane_axis 2, planes along y): at most 16 warps per CTA (ceil(rows / 32)
+    along the rows), and a grid of several passes needs two warps along the
+    planes and nx >= 4 H + 2."""
     nx, ny, nz = n
-    wy = -(-ny // 32)
+    rows, planes = (ny, nz) if lane_axis == 1 else (nz, ny)
+    wy = -(-rows // 32)
     out = []
     for H in range(1, 17):
-        if wy * H > 16 or H > nz:
+        if wy * H > 16 or H > planes:
             continue
-        if -(-nz // H) > 1 and (H < 2 or nx < 4 * H + 2):
+        if -(-planes // H) > 1 and (H < 2 or nx < 4 * H + 2):
             continue
         out.append(H)
     return out
@@ -62,21 +65,23 @@ CASES = [
 
 @pytest.mark.parametrize("name,kw", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("dw", [2, 4, 8])
-def test_fp32_fixed_iterations(bte, name, kw, dw):
+@pytest.mark.parametrize("axis", [1, 2], ids=["rows_y", "rows_z"])
+def test_fp32_fixed_iterations(bte, name, kw, dw, axis):
     p = bi.tiny(3, **kw)
     k = 12
     ref = oracle.solve(p, max_iter=k, tol=0.0)
     act = p.mask > 0
     plan = bte.Plan(p)
-    hs = heights(p.n)
+    hs = heights(p.n, axis)
     assert hs, "every case has a plane-pipeline tile"
     T_gen = np.zeros(p.n_cells)
     plan.solve(T_gen, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw if dw != 2 else 4, tile_kind=1)
     for H in sorted({hs[0], hs[len(hs) // 2], hs[-1]}):
         T = np.zeros(p.n_cells)
         rc, st = plan.solve(T, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=3,
-                            warps_z=H)
+                            warps_z=H, lane_axis=axis)
         assert st["tile_kind"] == 3 and st["warps_z"] == H and st["dirs_per_lane"] == dw
+        assert st["lane_axis"] == axis
         assert st["iterations"] == k
         assert rel(T, ref["T"], act) < 1e-5
         assert np.abs(T - ref["T"])[act].max() < 1e-4 * np.ptp(ref["T"][act]) + 1e-9
@@ -95,7 +100,8 @@ def test_matches_general_kernel_bitwise_at_same_grouping(bte, name, kw):
     plan.solve(T_gen, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=4, tile_kind=1)
     for H in heights(p.n)[-2:]:
         T = np.zeros(p.n_cells)
-        plan.solve(T, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=4, tile_kind=3, warps_z=H)
+        plan.solve(T, precision=bte.BTE_FP32, tol=0.0, max_iter=k, dirs_per_lane=4, tile_kind=3, warps_z=H,
+                   lane_axis=1)
         np.testing.assert_array_equal(T, T_gen)
 
 
@@ -158,37 +164,43 @@ def test_adjoint_matches_oracle_and_fd(bte):
 
 def test_adjoint_passes_matches_general(bte):
     """Several passes and a mask: the FP32 adjoint gradients of the plane
-    pipeline agree with the general kernel's to 1e-4."""
+    pipeline (rows along y and along z) agree with the general kernel's to
+    1e-4."""
     p = bi.tiny(3, **CASES[3][1])
     plan = bte.Plan(p)
     act = np.flatnonzero(p.mask)
     g = np.zeros(p.n_cells)
     g[act[[3, 200, 1500, act.size - 7]]] = [1.0, -0.5, 0.25, 2.0]
     out = []
-    for kind in (1, 3):
+    for kind, axis in ((1, 0), (3, 1), (3, 2)):
         T = np.zeros(p.n_cells)
-        plan.solve(T, precision=bte.BTE_FP32, tol=1e-7, tile_kind=kind, dirs_per_lane=4, check=False)
+        rc, st = plan.solve(T, precision=bte.BTE_FP32, tol=1e-7, tile_kind=kind, dirs_per_lane=4, lane_axis=axis,
+                            check=False)
+        assert st["lane_axis"] == axis
         rc, g_tau, g_Tw, g_Q, st = plan.adjoint(g, tol=1e-7, check=False)
         out.append((g_tau, g_Tw, g_Q))
-    np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-4)
-    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-4, atol=1e-4 * np.abs(out[0][1]).max())
-    assert out[1][2] == pytest.approx(out[0][2], rel=1e-4)
+    for o in out[1:]:
+        np.testing.assert_allclose(o[0], out[0][0], rtol=1e-4)
+        np.testing.assert_allclose(o[1], out[0][1], rtol=1e-4, atol=1e-4 * np.abs(out[0][1]).max())
+        assert o[2] == pytest.approx(out[0][2], rel=1e-4)
 
 
 @pytest.mark.parametrize("name,kw", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("dw", [2, 4])
-def test_fp64_fixed_iterations(bte, name, kw, dw):
+@pytest.mark.parametrize("axis", [1, 2], ids=["rows_y", "rows_z"])
+def test_fp64_fixed_iterations(bte, name, kw, dw, axis):
     """FP64 sweeps through the plane pipeline: within 1e-12 of the oracle."""
     p = bi.tiny(3, **kw)
     k = 7
     ref = oracle.solve(p, max_iter=k, tol=0.0)
     act = p.mask > 0
     plan = bte.Plan(p)
-    for H in sorted({heights(p.n)[0], heights(p.n)[-1]}):
+    hs = heights(p.n, axis)
+    for H in sorted({hs[0], hs[-1]}):
         T = np.zeros(p.n_cells)
         rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=k, dirs_per_lane=dw, tile_kind=3,
-                            warps_z=H)
-        assert st["tile_kind"] == 3 and st["warps_z"] == H
+                            warps_z=H, lane_axis=axis)
+        assert st["tile_kind"] == 3 and st["warps_z"] == H and st["lane_axis"] == axis
         assert rel(T, ref["T"], act) < 1e-12
 
 
@@ -203,6 +215,8 @@ def test_rejections(bte):
     rc, st = plan.solve(T, tol=0.0, max_iter=2, tile_kind=3, warps_z=bad[0], check=False)
     assert rc == binding.BTE_EINVAL
     rc, st = plan.solve(T, tol=0.0, max_iter=2, tile_kind=3, warps_z=17, check=False)
+    assert rc == binding.BTE_EINVAL
+    rc, st = plan.solve(T, tol=0.0, max_iter=2, tile_kind=3, lane_axis=3, check=False)
     assert rc == binding.BTE_EINVAL
     rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=2, tile_kind=3, dirs_per_lane=8, check=False)
     assert rc == binding.BTE_EINVAL

@@ -85,6 +85,8 @@ def test_model_detects_a_too_short_row():
 
 
 def skew_index(nx, ny, nz, f, X, Y, Z):
+    """Rows along y: row coordinate Y, plane coordinate Z (for rows along z
+    call it with the roles of y and z exchanged)."""
     nyp = 32 * (-(-ny // 32))
     nd = nx + ny - 1
     fam = nz * nd * nyp
