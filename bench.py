@@ -118,7 +118,7 @@ NCU_TRAFFIC = {
     # profiles/sweep2dp_square128.md: 202.2 KB read + 1.5 KB written (128 x 128 square, tile 3:4:4:1)
     ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 203776,
     # profiles/sweep3dp_hotspot64.md: 77.6 MB read + 271.2 MB written (64^3 hotspot, 15 bands, tile 3:8:8:2:4)
-    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4"): 348800000,
+    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4:1"): 348800000,
 }
 
 
@@ -254,8 +254,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     ap.add_argument("--store-e-every-iter", action="store_true")
     ap.add_argument("--tile", default="0:0:0:0",
-                    help="sweep tile kind:dirs_per_lane:dirs_per_cta:source_staging[:warps_z] "
-                         "(0:0:0:0 = autotuned; warps_z: the 3D plane-pipeline kernel's warps along z); "
+                    help="sweep tile kind:dirs_per_lane:dirs_per_cta:source_staging[:warps_z[:lane_axis]] "
+                         "(0:0:0:0 = autotuned; warps_z, lane_axis: the 3D plane-pipeline kernel's warps along "
+                         "the plane axis and its row axis, 1 = y, 2 = z); "
                          "profiling runs pin the tile the autotuner chose, since timings under a profiler are "
                          "not representative")
     args = ap.parse_args()
@@ -375,13 +376,14 @@ def run_single(p, ctx):
     g = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     per_update = p.n_active * p.B * p.D
-    tile_kind, tile_dw, tile_cw, tile_st, tile_wz = ((int(x) for x in (args.tile + ":0:0:0:0:0").split(":")[:5]))
+    tile_kind, tile_dw, tile_cw, tile_st, tile_wz, tile_ax = (
+        int(x) for x in (args.tile + ":0:0:0:0:0:0").split(":")[:6])
 
     def step():
         rc, sf = plan.solve(T, precision=prec, tol=tol, max_iter=100000, stream=sp,
                             store_e_every_iter=args.store_e_every_iter, tile_kind=tile_kind,
                             dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st,
-                            warps_z=tile_wz)
+                            warps_z=tile_wz, lane_axis=tile_ax)
         sa = None
         if ctx["with_adj"]:
             g.zero_()
@@ -425,7 +427,7 @@ def run_single(p, ctx):
     dw = fstats[-1]["dirs_per_lane"]
     tile = f"{fstats[-1]['tile_kind']}:{dw}:{fstats[-1]['dirs_per_cta']}:{2 - fstats[-1]['source_staged']}"
     if fstats[-1]["warps_z"]:
-        tile += f":{fstats[-1]['warps_z']}"
+        tile += f":{fstats[-1]['warps_z']}:{fstats[-1]['lane_axis']}"
     kernel = sweep_kernel_name(p, fstats[-1])
     roofline = roofline_object(kernel, tile, sweep_ms, per_update, p.B, p.D, {
         "sweep_launches_timed": fwd_sweeps + adj_sweeps,
@@ -445,7 +447,7 @@ def run_single(p, ctx):
         t0 = time.perf_counter()
         rc, sf = plan.solve(T_h, T_init=T_init_h, precision=prec, tol=tol, max_iter=100000, stream=sp,
                             tile_kind=tile_kind, dirs_per_lane=tile_dw, dirs_per_cta=tile_cw, source_staging=tile_st,
-                            warps_z=tile_wz)
+                            warps_z=tile_wz, lane_axis=tile_ax)
         u = sf["iterations"] * per_update
         if ctx["with_adj"]:
             g_h.zero_()
