@@ -117,8 +117,10 @@ class ClockSampler:
 NCU_TRAFFIC = {
     # profiles/sweep2dp_square128.md: 202.2 KB read + 1.5 KB written (128 x 128 square, tile 3:4:4:1)
     ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 203776,
-    # profiles/sweep3dp_hotspot64.md: 77.6 MB read + 271.2 MB written (64^3 hotspot, 15 bands, tile 3:8:8:2:4)
-    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4:1"): 348800000,
+    # profiles/sweep3dp_hotspot64.md: 78.2 MB read + 271.1 MB written (64^3 hotspot, 15 bands)
+    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4:1"): 349290000,
+    # profiles/sweep3dp_finfet.md: 457.1 MB read + 1300 MB written (FinFET, 15 bands, forward launch)
+    ("sweep3dp_kernel<float, 8, 1, 0, 1>", "3:8:8:2:8:2"): 1757060000,
 }
 
 
