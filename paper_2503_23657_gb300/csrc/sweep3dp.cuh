@@ -41,8 +41,10 @@
 //     sum_d mu_d = sum_d w_d nu_d; only the face-sum weights differ
 //     (forward w_d |s_d,a|, adjoint a_d w_d);
 //   * the per-cell weighted sums of a step sit on a diagonal; each warp
-//     parks them for 32 steps in a shared-memory tile [row][33] and writes
-//     them row by row (32 consecutive cells of a row).
+//     parks them in a shared-memory tile [row][33] of its last 32 steps and
+//     writes 4 of the 32 rows per chunk, each row's last 32 steps being 32
+//     consecutive cells of that row (coalesced stores, and the same work for
+//     every warp in every chunk, which the lockstep barrier rewards).
 #pragma once
 
 #include <stdint.h>
