@@ -340,6 +340,9 @@ bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H, int map) {
     if (WY * H > 16 || H > n2) return false;
     const int M = (n2 + H - 1) / H;
     if (M > 1 && (H < 2 || p->nx < kPipe3Chunk * H + 2)) return false;
+    // a lane's virtual columns (passes x nx) stay well inside the range in
+    // which the kernel's float reciprocal division by nx is exact
+    if ((long long)M * p->nx + 64 >= (1LL << 22)) return false;
     return sweep3dp_smem(p->R, WY, H, dw, real_bytes) <= 225 * 1024;
 }
 
