@@ -17,8 +17,9 @@ Conventions
   region ``r`` whose relaxation times are ``tau_b * tau_scale[r-1]``.
 * Domain faces are numbered 0:x-, 1:x+, 2:y-, 3:y+, 4:z-, 5:z+.  Faces of
   axes that the problem does not resolve (``axis >= dim``) are ignored.
-* ``bc_type`` is ``ISOTHERMAL`` (0) or ``DIFFUSE`` (1).  Faces between a
-  solid and a void cell are always diffusely reflecting.
+* ``bc_type`` is ``ISOTHERMAL`` (0), ``DIFFUSE`` (1) or ``SPECULAR`` (2, oracle
+  only so far).  Faces between a solid and a void cell are always diffusely
+  reflecting.
 * Directions ``s[d]`` follow the paper's angle convention
   s = (cos(theta), sin(theta)cos(phi), sin(theta)sin(phi)) with the polar
   axis along x (Methods, angle discretisation); weights sum to 4*pi.
@@ -33,6 +34,7 @@ import numpy as np
 
 ISOTHERMAL = 0
 DIFFUSE = 1
+SPECULAR = 2   # oracle only so far (the GPU library refuses it)
 
 MASTER_SEED = 20250330
 
@@ -283,9 +285,10 @@ def ensemble_2d(n_instances: int = 256, n_min: int = 32, n_max: int = 160,
 
 def tiny(dim: int, n=(4, 4, 3), B: int = 2, n_polar: int = 2, n_az: int = 4,
          masked: bool = False, diffuse=(), source: bool = False, seed: int = 7,
-         two_regions: bool = False, L: float = 40e-9) -> Problem:
+         two_regions: bool = False, L: float = 40e-9, specular=()) -> Problem:
     """Small random problem for dense brute-force comparisons.  ``diffuse``
-    lists the domain faces that are diffusely reflecting."""
+    and ``specular`` list the domain faces that reflect diffusely /
+    specularly."""
     rng = np.random.Generator(np.random.PCG64(seed))
     nx = n[0]
     ny = n[1] if dim >= 2 else 1
@@ -304,6 +307,8 @@ def tiny(dim: int, n=(4, 4, 3), B: int = 2, n_polar: int = 2, n_az: int = 4,
     types = [ISOTHERMAL] * 6
     for f in diffuse:
         types[f] = DIFFUSE
+    for f in specular:
+        types[f] = SPECULAR
     if masked:
         # knock out a few cells, then drop solid cells that no longer connect
         # to an isothermal domain face (they would form an adiabatic island

@@ -146,6 +146,8 @@ def solve(p, max_iter: int = 100000, tol: float = None, T_init=None, lib=None):
     tol = p.tol if tol is None else tol
     it = lib.orc_solve(ctypes.byref(st), _ptr(T), _ptr(e), ctypes.c_int(max_iter),
                        ctypes.c_double(tol), _ptr(eps))
+    if it == -2:
+        raise ValueError("oracle: a specular face needs the mirror of every direction in the direction set")
     if it < 0:
         raise MemoryError("oracle: allocation failed")
     q = np.empty((N, 3))
@@ -171,6 +173,8 @@ def adjoint(p, e, T, g, max_iter: int = 100000, tol: float = 1e-13, want_mu: boo
     it = lib.orc_adjoint(ctypes.byref(st), _ptr(e), _ptr(T), _ptr(g), ctypes.c_int(max_iter),
                          ctypes.c_double(tol), _ptr(g_tau), _ptr(g_Tw), ctypes.byref(g_Q),
                          _ptr(mu))
+    if it == -2:
+        raise ValueError("oracle: a specular face needs the mirror of every direction in the direction set")
     if it < 0:
         raise MemoryError("oracle: allocation failed")
     out = dict(g_tau=g_tau, g_Tw=g_Tw, g_Q=g_Q.value, iters=it)

@@ -16,16 +16,20 @@
  *   - the equilibrium energy e0 = C T / (4 pi) and the lattice temperature
  *     T = sum_b sum_d w_d e/tau / sum_b C_b/tau (Eq. updatee0_t),
  *   - the heat flux q = sum_b sum_d w_d v_b s_d e,
- *   - isothermal, and diffusely reflecting boundaries (Boundary conditions
- *     section); faces between solid and void cells are diffuse,
+ *   - isothermal, diffusely reflecting and specularly reflecting domain
+ *     faces (Boundary conditions section); faces between solid and void
+ *     cells are diffuse.  A specular face returns, into direction d, the
+ *     energy the cell sends out through it in the mirror direction of d
+ *     (the normal component reversed), which the direction set must
+ *     contain,
  *   - the per-band source Q_b = C_b Q / (4 pi sum C) per steradian, so that
  *     the divergence of q equals Q,
  *   - the outer iteration of the "solution procedure" list (Methods): start
  *     from e = e0(T_init), solve every (band, direction) transport problem
  *     exactly by sweeping in upwind order, update e0 and T, repeat until
  *     eps_T < tol (convergence criterion, Methods).
- *   The diffuse inflow uses the previous iterate's outgoing energy; the
- *   fixed point is unchanged by that lag.
+ *   The diffuse and specular inflows use the previous iterate's outgoing
+ *   energy; the fixed point is unchanged by that lag.
  *
  * The adjoint (Forward and inverse modelling workflow: discrete adjoint of
  * the implicit solve) solves (L - P W - R)^T mu = W^T g by the transposed
@@ -37,6 +41,7 @@
 
 #define ORC_ISOTHERMAL 0
 #define ORC_DIFFUSE 1
+#define ORC_SPECULAR 2
 
 typedef struct {
     int dim;
@@ -100,11 +105,45 @@ static double diffuse_norm(const orc_problem *p, int side) {
 }
 
 /* Boundary kind of side `side` of active cell c: 0 interior, 1 isothermal
- * domain face, 2 diffuse (domain face or solid/void interface). */
+ * domain face, 2 diffuse (domain face or solid/void interface), 3 specular
+ * domain face. */
 static int side_kind(const orc_problem *p, long c, int side) {
     long m = neighbour(p, c, side);
-    if (m < 0) return (p->bc_type[side] == ORC_ISOTHERMAL) ? 1 : 2;
+    if (m < 0) {
+        if (p->bc_type[side] == ORC_ISOTHERMAL) return 1;
+        return (p->bc_type[side] == ORC_SPECULAR) ? 3 : 2;
+    }
     return p->mask[m] ? 0 : 2;
+}
+
+/* mirror[3 * d + a]: the direction whose axis-a component is reversed and
+ * whose other components equal those of d (-1 if the set has none). */
+static int *mirror_table(const orc_problem *p) {
+    int *m = (int *)malloc(sizeof(int) * 3 * (size_t)p->D);
+    if (!m) return NULL;
+    for (int d = 0; d < p->D; ++d)
+        for (int a = 0; a < 3; ++a) {
+            m[3 * d + a] = -1;
+            for (int k = 0; k < p->D; ++k) {
+                double err = 0.0;
+                for (int q = 0; q < 3; ++q) {
+                    double want = (q == a) ? -p->s[3 * d + q] : p->s[3 * d + q];
+                    err += fabs(p->s[3 * k + q] - want);
+                }
+                if (err < 1e-12) { m[3 * d + a] = k; break; }
+            }
+        }
+    return m;
+}
+
+/* every specular face of the problem needs the mirror of every direction */
+static int mirrors_complete(const orc_problem *p, const int *m) {
+    for (int side = 0; side < 2 * p->dim; ++side) {
+        if (p->bc_type[side] != ORC_SPECULAR) continue;
+        for (int d = 0; d < p->D; ++d)
+            if (m[3 * d + side / 2] < 0) return 0;
+    }
+    return 1;
 }
 
 static double Q_band(const orc_problem *p, long c, int b) {
@@ -128,9 +167,9 @@ static double diffuse_inflow(const orc_problem *p, const double *e_old, long c, 
     return acc / diffuse_norm(p, side);
 }
 
-/* One exact transport solve for (b, d) at frozen T and frozen diffuse inflow:
- * a triple loop over the cells in the upwind order of d's octant. */
-static void sweep_one(const orc_problem *p, int b, int d, const double *T,
+/* One exact transport solve for (b, d) at frozen T and frozen reflected
+ * inflow: a triple loop over the cells in the upwind order of d's octant. */
+static void sweep_one(const orc_problem *p, const int *mirror, int b, int d, const double *T,
                       const double *e_old, double *e_new) {
     int start[3], stop[3], step[3];
     for (int a = 0; a < 3; ++a) {
@@ -158,6 +197,7 @@ static void sweep_one(const orc_problem *p, int b, int d, const double *T,
             double ein;
             if (kind == 0) ein = E(e_new, neighbour(p, c, side), b, d);
             else if (kind == 1) ein = p->C[b] * p->bc_T[side] / FOUR_PI;
+            else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + a]);
             else ein = diffuse_inflow(p, e_old, c, b, side);
             rhs += coef * ein;
         }
@@ -221,7 +261,9 @@ int orc_solve(const orc_problem *p, double *T_io, double *e_io, int max_iter,
     long NE = N * (long)p->B * p->D;
     double *e_old = (double *)malloc(sizeof(double) * NE);
     double *T_new = (double *)malloc(sizeof(double) * N);
-    if (!e_old || !T_new) { free(e_old); free(T_new); return -1; }
+    int *mirror = mirror_table(p);
+    if (!e_old || !T_new || !mirror) { free(e_old); free(T_new); free(mirror); return -1; }
+    if (!mirrors_complete(p, mirror)) { free(e_old); free(T_new); free(mirror); return -2; }
     /* step 1: e = e0(T_init) */
     for (long c = 0; c < N; ++c)
         for (int b = 0; b < p->B; ++b)
@@ -233,7 +275,7 @@ int orc_solve(const orc_problem *p, double *T_io, double *e_io, int max_iter,
         /* step 2: exact transport solve of every (band, direction) */
         for (int b = 0; b < p->B; ++b)
             for (int d = 0; d < p->D; ++d)
-                sweep_one(p, b, d, T_io, e_old, e_io);
+                sweep_one(p, mirror, b, d, T_io, e_old, e_io);
         /* step 3: update e0 and T */
         temperature(p, e_io, T_new);
         double eps = eps_T(p, T_io, T_new);
@@ -245,6 +287,7 @@ int orc_solve(const orc_problem *p, double *T_io, double *e_io, int max_iter,
     }
     free(e_old);
     free(T_new);
+    free(mirror);
     return it;
 }
 
@@ -287,8 +330,9 @@ static double adj_diffuse_sum(const orc_problem *p, const double *mu_old, long c
 }
 
 /* Transposed transport solve for (b, d): cells in downwind-first order; each
- * cell couples to the downwind neighbours that its upwind faces feed. */
-static void adj_sweep_one(const orc_problem *p, int b, int d, const double *Th,
+ * cell couples to the downwind neighbours that its upwind faces feed, and at
+ * a specular face it leaves by, to the mirror direction that the face feeds. */
+static void adj_sweep_one(const orc_problem *p, const int *mirror, int b, int d, const double *Th,
                           const double *mu_old, double *mu_new) {
     int start[3], stop[3], step[3];
     for (int a = 0; a < 3; ++a) {
@@ -317,6 +361,8 @@ static void adj_sweep_one(const orc_problem *p, int b, int d, const double *Th,
             if (kind == 0) rhs += coef * E(mu_new, neighbour(p, c, down), b, d);
             else if (kind == 2)
                 rhs += p->w[d] * fabs(sa) * adj_diffuse_sum(p, mu_old, c, b, down);
+            else if (kind == 3)
+                rhs += coef * E(mu_old, c, b, mirror[3 * d + a]);
         }
         E(mu_new, c, b, d) = rhs / diag;
     }
@@ -338,9 +384,14 @@ int orc_adjoint(const orc_problem *p, const double *e, const double *T, const do
     double *mu_old = (double *)malloc(sizeof(double) * NE);
     double *Th = (double *)malloc(sizeof(double) * N);
     double *Th_new = (double *)malloc(sizeof(double) * N);
-    if (!mu || !mu_old || !Th || !Th_new) {
-        free(mu); free(mu_old); free(Th); free(Th_new);
+    int *mirror = mirror_table(p);
+    if (!mu || !mu_old || !Th || !Th_new || !mirror) {
+        free(mu); free(mu_old); free(Th); free(Th_new); free(mirror);
         return -1;
+    }
+    if (!mirrors_complete(p, mirror)) {
+        free(mu); free(mu_old); free(Th); free(Th_new); free(mirror);
+        return -2;
     }
     adj_theta(p, mu, g, Th);
     int it = 0;
@@ -348,7 +399,7 @@ int orc_adjoint(const orc_problem *p, const double *e, const double *T, const do
         memcpy(mu_old, mu, sizeof(double) * NE);
         for (int b = 0; b < p->B; ++b)
             for (int d = 0; d < p->D; ++d)
-                adj_sweep_one(p, b, d, Th, mu_old, mu);
+                adj_sweep_one(p, mirror, b, d, Th, mu_old, mu);
         adj_theta(p, mu, g, Th_new);
         double ss = 0.0, mx = 0.0;
         long cnt = 0;
@@ -400,6 +451,6 @@ int orc_adjoint(const orc_problem *p, const double *e, const double *T, const do
         }
     }
     if (mu_out) memcpy(mu_out, mu, sizeof(double) * NE);
-    free(mu); free(mu_old); free(Th); free(Th_new);
+    free(mu); free(mu_old); free(Th); free(Th_new); free(mirror);
     return it;
 }

@@ -13,7 +13,10 @@ eliminated as the linear functional T = W e of Eq. (updatee0_t):
 * P W e -- the re-emission C_b T_c / (4 pi tau_cb) of Eq. (bte-2);
 * R  -- diffuse reflection (Boundary conditions: diffusely reflecting
         boundary) with the quadrature-consistent normaliser
-        sum_{s.n<0} w |s.n| in place of pi;
+        sum_{s.n<0} w |s.n| in place of pi, and specular reflection at
+        domain faces of that type: the inflow of direction d is the
+        outgoing value of the mirror direction (normal component reversed)
+        in the same cell;
 * s  -- per-band source Q_b phi_c (Q_b = C_b Q/(4 pi sum C)) plus the
         isothermal inflow v |s.n| C_b T_w / (4 pi h).
 
@@ -80,6 +83,15 @@ class System:
                     wc.append(self.u(c, b, d))
                     wv.append(p.w[d] / (self.tau_cb[c, b] * self.K[c]))
         self.W = sp.csr_matrix((wv, (wr, wc)), shape=(self.active.size, self.n_unknowns))
+        # mirror[a][d]: the direction with component a reversed
+        mirror = np.full((3, p.D), -1, dtype=np.int64)
+        for a in range(3):
+            want = p.s.copy()
+            want[:, a] *= -1.0
+            for d in range(p.D):
+                hit = np.flatnonzero(np.abs(p.s - want[d]).sum(axis=1) < 1e-12)
+                if hit.size:
+                    mirror[a, d] = hit[0]
         norm = {}
         for side in range(6):
             a, sg = side // 2, (1.0 if side % 2 else -1.0)
@@ -105,6 +117,10 @@ class System:
                             rows.append(r); cols.append(self.u(m, b, d)); vals.append(-coef)
                         elif m < 0 and p.bc_type[side] == 0:
                             rhs[r] += coef * p.C[b] * p.bc_T[side] / FOUR_PI
+                        elif m < 0 and p.bc_type[side] == 2:
+                            if mirror[a, d] < 0:
+                                raise ValueError("specular face without the mirror direction")
+                            rows.append(r); cols.append(self.u(c, b, mirror[a, d])); vals.append(-coef)
                         else:
                             sg = 1.0 if side % 2 else -1.0
                             for d2 in range(p.D):

@@ -81,6 +81,59 @@ def _battery(lib):
     return failed
 
 
+SPECULAR_MUTATIONS = {
+    "specular_same_direction": ("else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + a]);",
+                                "else if (kind == 3) ein = E(e_old, c, b, d);"),
+    "specular_wrong_axis": ("else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + a]);",
+                            "else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + (a + 1) % 3]);"),
+    "specular_as_diffuse": ("return (p->bc_type[side] == ORC_SPECULAR) ? 3 : 2;", "return 2;"),
+    "adjoint_without_specular": ("rhs += coef * E(mu_old, c, b, mirror[3 * d + a]);",
+                                 "rhs += 0.0 * E(mu_old, c, b, mirror[3 * d + a]);"),
+}
+
+
+def _specular_battery(lib):
+    """Pins of the specular faces (see test_oracle_specular.py)."""
+    failed = []
+    p = bi.tiny(2, n=(10, 4, 1), B=2, n_polar=4, n_az=8, specular=(2, 3))
+    q = bi.tiny(1, n=(10, 1, 1), B=2, n_polar=2)
+    T2 = oracle.solve(p, max_iter=100000, tol=1e-15, lib=lib)["T"].reshape(-1, 10)
+    T1 = oracle.solve(q, max_iter=100000, tol=1e-15, lib=lib)["T"]
+    if not np.abs(T2 - T1[None, :]).max() < 1e-10 * np.ptp(T1):
+        failed.append("slab1d")
+    p = bi.tiny(2, n=(7, 6, 1), B=3, specular=(1, 3), masked=True, source=True, two_regions=True)
+    ref = dense.solve(p)
+    r = oracle.solve(p, max_iter=100000, tol=1e-15, lib=lib)
+    act = p.mask > 0
+    if not np.allclose(r["T"][act], ref["T"][act], rtol=1e-11, atol=0):
+        failed.append("direct")
+    rng = np.random.default_rng(5)
+    probes = np.sort(rng.choice(np.flatnonzero(act), 4, replace=False))
+    T_obs = ref["T"][probes] - 1.0
+    g = np.zeros(p.n_cells)
+    np.add.at(g, probes, ref["T"][probes] - T_obs)
+    a = oracle.adjoint(p, ref["e"], ref["T"], g, max_iter=20000, tol=1e-15, lib=lib)
+    fd = dense.fd_gradients(p, probes, T_obs)
+    if not (np.allclose(a["g_tau"], fd["g_tau"], rtol=1e-4) and abs(a["g_Q"] - fd["g_Q"]) <= 1e-4 * abs(fd["g_Q"])):
+        failed.append("adjoint")
+    return failed
+
+
+def test_unmutated_oracle_passes_specular_battery():
+    assert _specular_battery(oracle.load_library(oracle.build())) == []
+
+
+@pytest.mark.parametrize("name", sorted(SPECULAR_MUTATIONS))
+def test_planted_specular_mistake_is_caught(name, tmp_path):
+    old, new = SPECULAR_MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib = oracle.load_library(oracle.compile_c(str(path), str(tmp_path / "mutant.so")))
+    assert _specular_battery(lib), f"planted mistake {name} was not detected"
+
+
 def test_unmutated_oracle_passes_battery():
     assert _battery(oracle.load_library(oracle.build())) == []
 
