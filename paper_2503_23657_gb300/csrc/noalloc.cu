@@ -105,7 +105,8 @@ eps_noalloc_kernel(const double *__restrict__ T_old, const double *__restrict__ 
     }
     na_block_reduce(tss, tmx, tn, sh);
     if (threadIdx.x == 0) {
-        out[0] = (tn > 0.0 && tmx > 0.0) ? sqrt(tss / tn) / tmx : 0.0;
+        // NaN anywhere: NaN (fmax skips NaN, so the maximum alone cannot tell)
+        out[0] = isnan(tss) || isnan(tmx) ? NAN : ((tn > 0.0 && tmx > 0.0) ? sqrt(tss / tn) / tmx : 0.0);
         out[1] = tmx;
         out[2] = tn;
         *counter = 0ull;  // ready for the next call

@@ -249,6 +249,21 @@ def test_not_converged_status(bte):
     assert rc == -4 and st["iterations"] == 3 and T.max() > 300.0
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_overflow_is_a_numeric_error(bte, dim):
+    """A finite source amplitude too large for FP32 (the per-band source
+    overflows to Inf in the sweep) is caught by the update's finiteness check
+    and reported as BTE_ENUMERIC, not as convergence or a silent NaN field."""
+    p = bi.tiny(dim, n=(6, 5, 4), B=2, source=True)
+    plan = bte.Plan(p)
+    T = np.zeros(p.n_cells)
+    rc, st = plan.solve(T, precision=bte.BTE_FP32, tol=1e-6, max_iter=50, Q_amp=1e300, check=False)
+    assert rc == -6
+    # the plan stays usable
+    rc, st = plan.solve(T, precision=bte.BTE_FP32, tol=0.0, max_iter=3)
+    assert rc == 0 and np.isfinite(T).all()
+
+
 def test_adjoint_before_solve_is_state_error(bte):
     p = bi.tiny(2)
     plan = bte.Plan(p)
