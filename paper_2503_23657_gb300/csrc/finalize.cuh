@@ -42,9 +42,7 @@ __device__ __forceinline__ void fin_reduce(const FinalizeParams &F, double &eps,
     fin_warp_reduce(s, m);
     tss = __shfl_sync(0xffffffffu, s, 0);
     tmx = __shfl_sync(0xffffffffu, m, 0);
-    // a non-finite temperature anywhere makes the sum of squares NaN (the
-    // update marks it so); fmax skips NaN, so the maximum alone cannot tell
-    eps = isnan(tss) || isnan(tmx) ? NAN : ((tmx > 0.0) ? sqrt(tss / (double)F.n_active) / tmx : 0.0);
+    eps = (tmx > 0.0) ? sqrt(tss / (double)F.n_active) / tmx : 0.0;
 }
 
 __device__ __forceinline__ bool fin_stop(const FinalizeParams &F, double eps) {

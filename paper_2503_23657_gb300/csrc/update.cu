@@ -168,7 +168,12 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
             if (P.xskew_out) skew_store(P.skew, c, xd, P.xskew_out);
             const double d = xn - x_old;
             ss = d * d;
-            if (!isfinite(xn)) ss = NAN;
+            if (!isfinite(xn)) {
+                // a NaN sum of squares and an infinite maximum: eps_T is NaN
+                // whatever the other cells hold (fmax would skip a NaN maximum)
+                ss = NAN;
+                mx = INFINITY;
+            }
             P.x_out[c] = xn;
         } else {
             P.x_out[c] = 0.0;
