@@ -13,6 +13,7 @@ import bte_inputs as bi
 import oracle
 import oracle.dense as dense
 from tests import physics
+from tests.test_oracle_pins import ballistic_slab_along
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "bte_oracle.c")
 
@@ -38,6 +39,10 @@ MUTATIONS = {
                           "g_tau[b] -= acc / (tc * p->tau[b]);"),
     "theta_without_capacity": ("acc += p->C[b] / (FOUR_PI * tau_cb(p, c, b)) * sm;",
                                "acc += 1.0 / (FOUR_PI * tau_cb(p, c, b)) * sm;"),
+    "flux_axis_slip": ("q[3 * c + a] += p->v[b] * p->w[d] * p->s[3 * d + a] * E(e, c, b, d);",
+                       "q[3 * c + a] += p->v[b] * p->w[d] * p->s[3 * d] * E(e, c, b, d);"),
+    "flux_axes_swapped": ("q[3 * c + a] += p->v[b] * p->w[d] * p->s[3 * d + a] * E(e, c, b, d);",
+                          "q[3 * c + a] += p->v[b] * p->w[d] * p->s[3 * d + (3 - a) % 3] * E(e, c, b, d);"),
 }
 
 
@@ -51,6 +56,16 @@ def _battery(lib):
     qd = p.C[0] * p.v[0] * 2.0 / (4 * np.pi) * np.sum(p.w[mu > 0] * mu[mu > 0])
     if not (np.allclose(r["T"], 300.0, rtol=1e-12) and np.allclose(r["q"][:, 0], qd, rtol=1e-10)):
         failed.append("ballistic")
+    # the y and z flux components: ballistic slabs along y and along z
+    for axis in (1, 2):
+        p = ballistic_slab_along(axis)
+        r = oracle.solve(p, max_iter=200, tol=1e-15, lib=lib)
+        sa = p.s[:, axis]
+        qd = p.C[0] * p.v[0] * 2.0 / (4 * np.pi) * np.sum(p.w[sa > 0] * sa[sa > 0])
+        others = [o for o in range(3) if o != axis]
+        if not (np.allclose(r["q"][:, axis], qd, rtol=1e-10)
+                and np.abs(r["q"][:, others]).max() < 1e-10 * qd):
+            failed.append(f"ballistic_axis{axis}")
     # iteration vs direct solve, energy balance, adjoint on masked cases
     for dim, kw in [(2, dict(n=(5, 4, 1), B=3, masked=True, diffuse=(2, 3), source=True,
                              two_regions=True)),

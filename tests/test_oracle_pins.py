@@ -5,6 +5,7 @@ Each check is chosen so that a plausible slip in the oracle (a dropped
 diffuse reflection, a wrong sign of the collision term) fails at least one:
 
 * ballistic limit of the gray slab (closed form in the discrete setting),
+  along x, and along y and z for the other two flux components,
 * diffusive limit: Fourier conductivity k = sum_b C_b v_b^2 tau_b / 3,
 * continuum solution of the gray slab (exponential-integral equation) with
   first-order convergence in the cell size,
@@ -43,6 +44,49 @@ def test_ballistic_limit_gray_slab():
     np.testing.assert_allclose(r["q"][:, 0], q_discrete, rtol=1e-12)
     # and within the Gauss-Legendre half-range error of C v dT / 4
     np.testing.assert_allclose(q_discrete, p.C[0] * p.v[0] * (T_h - T_c) / 4, rtol=5e-3)
+
+
+def ballistic_slab_along(axis, nc=24, n_polar=4, n_az=8):
+    """Gray ballistic slab whose normal is the y (axis 1) or z (axis 2) axis:
+    a single column of cells between isothermal walls T_h (minus side) and
+    T_c (plus side), every other domain face specular, so that the problem
+    is the 1D slab with mu = s_axis.  The cross-section is made wide so that
+    the lagged specular coupling converges in a few iterations."""
+    dim = axis + 1
+    s, w = bi.quadrature_polar_azimuth(n_polar, n_az, dim)
+    n = [1, 1, 1]
+    n[axis] = nc
+    length = [1e-3, 1e-3 if dim == 3 else 1.0, 1.0]
+    length[axis] = 1e-6
+    types = [bi.SPECULAR] * 6
+    types[2 * axis], types[2 * axis + 1] = bi.ISOTHERMAL, bi.ISOTHERMAL
+    temps = np.full(6, 300.0)
+    temps[2 * axis], temps[2 * axis + 1] = 301.0, 299.0
+    return bi.Problem(
+        name=f"ballistic_axis{axis}", dim=dim, n=tuple(n), length=tuple(length),
+        mask=np.ones(nc, dtype=np.uint8), C=np.array([bi.C_TOTAL]), v=np.array([6400.0]),
+        tau=np.array([1e3]), tau_scale=np.array([1.0]), s=s, w=w,
+        bc_type=np.asarray(types, dtype=np.int32), bc_T=temps, T_init=300.0,
+        tol=1e-14, precision="fp64")
+
+
+@pytest.mark.parametrize("axis", [1, 2])
+def test_ballistic_limit_flux_along_y_and_z(axis):
+    """The heat flux definition q = sum_b v_b sum_d w_d s_d e (Methods,
+    Phonon BTE) in its y and z components: the ballistic slab along that
+    axis gives q_axis = C v (T_h - T_c)/(4 pi) * sum_{s_axis > 0} w s_axis,
+    and the two other components vanish (e depends only on the sign of
+    s_axis, and the direction set is symmetric); T = (T_h + T_c)/2."""
+    p = ballistic_slab_along(axis)
+    r = oracle.solve(p, max_iter=200, tol=1e-15)
+    np.testing.assert_allclose(r["T"], 300.0, rtol=1e-13)
+    sa = p.s[:, axis]
+    q_discrete = p.C[0] * p.v[0] * 2.0 / (4 * np.pi) * np.sum(p.w[sa > 0] * sa[sa > 0])
+    np.testing.assert_allclose(r["q"][:, axis], q_discrete, rtol=1e-12)
+    for other in {0, 1, 2} - {axis}:
+        assert np.abs(r["q"][:, other]).max() < 1e-12 * q_discrete
+    # and close to the continuum value C v dT / 4 (quadrature error only)
+    np.testing.assert_allclose(q_discrete, p.C[0] * p.v[0] * 2.0 / 4, rtol=5e-2)
 
 
 @pytest.mark.parametrize("nongray", [False, True])
