@@ -1,19 +1,24 @@
 """Benchmark: cell x band x direction updates/s and time-to-converge of the
 steady nongray phonon-BTE hot path on one GB300 (or N replicas).
 
-Default workload (one "step"): the 2D nongray square -- 128 x 128 cells on
-2 um x 2 um, 15 synthetic silicon-like bands, 64 directions (8 Gauss-Legendre
-polar x 8 azimuths), left wall 310 K, right wall 300 K, top/bottom diffuse --
-solved from T = 300 K to eps_T < 1e-6 with FP32 sweeps and FP64 reductions
-(forward), followed by the discrete adjoint of the probe-temperature misfit
-(64 seeded probes) to a relative change of 1e-6.  ``value`` counts the
-updates of every forward and adjoint source iteration.
+Default workload (one "step"): the inverse FinFET-like problem -- a masked
+160 x 80 x 64 grid (2.5 nm cells; substrate, oxide with tau x 0.1, a 20 nm x
+40 nm fin, Joule source in the fin's top 10 nm), 15 synthetic silicon-like
+bands, 128 directions (8 Gauss-Legendre polar x 16 azimuths), bottom face
+isothermal, every other face diffuse -- solved from T = 300 K to eps_T < 1e-6
+with FP32 sweeps and FP64 reductions (forward), followed by the discrete
+adjoint of the misfit of 64 seeded probe temperatures to a relative change of
+1e-6 (gradients w.r.t. the 15 tau_b, the substrate temperature and the source
+amplitude).  ``value`` counts the updates of every forward and adjoint source
+iteration.  The same line reports the batched ensemble (256 uneven 2D
+squares) solved in FP32 and in FP64 on the GPU: the FP32 batched form's
+speedup over the FP64 path and its error (``ensemble`` key).
 
-Other workloads (--workload): ``slab`` (1D gray slab, 200 cells, FP64 to
+Other workloads (--workload): ``square`` (2D nongray square 128^2, 64
+directions, forward + adjoint), ``slab`` (1D gray slab, 200 cells, FP64 to
 1e-10), ``hotspot`` (3D cube 64^3, 15 bands x 128 directions, Gaussian
-source, forward to 1e-6), ``finfet`` (masked 160x80x64 FinFET, forward +
-adjoint to 1e-6), ``ensemble`` (256 uneven 2D squares solved as one batch,
-forward to 1e-6 per instance).
+source, forward to 1e-6), ``ensemble`` (256 uneven 2D squares solved as one
+batch, forward to 1e-6 per instance).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 
@@ -111,17 +116,33 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
-# capture summarised in profiles/ (keyed by the exact kernel; a kernel changed
-# since the capture has no entry)
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the sweep
+# kernel, from an ncu capture of that kernel (one launch, --clock-control
+# none), keyed by the kernel, the tile and a fingerprint of the kernel's
+# sources at capture time: a kernel edited since its capture has no entry and
+# reports null.  Full-size captures where the launch fits the capture rules;
+# otherwise a capture with fewer bands, scaled to all bands (traffic grows in
+# proportion to the bands: every band is an independent set of CTAs).
 NCU_TRAFFIC = {
-    # profiles/sweep2dp_square128.md: 202.2 KB read + 1.5 KB written (128 x 128 square, tile 3:4:4:1)
-    ("sweep2dp_kernel<float, 4, 8, 0, 0, 1>", "3:4:4:1"): 203776,
-    # profiles/sweep3dp_hotspot64.md: 78.2 MB read + 271.1 MB written (64^3 hotspot, 15 bands)
-    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4:1"): 349290000,
-    # profiles/sweep3dp_finfet.md: 457.1 MB read + 1300 MB written (FinFET, 15 bands, forward launch)
-    ("sweep3dp_kernel<float, 8, 1, 0, 1>", "3:8:8:2:8:2"): 1757060000,
 }
+KERNEL_SOURCES = {
+    "sweep3dp_kernel": ["sweep3dp.cuh", "bte_internal.cuh", "finalize.cuh", "tma.cuh"],
+    "sweep2dp_kernel": ["sweep2dp.cuh", "bte_internal.cuh", "finalize.cuh", "tma.cuh"],
+}
+
+
+def kernel_fingerprint(kernel):
+    """Short hash of the sources a sweep kernel is compiled from."""
+    import hashlib
+    base = kernel.split("<")[0]
+    files = KERNEL_SOURCES.get(base)
+    if not files:
+        return None
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2503_23657_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
 
 
 def measured_hbm_peak():
@@ -162,22 +183,40 @@ def oracle_iters(units_per_iter, seconds=15.0, rate=4e7):
     return max(1, int(round(seconds * rate / max(units_per_iter, 1))))
 
 
-def cpu_baseline_oracle(probs, iters):
+def oracle_sample(p, seconds, rate=4e7):
+    """A bounded sample of workload `p` for the single-thread oracle: whole
+    source iterations of the full problem when one takes less than `seconds`,
+    else one iteration of the problem restricted to its first bands (every
+    band is an independent set of sweeps; at least one band).  Returns the
+    sampled problem, its iteration count and a description."""
+    per_band = p.n_active * p.D
+    if p.B * per_band <= seconds * rate:
+        return p, oracle_iters(p.B * per_band, seconds, rate), "all bands"
+    nb = max(1, min(p.B, int(seconds * rate / per_band)))
+    q = p.copy(C=p.C[:nb], v=p.v[:nb], tau=p.tau[:nb])
+    return q, 1, f"the first {nb} of {p.B} bands"
+
+
+def cpu_baseline_oracle(probs, iters=0):
     """The FP64 oracle (single thread) on a bounded sample of the workload:
-    `iters` forward source iterations of (the first instances of) it."""
+    forward source iterations of (the first instances of) it, restricted to
+    its first bands where one full iteration would take too long."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
     units = 0
+    what = "all bands"
     for p in probs:
-        oracle.solve(p, max_iter=iters, tol=0.0)
-        units += iters * p.n_active * p.B * p.D
+        q, k, what = oracle_sample(p, 15.0)
+        k = iters or k
+        oracle.solve(q, max_iter=k, tol=0.0)
+        units += k * q.n_active * q.B * q.D
         if time.perf_counter() - t0 > 20.0:
             break
     dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} forward source iterations of {len(probs) if len(probs) == 1 else 'the first'} "
-                      f"instance(s) of the workload ({units:.3g} updates, {dt:.1f} s, FP64, 1 thread)"}
+            "sample": f"{k} forward source iteration(s) of {len(probs) if len(probs) == 1 else 'the first'} "
+                      f"instance(s) of the workload, {what} ({units:.3g} updates, {dt:.1f} s, FP64, 1 thread)"}
 
 
 def run_reference(args, ws, rank):
@@ -190,8 +229,7 @@ def run_reference(args, ws, rank):
     make, name, tol, fp64, adj = WORKLOADS[args.workload]
     probs = make(bi)
     probs = probs if isinstance(probs, list) else [probs]
-    p = probs[0]
-    k_iter = oracle_iters(p.n_active * p.B * p.D, seconds=3.0)
+    p, k_iter, what = oracle_sample(probs[0], 3.0)
     units_step = k_iter * p.n_active * p.B * p.D
     for _ in range(args.warmup):
         oracle.solve(p, max_iter=1, tol=0.0)
@@ -206,9 +244,9 @@ def run_reference(args, ws, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": name, "reference": "FP64 CPU oracle (oracle/bte_oracle.c), 1 thread",
-                   "step": f"{k_iter} forward source iterations of {p.name} (bounded sample)"},
+                   "step": f"{k_iter} forward source iteration(s) of {p.name}, {what} (bounded sample)"},
         "cpu_baseline": {"value": val, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps x {k_iter} source iterations of {p.name}"},
+                         "sample": f"{args.steps} steps x {k_iter} source iteration(s) of {p.name}, {what}"},
         "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -229,7 +267,8 @@ def roofline_object(kernel, tile, sweep_ms, updates_per_launch, B, D, extra):
     peak_fp32 = sm_count * 128 * 2 * smax * 1e6 / 1e12
     alu_achieved = flops_per_update * updates_per_launch / (sweep_ms * 1e-3) / 1e12
     r = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
-         "traffic": NCU_TRAFFIC.get((kernel, tile)), "kernel": kernel, "tile": tile, "peak_source": peak_src,
+         "traffic": NCU_TRAFFIC.get((kernel, tile, kernel_fingerprint(kernel))), "kernel": kernel, "tile": tile,
+         "kernel_sources": kernel_fingerprint(kernel), "peak_source": peak_src,
          "algorithmic": f"{bytes_per_update:.4f} B x {updates_per_launch} cell*band*direction updates per launch "
                         f"(e write per update + per-cell T, S, q); the kernel keeps e on chip (e is regenerated "
                         f"once after convergence), so DRAM traffic is far lower",
@@ -246,7 +285,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="square", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="finfet", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="finfet: skip the FP32-vs-FP64 batched-ensemble comparison")
     ap.add_argument("--instances", type=int, default=256, help="ensemble: number of instances (a profiler "
                                                                   "capture uses a small batch)")
     ap.add_argument("--bands", type=int, default=0, help="keep only the first N bands (0 = all): the small "
@@ -288,7 +329,7 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         p0 = probs[0]
-        cpu = cpu_baseline_oracle(probs, args.cpu_iters or oracle_iters(p0.n_active * p0.B * p0.D))
+        cpu = cpu_baseline_oracle(probs, args.cpu_iters)
 
     import __graft_entry__
     __graft_entry__.build()
@@ -300,6 +341,8 @@ def main():
         line = run_ensemble(probs, ctx)
     else:
         line = run_single(probs[0], ctx)
+        if args.workload == "finfet" and ws == 1 and not args.no_ensemble:
+            line["ensemble"] = ensemble_fp32_vs_fp64(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -480,6 +523,43 @@ def run_single(p, ctx):
                 "d2h_bytes_per_step": 8 * p.n_cells + (8 * (p.B + 7) if ctx["with_adj"] else 0)},
         "gpu_launches": launches, "clocks": clk})
     return line
+
+
+def ensemble_fp32_vs_fp64(ctx):
+    """The batched ensemble (256 uneven 2D squares, 15 bands x 64 directions)
+    solved to eps_T < 1e-6 per instance in FP32 (sweeps; FP64 reductions) and
+    in FP64 on the GPU, outside the timed steps: the FP32 batched form's
+    speedup over the FP64 GPU path and the FP32 temperatures' error against
+    the FP64 ones.  Each precision first runs one graph replay (tile
+    autotuning and graph capture), then the timed solve."""
+    torch, m = ctx["torch"], ctx["m"]
+    import bte_inputs as bi
+    probs = bi.ensemble_2d()
+    plans = [m.Plan(p) for p in probs]
+    batch = m.Batch(plans)
+    n = sum(p.n_cells for p in probs)
+    res = {}
+    for prec in (m.BTE_FP32, m.BTE_FP64):
+        T = torch.zeros(n, dtype=torch.float64, device="cuda")
+        batch.solve(T, precision=prec, tol=1e-6, max_iter=32, check=False)
+        rc, st, bs = batch.solve(T, precision=prec, tol=1e-6, max_iter=100000)
+        res[prec] = (T, st, bs)
+    (T32, st32, bs32), (T64, st64, bs64) = res[m.BTE_FP32], res[m.BTE_FP64]
+    o = batch.offsets
+    errs = [float((T32[o[i]:o[i + 1]] - T64[o[i]:o[i + 1]]).abs().max() / T64[o[i]:o[i + 1]].abs().max())
+            for i in range(len(probs))]
+    out = {"workload": WORKLOADS["ensemble"][1], "instances": len(probs), "cells": n,
+           "fp32_time_to_converge_ms": bs32["seconds"] * 1e3, "fp64_time_to_converge_ms": bs64["seconds"] * 1e3,
+           "speedup_fp32_vs_fp64": bs64["seconds"] / bs32["seconds"],
+           "fp32_updates_per_s": bs32["updates_per_s"], "fp64_updates_per_s": bs64["updates_per_s"],
+           "T_fp32_vs_fp64_rel_max": max(errs),
+           "iterations_equal_fp32_fp64": sum(int(a["iterations"] == b["iterations"]) for a, b in zip(st32, st64)),
+           "converged_fp32_fp64": [bs32["converged"], bs64["converged"]],
+           "gpu_launches_fp32": bs32["kernel_launches"]}
+    batch.close()
+    for pl in plans:
+        pl.close()
+    return out
 
 
 def run_ensemble(probs, ctx):

@@ -147,9 +147,21 @@ def eps_T_noalloc(T_old, T_new, out, mask=None, stream=None):
     """bte_eps_T_noalloc: eps_T of two device temperature fields, written to
     the device buffer ``out`` (3 doubles), without any device allocation --
     for callers that cannot call cudaMalloc where they need the measure."""
+    import torch
+
+    n = int(T_new.numel())
+    for name, t, dt, size in (("T_old", T_old, torch.float64, n), ("T_new", T_new, torch.float64, n),
+                              ("out", out, torch.float64, 3), ("mask", mask, torch.uint8, n)):
+        if t is None and name == "mask":
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"eps_T_noalloc: {name} must be a CUDA tensor")
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"eps_T_noalloc: {name} must be a contiguous {dt} tensor")
+        if (t.numel() < size) if name == "out" else (t.numel() != size):
+            raise ValueError(f"eps_T_noalloc: {name} has {t.numel()} elements, expected {size}")
     lib = load()
-    rc = lib.bte_eps_T_noalloc(_addr(T_old), _addr(T_new), _addr(mask), int(T_new.numel()),
-                               _addr(out), stream)
+    rc = lib.bte_eps_T_noalloc(_addr(T_old), _addr(T_new), _addr(mask), n, _addr(out), stream)
     if rc != BTE_OK:
         raise BTEError(rc, lib.bte_last_error(None).decode())
     return rc

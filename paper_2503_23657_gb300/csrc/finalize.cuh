@@ -57,8 +57,13 @@ __device__ __forceinline__ void fin_record(const FinalizeParams &F, double eps, 
     F.last[1] = tmx;
     F.last[2] = tss;
     *F.iter = it + 1;
-    if (!isfinite(eps)) *F.status = 1;
-    if (fin_stop(F, eps)) {
+    // a NaN residual marks status 1 unless a sweep already recorded an
+    // expired wait (2), which stays the reported cause
+    if (!isfinite(eps)) atomicCAS(F.status, 0, 1);
+    // an instance whose status is set (a non-finite residual, or a sweep's
+    // bounded wait that expired) stops too, so a batched solve does not keep
+    // iterating it until max_iter
+    if (fin_stop(F, eps) || *((volatile const int *)F.status) != 0) {
         *F.done = 1;
         if (F.batch_done) atomicAdd(F.batch_done, 1);
     }

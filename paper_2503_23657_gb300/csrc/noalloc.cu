@@ -16,6 +16,7 @@
 // result is deterministic.  The scratch array is shared by every call on a
 // device and keeps the last call's contents; calls that overlap on the GPU
 // (different streams without ordering) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -40,6 +41,37 @@ static __device__ __align__(256) double g_noalloc_scratch[3 * kNaMaxBlocks + 1];
 
 std::mutex g_na_mutex;
 double *g_na_ptr[kNaMaxDevices] = {nullptr};
+// id of the context each cached address belongs to: a device reset destroys
+// the primary context, the module is loaded again into the next one and the
+// array's address may change, so the address is looked up again whenever
+// the current context is a different one (context ids are never reused
+// within a process)
+unsigned long long g_na_ctx[kNaMaxDevices] = {0};
+
+// cuCtxGetCurrent / cuCtxGetId reached through the runtime (no link against
+// the driver library)
+typedef CUresult (*NaCtxGetCurrent)(CUcontext *);
+typedef CUresult (*NaCtxGetId)(CUcontext, unsigned long long *);
+
+bool na_current_context_id(unsigned long long *id) {
+    static NaCtxGetCurrent get_current = nullptr;
+    static NaCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return false;
+        }
+        get_current = reinterpret_cast<NaCtxGetCurrent>(f1);
+        get_id = reinterpret_cast<NaCtxGetId>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 __device__ __forceinline__ void na_block_reduce(double &a, double &m, double &n, double *sh) {
 #pragma unroll
@@ -130,20 +162,26 @@ extern "C" int bte_eps_T_noalloc(const double *T_old, const double *T_new, const
         cudaGetLastError();
         return na_fail(BTE_ECUDA, "bte_eps_T_noalloc: no usable current CUDA device");
     }
+    // (before the runtime has made its context on this device there is no
+    // current context yet; the symbol lookup below makes it)
+    unsigned long long ctx_id = 0;
+    const bool have_ctx = na_current_context_id(&ctx_id);
     double *scratch = nullptr;
     {
-        // once per device, with that device current: the device address of
-        // the file-scope scratch array (its host-side name is not a device
-        // address and must never be passed to a kernel)
+        // once per device and context, with that device current: the device
+        // address of the file-scope scratch array (its host-side name is not
+        // a device address and must never be passed to a kernel)
         std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (g_na_ptr[dev] == nullptr) {
+        if (!have_ctx || g_na_ptr[dev] == nullptr || g_na_ctx[dev] != ctx_id) {
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || p == nullptr) {
+            if (e != cudaSuccess || p == nullptr || !na_current_context_id(&ctx_id)) {
                 cudaGetLastError();
+                g_na_ptr[dev] = nullptr;
                 return na_fail(BTE_ECUDA, "bte_eps_T_noalloc: cudaGetSymbolAddress failed");
             }
             g_na_ptr[dev] = static_cast<double *>(p);
+            g_na_ctx[dev] = ctx_id;
         }
         scratch = g_na_ptr[dev];
     }
