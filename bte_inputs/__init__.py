@@ -17,9 +17,8 @@ Conventions
   region ``r`` whose relaxation times are ``tau_b * tau_scale[r-1]``.
 * Domain faces are numbered 0:x-, 1:x+, 2:y-, 3:y+, 4:z-, 5:z+.  Faces of
   axes that the problem does not resolve (``axis >= dim``) are ignored.
-* ``bc_type`` is ``ISOTHERMAL`` (0), ``DIFFUSE`` (1) or ``SPECULAR`` (2, oracle
-  only so far).  Faces between a solid and a void cell are always diffusely
-  reflecting.
+* ``bc_type`` is ``ISOTHERMAL`` (0), ``DIFFUSE`` (1) or ``SPECULAR`` (2).
+  Faces between a solid and a void cell are always diffusely reflecting.
 * Directions ``s[d]`` follow the paper's angle convention
   s = (cos(theta), sin(theta)cos(phi), sin(theta)sin(phi)) with the polar
   axis along x (Methods, angle discretisation); weights sum to 4*pi.
@@ -34,7 +33,7 @@ import numpy as np
 
 ISOTHERMAL = 0
 DIFFUSE = 1
-SPECULAR = 2   # oracle only so far (the GPU library refuses it)
+SPECULAR = 2
 
 MASTER_SEED = 20250330
 
@@ -68,6 +67,7 @@ class Problem:
     T_obs: Optional[np.ndarray] = None    # observed probe temperatures
     tol: float = 1e-6
     precision: str = "fp32"
+    order: int = 1      # face values: 1 step (first-order) upwind, 2 Green-Gauss reconstructed
 
     @property
     def n_cells(self) -> int:

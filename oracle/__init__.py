@@ -9,8 +9,14 @@ Two independent parts:
 
 * ``solve`` / ``adjoint`` wrap ``bte_oracle.c``: the paper's outer source
   iteration (Methods, solution procedure) with exact per-(band, direction)
-  upwind sweeps, and the transposed fixed-point iteration of the discrete
-  adjoint (Forward and inverse modelling workflow).
+  upwind sweeps -- with step faces, or with the second-order Green-Gauss
+  faces of "Spatial discretization" as a deferred correction
+  (``problem.order = 2``) -- and the transposed fixed-point iteration of the
+  discrete adjoint (Forward and inverse modelling workflow), with the
+  gradients w.r.t. tau_b, the wall temperatures, the source amplitude and
+  the domain lengths.
+* ``transient`` wraps the implicit-Euler time stepping of the transient BTE
+  (the extension the paper's Conclusion announces).
 * ``dense`` assembles the linear system (L - P W - R) e = s that the
   iteration converges to and solves it directly (tiny grids only).
 
@@ -55,6 +61,7 @@ def load_library(path: str):
     lib = ctypes.CDLL(path)
     lib.orc_solve.restype = ctypes.c_int
     lib.orc_adjoint.restype = ctypes.c_int
+    lib.orc_transient.restype = ctypes.c_int
     return lib
 
 
@@ -77,6 +84,7 @@ class _Problem(ctypes.Structure):
         ("bc_T", ctypes.c_void_p),
         ("phi", ctypes.c_void_p),
         ("Q_amp", ctypes.c_double),
+        ("order", ctypes.c_int),
     ]
 
 
@@ -124,6 +132,7 @@ def _marshal(p, keep):
     st.bc_type, st.bc_T = _ptr(arrs["bc_type"]), _ptr(arrs["bc_T"])
     st.phi = _ptr(arrs["phi"])
     st.Q_amp = float(p.Q_amp)
+    st.order = int(getattr(p, "order", 1))
     return st
 
 
@@ -169,18 +178,46 @@ def adjoint(p, e, T, g, max_iter: int = 100000, tol: float = 1e-13, want_mu: boo
     g_tau = np.zeros(p.B)
     g_Tw = np.zeros(6)
     g_Q = ctypes.c_double(0.0)
+    g_L = np.zeros(3)
     mu = np.empty_like(e) if want_mu else None
     it = lib.orc_adjoint(ctypes.byref(st), _ptr(e), _ptr(T), _ptr(g), ctypes.c_int(max_iter),
                          ctypes.c_double(tol), _ptr(g_tau), _ptr(g_Tw), ctypes.byref(g_Q),
-                         _ptr(mu))
+                         _ptr(g_L), _ptr(mu))
     if it == -2:
         raise ValueError("oracle: a specular face needs the mirror of every direction in the direction set")
+    if it == -3:
+        raise ValueError("oracle: the adjoint is that of the first-order (step face) system")
     if it < 0:
         raise MemoryError("oracle: allocation failed")
-    out = dict(g_tau=g_tau, g_Tw=g_Tw, g_Q=g_Q.value, iters=it)
+    out = dict(g_tau=g_tau, g_Tw=g_Tw, g_Q=g_Q.value, g_L=g_L, iters=it)
     if want_mu:
         out["mu"] = mu
     return out
+
+
+def transient(p, dt, n_steps, max_iter: int = 100000, tol: float = 1e-13, T_init=None, lib=None):
+    """Implicit Euler time steps of the transient BTE from the equilibrium at
+    T_init (default ``p.T_init``), each converged to eps_T < tol.
+
+    Returns dict(T [N] final, e [N,B,D] final, T_hist [n_steps, N],
+    iters [n_steps], total)."""
+    lib = lib or _load()
+    keep = []
+    st = _marshal(p, keep)
+    N = p.n_cells
+    T = np.empty(N)
+    T[:] = p.T_init if T_init is None else T_init
+    T[p.mask == 0] = 0.0
+    e = np.empty((N, p.B, p.D))
+    T_hist = np.zeros((n_steps, N))
+    iters = np.zeros(n_steps, dtype=np.int32)
+    total = lib.orc_transient(ctypes.byref(st), _ptr(T), _ptr(e), ctypes.c_double(dt), ctypes.c_int(n_steps),
+                              ctypes.c_int(max_iter), ctypes.c_double(tol), _ptr(T_hist), _ptr(iters))
+    if total == -2:
+        raise ValueError("oracle: a specular face needs the mirror of every direction in the direction set")
+    if total < 0:
+        raise MemoryError("oracle: allocation failed")
+    return dict(T=T, e=e, T_hist=T_hist, iters=iters, total=total)
 
 
 def flux(p, e, lib=None):

@@ -33,7 +33,35 @@
  *
  * The adjoint (Forward and inverse modelling workflow: discrete adjoint of
  * the implicit solve) solves (L - P W - R)^T mu = W^T g by the transposed
- * fixed-point iteration and returns dJ/dtau_b, dJ/dT_wall and dJ/dQ_amp.
+ * fixed-point iteration and returns dJ/dtau_b, dJ/dT_wall, dJ/dQ_amp and the
+ * geometric gradient dJ/dL_a (the paper's 1D inverse problem recovers a film
+ * thickness): a^a = v |s_a| / h_a with h_a = L_a / n_a, so with the inflow
+ * value e_in of axis a (upwind cell, wall or reflection)
+ *   dJ/dL_a = (1/L_a) sum_{c,b,d} mu_cbd a^a_bd (e_cbd - e_in,a,cbd).
+ *
+ * Second-order faces (p->order == 2; Spatial discretization: the face value
+ * is the upwind cell's value plus its Green-Gauss gradient times the vector
+ * from the cell centre to the face centre), solved as the paper's
+ * incremental form prescribes: the implicit operator keeps the step
+ * (first-order) faces and the reconstruction increments
+ *   delta_a(c) = sign(s_a) h_a/2 * grad_a e(c)
+ * of the previous iterate enter the right-hand side (deferred correction),
+ *   rhs += sum_a a^a (delta_a(upwind cell) [interior in-face] - delta_a(c)).
+ * Green-Gauss gradient: grad_a e(c) = (G+ - G-)/h_a with the face values
+ *   interior face                       (e_c + e_neighbour)/2,
+ *   boundary face the direction enters  its inflow value,
+ *   boundary face the direction leaves  e_c + (e_c - e_neighbour)/2 (linear
+ *                                        extrapolation from the neighbour),
+ * and grad_a = 0 in a cell that has no neighbour along a.  Outgoing face
+ * values at boundary faces are reconstructed too (e_c + delta), also in the
+ * diffuse and specular reflections.  Readings of the paper, which gives the
+ * reconstruction but not its boundary treatment.
+ *
+ * Transient steps (orc_transient; the paper's Conclusion names transient
+ * transport as the next extension): implicit Euler in time of
+ *   de/dt + v s.grad e = -(e - e0)/tau + Q,
+ * every step solved like the steady problem (source iteration with exact
+ * sweeps) with 1/dt added to the diagonal and e^m/dt to the source.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -59,6 +87,7 @@ typedef struct {
     const double *bc_T;          /* 6 */
     const double *phi;           /* N or NULL */
     double Q_amp;
+    int order;                   /* 1: step faces; 2: Green-Gauss reconstructed faces */
 } orc_problem;
 
 static const double FOUR_PI = 4.0 * M_PI;
@@ -155,22 +184,92 @@ static double Q_band(const orc_problem *p, long c, int b) {
 
 #define E(arr, c, b, d) (arr)[((c) * (long)p->B + (b)) * p->D + (d)]
 
+/* Reconstruction increments of second-order faces: DEL(del, c, b, d, a). */
+#define DEL(arr, c, b, d, a) (arr)[(((c) * (long)p->B + (b)) * p->D + (d)) * 3 + (a)]
+
 /* Energy carried into a diffuse side of cell c, band b, by the previous
- * iterate: sum over outgoing d' of w |s.n| e_old, over the normaliser. */
-static double diffuse_inflow(const orc_problem *p, const double *e_old, long c, int b, int side) {
+ * iterate: sum over outgoing d' of w |s.n| times the outgoing face value
+ * (the cell value, plus its reconstruction increment for second-order
+ * faces: del non-NULL), over the normaliser. */
+static double diffuse_inflow(const orc_problem *p, const double *e_old, const double *del, long c, int b,
+                             int side) {
     int a = side / 2;
     double sg = side_sign(side), acc = 0.0;
     for (int d = 0; d < p->D; ++d) {
         double sn = p->s[3 * d + a] * sg;
-        if (sn > 0.0) acc += p->w[d] * sn * E(e_old, c, b, d);
+        if (sn > 0.0) acc += p->w[d] * sn * (E(e_old, c, b, d) + (del ? DEL(del, c, b, d, a) : 0.0));
     }
     return acc / diffuse_norm(p, side);
 }
 
+/* Value entering cell c (band b, direction d) through its boundary side
+ * `side` of kind 1 (isothermal), 2 (diffuse) or 3 (specular), from the
+ * previous iterate. */
+static double boundary_inflow(const orc_problem *p, const int *mirror, const double *e_old, const double *del,
+                              long c, int b, int d, int side, int kind) {
+    int a = side / 2;
+    if (kind == 1) return p->C[b] * p->bc_T[side] / FOUR_PI;
+    if (kind == 3) {
+        int m = mirror[3 * d + a];
+        return E(e_old, c, b, m) + (del ? DEL(del, c, b, m, a) : 0.0);
+    }
+    return diffuse_inflow(p, e_old, del, c, b, side);
+}
+
+/* Second-order faces: the reconstruction increments delta_a(c, b, d) =
+ * sign(s_a) h_a/2 grad_a e of iterate e, for every solid cell, band,
+ * direction and resolved axis (zero for s_a = 0).  Directions that leave a
+ * cell through a boundary face are done first (their Green-Gauss value there
+ * is an extrapolation), since the inflow values of the others at that face
+ * are built from them. */
+static void reconstruct(const orc_problem *p, const int *mirror, const double *e, double *del) {
+    long N = n_cells(p);
+    for (long c = 0; c < N; ++c)
+        for (int b = 0; b < p->B; ++b)
+            for (int d = 0; d < p->D; ++d)
+                for (int a = 0; a < 3; ++a) DEL(del, c, b, d, a) = 0.0;
+    for (int pass = 0; pass < 2; ++pass)
+    for (long c = 0; c < N; ++c) {
+        if (!p->mask[c]) continue;
+        for (int b = 0; b < p->B; ++b)
+            for (int d = 0; d < p->D; ++d)
+                for (int a = 0; a < p->dim; ++a) {
+                    double sa = p->s[3 * d + a];
+                    if (sa == 0.0) continue;
+                    int side_in = upwind_side(p, d, a), side_out = side_in ^ 1;
+                    int k_in = side_kind(p, c, side_in), k_out = side_kind(p, c, side_out);
+                    /* pass 0: directions leaving through a boundary face; pass 1: the rest */
+                    if ((pass == 0) != (k_out != 0)) continue;
+                    double ec = E(e, c, b, d), g = 0.0;
+                    if (k_in == 0 || k_out == 0) {
+                        double G[2];   /* face values on the minus and plus sides of axis a */
+                        for (int sd = 0; sd < 2; ++sd) {
+                            int side = 2 * a + sd;
+                            int kind = side_kind(p, c, side);
+                            if (kind == 0) {
+                                G[sd] = 0.5 * (ec + E(e, neighbour(p, c, side), b, d));
+                            } else if (side == side_in) {
+                                G[sd] = boundary_inflow(p, mirror, e, del, c, b, d, side, kind);
+                            } else {
+                                double en = E(e, neighbour(p, c, side ^ 1), b, d);
+                                G[sd] = ec + 0.5 * (ec - en);
+                            }
+                        }
+                        g = (G[1] - G[0]) / p->h[a];
+                    }
+                    DEL(del, c, b, d, a) = (sa > 0.0 ? 1.0 : -1.0) * 0.5 * p->h[a] * g;
+                }
+    }
+}
+
 /* One exact transport solve for (b, d) at frozen T and frozen reflected
- * inflow: a triple loop over the cells in the upwind order of d's octant. */
+ * inflow: a triple loop over the cells in the upwind order of d's octant.
+ * del: reconstruction increments of the previous iterate (second-order
+ * faces) or NULL; e_prev, inv_dt: the previous time step's e and 1/dt of a
+ * transient step, or NULL and 0. */
 static void sweep_one(const orc_problem *p, const int *mirror, int b, int d, const double *T,
-                      const double *e_old, double *e_new) {
+                      const double *e_old, double *e_new, const double *del, const double *e_prev,
+                      double inv_dt) {
     int start[3], stop[3], step[3];
     for (int a = 0; a < 3; ++a) {
         int fwd = (a >= p->dim) || (p->s[3 * d + a] >= 0.0);
@@ -187,6 +286,10 @@ static void sweep_one(const orc_problem *p, const int *mirror, int b, int d, con
         double tc = tau_cb(p, c, b);
         double diag = 1.0 / tc;
         double rhs = p->C[b] * T[c] / (FOUR_PI * tc) + Q_band(p, c, b);
+        if (e_prev) {
+            diag += inv_dt;
+            rhs += inv_dt * E(e_prev, c, b, d);
+        }
         for (int a = 0; a < p->dim; ++a) {
             double sa = p->s[3 * d + a];
             if (sa == 0.0) continue;
@@ -196,10 +299,13 @@ static void sweep_one(const orc_problem *p, const int *mirror, int b, int d, con
             int kind = side_kind(p, c, side);
             double ein;
             if (kind == 0) ein = E(e_new, neighbour(p, c, side), b, d);
-            else if (kind == 1) ein = p->C[b] * p->bc_T[side] / FOUR_PI;
-            else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + a]);
-            else ein = diffuse_inflow(p, e_old, c, b, side);
+            else ein = boundary_inflow(p, mirror, e_old, del, c, b, d, side, kind);
             rhs += coef * ein;
+            if (del) {
+                /* deferred correction: reconstructed minus step face values */
+                if (kind == 0) rhs += coef * DEL(del, neighbour(p, c, side), b, d, a);
+                rhs -= coef * DEL(del, c, b, d, a);
+            }
         }
         E(e_new, c, b, d) = rhs / diag;
     }
@@ -269,13 +375,19 @@ int orc_solve(const orc_problem *p, double *T_io, double *e_io, int max_iter,
         for (int b = 0; b < p->B; ++b)
             for (int d = 0; d < p->D; ++d)
                 E(e_io, c, b, d) = p->mask[c] ? p->C[b] * T_io[c] / FOUR_PI : 0.0;
+    double *del = NULL;
+    if (p->order == 2) {
+        del = (double *)malloc(sizeof(double) * NE * 3);
+        if (!del) { free(e_old); free(T_new); free(mirror); return -1; }
+    }
     int it = 0;
     while (it < max_iter) {
         memcpy(e_old, e_io, sizeof(double) * NE);
+        if (del) reconstruct(p, mirror, e_old, del);
         /* step 2: exact transport solve of every (band, direction) */
         for (int b = 0; b < p->B; ++b)
             for (int d = 0; d < p->D; ++d)
-                sweep_one(p, mirror, b, d, T_io, e_old, e_io);
+                sweep_one(p, mirror, b, d, T_io, e_old, e_io, del, NULL, 0.0);
         /* step 3: update e0 and T */
         temperature(p, e_io, T_new);
         double eps = eps_T(p, T_io, T_new);
@@ -288,7 +400,62 @@ int orc_solve(const orc_problem *p, double *T_io, double *e_io, int max_iter,
     free(e_old);
     free(T_new);
     free(mirror);
+    free(del);
     return it;
+}
+
+/*
+ * Transient: n_steps implicit Euler steps of length dt from the equilibrium
+ * at T_io (e = e0(T_init)).  Every step is converged by source iteration
+ * (eps_T < tol, at most max_iter iterations; the first iteration of a step
+ * starts from the previous step's T and e).  T_io holds the final T on exit,
+ * e_io the final e; T_hist (n_steps * N, may be NULL) the temperature after
+ * every step, iters (n_steps, may be NULL) the iterations of every step.
+ * First-order faces.  Returns the total number of iterations, or -1/-2 as
+ * orc_solve.
+ */
+int orc_transient(const orc_problem *p, double *T_io, double *e_io, double dt, int n_steps, int max_iter,
+                  double tol, double *T_hist, int *iters) {
+    long N = n_cells(p);
+    long NE = N * (long)p->B * p->D;
+    double *e_old = (double *)malloc(sizeof(double) * NE);
+    double *e_prev = (double *)malloc(sizeof(double) * NE);
+    double *T_new = (double *)malloc(sizeof(double) * N);
+    int *mirror = mirror_table(p);
+    if (!e_old || !e_prev || !T_new || !mirror) {
+        free(e_old); free(e_prev); free(T_new); free(mirror);
+        return -1;
+    }
+    if (!mirrors_complete(p, mirror)) {
+        free(e_old); free(e_prev); free(T_new); free(mirror);
+        return -2;
+    }
+    double inv_dt = 1.0 / dt;
+    for (long c = 0; c < N; ++c)
+        for (int b = 0; b < p->B; ++b)
+            for (int d = 0; d < p->D; ++d)
+                E(e_io, c, b, d) = p->mask[c] ? p->C[b] * T_io[c] / FOUR_PI : 0.0;
+    int total = 0;
+    for (int m = 0; m < n_steps; ++m) {
+        memcpy(e_prev, e_io, sizeof(double) * NE);
+        int it = 0;
+        while (it < max_iter) {
+            memcpy(e_old, e_io, sizeof(double) * NE);
+            for (int b = 0; b < p->B; ++b)
+                for (int d = 0; d < p->D; ++d)
+                    sweep_one(p, mirror, b, d, T_io, e_old, e_io, NULL, e_prev, inv_dt);
+            temperature(p, e_io, T_new);
+            double eps = eps_T(p, T_io, T_new);
+            memcpy(T_io, T_new, sizeof(double) * N);
+            ++it;
+            if (tol > 0.0 && eps < tol) break;
+        }
+        total += it;
+        if (iters) iters[m] = it;
+        if (T_hist) memcpy(T_hist + (long)m * N, T_io, sizeof(double) * N);
+    }
+    free(e_old); free(e_prev); free(T_new); free(mirror);
+    return total;
 }
 
 /* ----------------------------------------------------------------------- */
@@ -372,12 +539,14 @@ static void adj_sweep_one(const orc_problem *p, const int *mirror, int b, int d,
  * Adjoint of the converged forward state (e, T) for the loss gradient
  * g = dJ/dT.  Iterates mu <- L^{-T}(W^T(P^T mu + g) + R^T mu) from mu = 0
  * until the relative RMS change of Theta drops below tol (or max_iter).
- * Outputs: g_tau[B], g_Tw[6] (isothermal domain faces), g_Q (scalar).
- * mu_out (N*B*D) may be NULL.  Returns the iteration count.
+ * Outputs: g_tau[B], g_Tw[6] (isothermal domain faces), g_Q (scalar),
+ * g_L[3] (dJ/dL_a, zero for unresolved axes).  mu_out (N*B*D) may be NULL.
+ * Returns the iteration count (-3 for a second-order problem).
  */
 int orc_adjoint(const orc_problem *p, const double *e, const double *T, const double *g,
                 int max_iter, double tol, double *g_tau, double *g_Tw, double *g_Q,
-                double *mu_out) {
+                double *g_L, double *mu_out) {
+    if (p->order == 2) return -3;   /* the adjoint is that of the step-face system */
     long N = n_cells(p);
     long NE = N * (long)p->B * p->D;
     double *mu = (double *)calloc(NE, sizeof(double));
@@ -421,6 +590,7 @@ int orc_adjoint(const orc_problem *p, const double *e, const double *T, const do
     for (int b = 0; b < p->B; ++b) g_tau[b] = 0.0;
     for (int f = 0; f < 6; ++f) g_Tw[f] = 0.0;
     *g_Q = 0.0;
+    for (int a = 0; a < 3; ++a) g_L[a] = 0.0;
     for (long c = 0; c < N; ++c) {
         if (!p->mask[c]) continue;
         for (int b = 0; b < p->B; ++b) {
@@ -434,6 +604,20 @@ int orc_adjoint(const orc_problem *p, const double *e, const double *T, const do
             /* d/dtau_b of 1/tau_cb is -1/(tau_cb tau_b) */
             g_tau[b] += acc / (tc * p->tau[b]);
             if (p->phi) *g_Q += p->phi[c] * p->C[b] / (FOUR_PI * Csum) * musum;
+            /* cell size: a^a = v |s_a| / h_a, h_a = L_a / n_a; the inflow
+             * value of axis a is the upwind cell's, the wall's or the
+             * reflection of the converged e */
+            for (int d = 0; d < p->D; ++d)
+                for (int a = 0; a < p->dim; ++a) {
+                    double sa = p->s[3 * d + a];
+                    if (sa == 0.0) continue;
+                    int side = upwind_side(p, d, a);
+                    int kind = side_kind(p, c, side);
+                    double ein = (kind == 0) ? E(e, neighbour(p, c, side), b, d)
+                                             : boundary_inflow(p, mirror, e, NULL, c, b, d, side, kind);
+                    double coef = p->v[b] * fabs(sa) / p->h[a];
+                    g_L[a] += E(mu, c, b, d) * coef * (E(e, c, b, d) - ein) / (p->h[a] * p->n[a]);
+                }
             /* isothermal inflow a_bd C_b T_w / (4 pi) enters the source */
             for (int a = 0; a < p->dim; ++a) {
                 for (int sd = 0; sd < 2; ++sd) {

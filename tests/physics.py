@@ -80,3 +80,41 @@ def gray_slab_integral_equation(eta_L: float, M: int = 4000):
     K[np.arange(M), np.arange(M)] = 2.0 * (1.0 - E2(d / 2))
     phi = np.linalg.solve(np.eye(M) - 0.5 * K, 0.5 * E2(eta))
     return eta, phi
+
+
+def gray_slab_discrete_ordinates(mu, w, L_over_mfp: float, M: int):
+    """Spatially continuous solution of the discrete-ordinates gray slab:
+    for each ordinate mu_i the transport along x is integrated exactly
+    (exponential attenuation over the mean free path times |mu_i|), which
+    leaves one integral equation for phi = (T - T_c)/(T_h - T_c) with the
+    walls at phi = 1 (x = 0) and 0 (x = L):
+
+        phi(x) = sum_{mu_i > 0} w_i/(4 pi) [exp(-x/l_i)
+                    + int_0^x phi(x') exp(-(x - x')/l_i) dx'/l_i]
+               + sum_{mu_i < 0} w_i/(4 pi) int_x^L phi(x') exp(-(x' - x)/l_i) dx'/l_i,
+
+    l_i = |mu_i| (in units of the mean free path, L = L_over_mfp).  Solved
+    by collocation at the midpoints of M panels with phi constant on each
+    panel and the exponentials integrated exactly over it.  Only the angular
+    discretisation is shared with a finite-volume solution, so it isolates
+    the spatial discretisation error.  Returns (panel midpoints, phi)."""
+    L = float(L_over_mfp)
+    h = L / M
+    xm = (np.arange(M) + 0.5) * h
+    lo, hi = xm - h / 2, xm + h / 2
+    K = np.zeros((M, M))
+    f = np.zeros(M)
+    for mi, wi in zip(mu, w):
+        li = abs(mi)
+        c = wi / FOUR_PI
+        if mi > 0:
+            f += c * np.exp(-xm / li)
+            d_hi = np.clip(xm[:, None] - hi[None, :], 0.0, None)
+            d_lo = np.clip(xm[:, None] - lo[None, :], 0.0, None)
+            K += c * (np.exp(-d_hi / li) - np.exp(-d_lo / li))
+        else:
+            d_lo = np.clip(lo[None, :] - xm[:, None], 0.0, None)
+            d_hi = np.clip(hi[None, :] - xm[:, None], 0.0, None)
+            K += c * (np.exp(-d_lo / li) - np.exp(-d_hi / li))
+    phi = np.linalg.solve(np.eye(M) - K, f)
+    return xm, phi

@@ -23,10 +23,10 @@ MUTATIONS = {
                        "double rhs = -p->C[b] * T[c] / (FOUR_PI * tc)"),
     "temperature_without_tau": ("num += acc / tc;", "num += acc;"),
     "upwind_side_swapped": ("> 0.0) ? 2 * a : 2 * a + 1;", "> 0.0) ? 2 * a + 1 : 2 * a;"),
-    "diffuse_from_incoming": ("if (sn > 0.0) acc += p->w[d] * sn * E(e_old",
-                              "if (sn < 0.0) acc += p->w[d] * sn * E(e_old"),
-    "diffuse_norm_pi": ("return acc / diffuse_norm(p, side);\n}\n\n/* One exact",
-                        "return acc / M_PI;\n}\n\n/* One exact"),
+    "diffuse_from_incoming": ("if (sn > 0.0) acc += p->w[d] * sn * (E(e_old",
+                              "if (sn < 0.0) acc += p->w[d] * sn * (E(e_old"),
+    "diffuse_norm_pi": ("return acc / diffuse_norm(p, side);\n}\n\n/* Value entering",
+                        "return acc / M_PI;\n}\n\n/* Value entering"),
     "coef_without_velocity": ("double coef = p->v[b] * fabs(sa) / p->h[a];   /* v|s.n| S / V */",
                               "double coef = fabs(sa) / p->h[a];"),
     "coef_wrong_axis": ("double coef = p->v[b] * fabs(sa) / p->h[a];   /* v|s.n| S / V */",
@@ -39,6 +39,10 @@ MUTATIONS = {
                           "g_tau[b] -= acc / (tc * p->tau[b]);"),
     "theta_without_capacity": ("acc += p->C[b] / (FOUR_PI * tau_cb(p, c, b)) * sm;",
                                "acc += 1.0 / (FOUR_PI * tau_cb(p, c, b)) * sm;"),
+    "length_gradient_wrong_axis": ("g_L[a] += E(mu, c, b, d) * coef * (E(e, c, b, d) - ein) / (p->h[a] * p->n[a]);",
+                                   "g_L[a] += E(mu, c, b, d) * coef * (E(e, c, b, d) - ein) / (p->h[0] * p->n[0]);"),
+    "length_gradient_no_inflow": ("g_L[a] += E(mu, c, b, d) * coef * (E(e, c, b, d) - ein) / (p->h[a] * p->n[a]);",
+                                  "g_L[a] += E(mu, c, b, d) * coef * (E(e, c, b, d) - 0.0 * ein) / (p->h[a] * p->n[a]);"),
     "flux_axis_slip": ("q[3 * c + a] += p->v[b] * p->w[d] * p->s[3 * d + a] * E(e, c, b, d);",
                        "q[3 * c + a] += p->v[b] * p->w[d] * p->s[3 * d] * E(e, c, b, d);"),
     "flux_axes_swapped": ("q[3 * c + a] += p->v[b] * p->w[d] * p->s[3 * d + a] * E(e, c, b, d);",
@@ -90,17 +94,18 @@ def _battery(lib):
         fd = dense.fd_gradients(p, probes, T_obs)
         ok = (np.allclose(a["g_tau"], fd["g_tau"], rtol=1e-4)
               and np.allclose(a["g_Tw"], fd["g_Tw"], rtol=1e-4, atol=1e-8)
-              and abs(a["g_Q"] - fd["g_Q"]) <= 1e-4 * abs(fd["g_Q"]))
+              and abs(a["g_Q"] - fd["g_Q"]) <= 1e-4 * abs(fd["g_Q"])
+              and np.allclose(a["g_L"], fd["g_L"], rtol=1e-4, atol=1e-6 * np.abs(fd["g_L"]).max()))
         if not ok:
             failed.append(f"adjoint{dim}")
     return failed
 
 
 SPECULAR_MUTATIONS = {
-    "specular_same_direction": ("else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + a]);",
-                                "else if (kind == 3) ein = E(e_old, c, b, d);"),
-    "specular_wrong_axis": ("else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + a]);",
-                            "else if (kind == 3) ein = E(e_old, c, b, mirror[3 * d + (a + 1) % 3]);"),
+    "specular_same_direction": ("int m = mirror[3 * d + a];\n        return E(e_old, c, b, m)",
+                                "int m = d;\n        return E(e_old, c, b, m)"),
+    "specular_wrong_axis": ("int m = mirror[3 * d + a];\n        return E(e_old, c, b, m)",
+                            "int m = mirror[3 * d + (a + 1) % 3];\n        return E(e_old, c, b, m)"),
     "specular_as_diffuse": ("return (p->bc_type[side] == ORC_SPECULAR) ? 3 : 2;", "return 2;"),
     "adjoint_without_specular": ("rhs += coef * E(mu_old, c, b, mirror[3 * d + a]);",
                                  "rhs += 0.0 * E(mu_old, c, b, mirror[3 * d + a]);"),
