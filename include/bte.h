@@ -64,6 +64,7 @@ extern "C" {
 
 #define BTE_BC_ISOTHERMAL 0
 #define BTE_BC_DIFFUSE 1
+#define BTE_BC_SPECULAR 2
 
 #define BTE_FP32 0
 #define BTE_FP64 1
@@ -98,8 +99,16 @@ typedef struct {
     const double *w;
 } bte_quad;
 
-/* Per domain face: type BTE_BC_ISOTHERMAL (wall temperature T[f], K) or
- * BTE_BC_DIFFUSE.  At least one isothermal face must touch the solid. */
+/* Per domain face: type BTE_BC_ISOTHERMAL (wall temperature T[f], K),
+ * BTE_BC_DIFFUSE or BTE_BC_SPECULAR (Methods, Boundary conditions: a
+ * specularly reflecting wall returns into direction d the energy the cell
+ * sends out through it in the mirror direction of d, the component normal to
+ * the face reversed; like the diffuse inflow it is taken from the previous
+ * iterate, which leaves the converged fixed point unchanged).  A specular
+ * face needs the mirror of every direction in the direction set (a product
+ * set of Gauss-Legendre polar nodes and an even number of mid-point azimuths
+ * has them); problems with specular faces are swept by the general kernel
+ * (tile_kind 1).  At least one isothermal face must touch the solid. */
 typedef struct {
     int type[6];
     double T[6];
@@ -112,7 +121,8 @@ typedef struct {
  *   q_profile N doubles, W/m^3 per unit source amplitude, or NULL (no source)
  *   out       receives the plan (NULL on failure)
  * Returns BTE_OK, BTE_EINVAL (bad sizes, sum w != 4 pi, tau <= 0, mask value
- * > R, no isothermal face touching the solid), BTE_ENOMEM or BTE_ECUDA.
+ * > R, no isothermal face touching the solid, a specular face without the
+ * mirror of every direction), BTE_ENOMEM or BTE_ECUDA.
  * Uses the current CUDA device.  On failure nothing is leaked.
  */
 int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands,
@@ -144,6 +154,17 @@ typedef struct {
                                (planes in flight per pass); 0 = autotuned */
     int lane_axis;          /* 3D plane-pipeline kernel: axis of the rows its lanes hold,
                                1 = y (planes along z), 2 = z (planes along y); 0 = autotuned */
+    int face_order;         /* face values (Methods, Spatial discretization): 0 or 1 = step
+                               (first-order) upwind faces; 2 = the paper's second-order faces,
+                               upwind cell value plus its Green-Gauss gradient times the centre-to-
+                               face vector, solved as a deferred correction (the incremental form:
+                               step faces implicit, the reconstruction increments of the previous
+                               iterate in the source).  Green-Gauss face values at a boundary face:
+                               the inflow value where a direction enters it, linear extrapolation
+                               from the neighbour where it leaves, no gradient along an axis without
+                               a neighbour; outgoing boundary values are reconstructed, also in the
+                               reflections.  face_order 2 runs the general kernel, stores e every
+                               iteration and needs 4 N B D extra values of device memory */
 } bte_solve_opts;
 
 typedef struct {
@@ -166,6 +187,11 @@ typedef struct {
     int warps_z;            /* 3D plane-pipeline tile: warps along the plane axis per CTA
                                (other kernels: 0) */
     int lane_axis;          /* 3D plane-pipeline tile: row axis, 1 = y, 2 = z (other kernels: 0) */
+    double eps_q;           /* bte_solve with q_out: the flux residual of the convergence criteria
+                               (Methods, solution procedure), sqrt(mean_c (|q|^n - |q|^{n+1})^2) /
+                               max_c |q|^{n+1} over solid cells, for the returned iterate n and one
+                               more iteration from it (reported, not used to stop); NaN when not
+                               computed (no q_out, specular faces, face_order 2, adjoint) */
 } bte_stats;
 
 /* Fill opts with defaults: FP32, tol 1e-6, max_iter 100000, T_init 300 K,
@@ -203,6 +229,42 @@ int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out
  */
 int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau,
                 double *g_Twall, double *g_Qamp, bte_stats *st);
+
+/*
+ * bte_adjoint_ex -- bte_adjoint that also returns, when g_L is not NULL,
+ *   g_L[3]     dJ/dL_a, the derivative with respect to the domain length
+ *              along each resolved axis (0 for the others), host memory.
+ * The cell size is h_a = L_a / n_a and the coupling a^a = v |s_a| / h_a, so
+ * dJ/dL_a = (1/L_a) sum_{c,b,d} mu_cbd a^a_bd (e_cbd - e_in,a,cbd) with e_in
+ * the value entering along a (upwind cell, wall or reflection of the
+ * converged state); the source profile stays per cell.  (The paper's 1D
+ * inverse problem recovers a film thickness this way.)  Needs 3 N B S extra
+ * values of device memory (S direction subsets of the general kernel).
+ * Returns as bte_adjoint; BTE_ESTATE also after a second-order solve (the
+ * adjoint is that of the step-face system).
+ */
+int bte_adjoint_ex(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau,
+                   double *g_Twall, double *g_Qamp, double *g_L, bte_stats *st);
+
+/*
+ * bte_transient -- transient phonon transport (the extension the paper's
+ * Conclusion announces): n_steps implicit-Euler steps of length dt (s) of
+ *   de/dt + v s.grad e = -(e - e0)/tau + Q
+ * from the equilibrium at o->T_init (or T_init_uniform).  Every step is the
+ * steady problem with 1/dt added to the diagonal and e^m/dt to the source,
+ * solved by the same source iteration to eps_T < o->tol (at most o->max_iter
+ * iterations per step); the temperature follows from the same energy
+ * balance of the scattering term (Eq. updatee0_t).  Step faces; general
+ * kernel (tile_kind 0 or 1).
+ *   T_out   N doubles: T after the last step (host or device), required
+ *   T_hist  n_steps * N doubles: T after every step (host or device), or NULL
+ *   st      totals over the steps (iterations, seconds), or NULL
+ * Returns BTE_OK, BTE_ENOTCONVERGED (a step reached max_iter; outputs still
+ * written), BTE_EINVAL, BTE_ENUMERIC, BTE_ECUDA.  The plan holds no
+ * adjoint-ready state afterwards.
+ */
+int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, double *T_out,
+                  double *T_hist, bte_stats *st);
 
 /*
  * bte_profile_sweep -- time the dominant kernel: `reps` forward sweep
@@ -278,32 +340,46 @@ const char *bte_batch_last_error(const bte_batch *b);
  * BTE_OK, BTE_EINVAL or BTE_ECUDA. */
 int bte_batch_set_sweep_timing(bte_batch *b, int on);
 
+/*
+ * bte_debug_set_wait_limit -- test hook: the number of polls after which the
+ * row-pipeline kernel's waits for the warp below give up (0 restores the
+ * default, about 1e6 polls of ~32 ns).  A wait that gives up records the
+ * failure and the solve returns BTE_ETIMEOUT (its results are then not
+ * valid); the kernel still ends normally, with every access in bounds, and
+ * the plan stays usable.  Waits for bulk copies in flight keep their own
+ * limit.  Returns BTE_OK or BTE_EINVAL (null plan, polls < 0).
+ */
+int bte_debug_set_wait_limit(bte_plan *p, long long polls);
+
 /* Copy the eps_T history of the last bte_solve (one value per iteration,
  * at most n, the first 65536 iterations) into out (host).  Returns the
  * number of values copied or a negative code. */
 int bte_eps_history(const bte_plan *p, double *out, int n);
 
 /*
- * bte_eps_T_noalloc -- the convergence measure of the solution procedure,
+ * bte_eps_T_noalloc -- the outer iteration's convergence measure,
  * eps_T = sqrt(mean_c (T_old - T_new)^2) / max_c T_new over solid cells,
- * computed on the GPU without allocating any memory.  (The paper has no
- * counterpart; this is an interface for callers that cannot call cudaMalloc:
- * e.g. hosts whose device memory is owned by their own pool, loops that must
- * not trigger cudaMalloc's implicit device synchronisation, or code running
- * while another thread captures a CUDA graph in global mode.)
+ * computed on the GPU without allocating any memory.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc
+ * where they need the measure -- a host framework whose device memory all
+ * belongs to its own pool, a loop that must never trigger the implicit
+ * device synchronisation of cudaMalloc, or code that runs while another
+ * thread captures a CUDA graph in global mode, where such calls are refused.
  *   T_old, T_new  N doubles, device memory
  *   mask          N bytes, device memory (0 = void, skipped), or NULL (all solid)
  *   N             1 <= N <= BTE_NOALLOC_MAX_CELLS
  *   out           3 doubles, device memory: {eps_T, max T_new, solid count}
  *   stream        cudaStream_t (NULL = legacy default stream)
- * Scratch lives in a fixed file-scope device array (about 24 KB, kept by
+ * Scratch lives in a fixed file-scope device array (about 24 KB, held by
  * every GPU that loads the library until the process exits).  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current; make that first call before any stream capture.
- * All calls on a device share the array: calls that overlap on the GPU race.
- * Returns BTE_OK, BTE_EINVAL (null pointer, N out of range; see
- * bte_last_error(NULL)) or BTE_ECUDA.  Asynchronous: out is written when the
- * stream reaches the launch.
+ * on a device -- and the first after a device reset, which gives the device
+ * a new context -- looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that call before any
+ * stream capture.  All calls on a device share the array and it keeps the
+ * last call's contents (the call clears its counter itself): calls that
+ * overlap on the GPU race.  Returns BTE_OK, BTE_EINVAL (null pointer, N out
+ * of range; see bte_last_error(NULL)) or BTE_ECUDA.  Asynchronous: out is
+ * written when the stream reaches the launch.
  */
 #define BTE_NOALLOC_MAX_CELLS (1LL << 24)
 int bte_eps_T_noalloc(const double *T_old, const double *T_new, const uint8_t *mask, long long N,

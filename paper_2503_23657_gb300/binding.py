@@ -35,7 +35,8 @@ ERROR_NAMES = {
 EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_error",
            "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep",
            "bte_set_sweep_timing", "bte_eps_T_noalloc", "bte_batch_create", "bte_batch_solve",
-           "bte_batch_destroy", "bte_batch_last_error", "bte_batch_set_sweep_timing"]
+           "bte_batch_destroy", "bte_batch_last_error", "bte_batch_set_sweep_timing", "bte_adjoint_ex",
+           "bte_transient", "bte_debug_set_wait_limit"]
 
 
 class Grid(ctypes.Structure):
@@ -62,7 +63,7 @@ class SolveOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("poll_every", ctypes.c_int),
                 ("dirs_per_lane", ctypes.c_int), ("store_e_every_iter", ctypes.c_int),
                 ("tile_kind", ctypes.c_int), ("dirs_per_cta", ctypes.c_int), ("source_staging", ctypes.c_int),
-                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int)]
+                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int), ("face_order", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -72,7 +73,7 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("tile_kind", ctypes.c_int),
                 ("dirs_per_cta", ctypes.c_int), ("sweep_seconds", ctypes.c_double),
                 ("sweep_launches", ctypes.c_longlong), ("source_staged", ctypes.c_int),
-                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int)]
+                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int), ("eps_q", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -133,6 +134,12 @@ def load(path: str = LIB_PATH):
     lib.bte_batch_set_sweep_timing.restype = ip
     lib.bte_eps_T_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp]
     lib.bte_eps_T_noalloc.restype = ip
+    lib.bte_adjoint_ex.argtypes = [vp, vp, dp, ip, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+    lib.bte_adjoint_ex.restype = ip
+    lib.bte_transient.argtypes = [vp, ctypes.POINTER(SolveOpts), dp, ip, vp, vp, ctypes.POINTER(Stats)]
+    lib.bte_transient.restype = ip
+    lib.bte_debug_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.bte_debug_set_wait_limit.restype = ip
     _lib = lib
     return lib
 
@@ -230,12 +237,9 @@ class Plan:
     def error(self) -> str:
         return self._lib.bte_last_error(self._h).decode()
 
-    def solve(self, T_out, q_out=None, e_out=None, precision=BTE_FP32, tol=1e-6, max_iter=100000,
-              T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None,
-              poll_every=32, dirs_per_lane=0, store_e_every_iter=False, tile_kind=0, dirs_per_cta=0,
-              source_staging=0, warps_z=0, lane_axis=0, check=True):
-        """Run bte_solve.  Buffers are numpy arrays (host) or torch tensors
-        (host or CUDA) of the documented sizes.  Returns (rc, stats dict)."""
+    def _opts(self, precision, tol, max_iter, T_init, T_init_uniform, Q_amp, tau, T_wall, stream, poll_every,
+              dirs_per_lane, store_e_every_iter, tile_kind, dirs_per_cta, source_staging, warps_z, lane_axis,
+              face_order, keep):
         p = self.problem
         o = SolveOpts()
         self._lib.bte_default_opts(ctypes.byref(o))
@@ -247,6 +251,7 @@ class Plan:
         o.Q_amp = p.Q_amp if Q_amp is None else Q_amp
         tau_a = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
         tw_a = None if T_wall is None else np.ascontiguousarray(T_wall, dtype=np.float64)
+        keep += [tau_a, tw_a]
         o.tau = _addr(tau_a)
         o.T_wall = _addr(tw_a)
         o.stream = stream
@@ -258,6 +263,35 @@ class Plan:
         o.source_staging = source_staging
         o.warps_z = warps_z
         o.lane_axis = lane_axis
+        o.face_order = face_order
+        return o
+
+    def transient(self, dt, n_steps, T_out, T_hist=None, precision=BTE_FP64, tol=1e-10, max_iter=100000,
+                  T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None, poll_every=32,
+                  check=True):
+        """Run bte_transient: n_steps implicit-Euler steps of length dt.
+        Returns (rc, stats dict)."""
+        keep = []
+        o = self._opts(precision, tol, max_iter, T_init, T_init_uniform, Q_amp, tau, T_wall, stream, poll_every,
+                       0, False, 0, 0, 0, 0, 0, 1, keep)
+        st = Stats()
+        rc = self._lib.bte_transient(self._h, ctypes.byref(o), float(dt), int(n_steps), _addr(T_out), _addr(T_hist),
+                                     ctypes.byref(st))
+        if check and rc != BTE_OK:
+            raise BTEError(rc, self.error())
+        return rc, st.as_dict()
+
+    def solve(self, T_out, q_out=None, e_out=None, precision=BTE_FP32, tol=1e-6, max_iter=100000,
+              T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None,
+              poll_every=32, dirs_per_lane=0, store_e_every_iter=False, tile_kind=0, dirs_per_cta=0,
+              source_staging=0, warps_z=0, lane_axis=0, face_order=1, check=True):
+        """Run bte_solve.  Buffers are numpy arrays (host) or torch tensors
+        (host or CUDA) of the documented sizes.  Returns (rc, stats dict)."""
+        p = self.problem
+        keep = []
+        o = self._opts(precision, tol, max_iter, T_init, T_init_uniform, Q_amp, tau, T_wall, stream, poll_every,
+                       dirs_per_lane, store_e_every_iter, tile_kind, dirs_per_cta, source_staging, warps_z,
+                       lane_axis, face_order, keep)
         st = Stats()
         rc = self._lib.bte_solve(self._h, ctypes.byref(o), _addr(T_out), _addr(q_out), _addr(e_out),
                                  ctypes.byref(st))
@@ -265,17 +299,22 @@ class Plan:
             raise BTEError(rc, self.error())
         return rc, st.as_dict()
 
-    def adjoint(self, dJ_dT, tol=1e-10, max_iter=100000, check=True):
-        """Run bte_adjoint; returns (rc, g_tau [B], g_Twall [6], g_Qamp, stats)."""
+    def adjoint(self, dJ_dT, tol=1e-10, max_iter=100000, check=True, lengths=False):
+        """Run bte_adjoint (bte_adjoint_ex with lengths=True); returns (rc,
+        g_tau [B], g_Twall [6], g_Qamp, stats), and g_L [3] last when
+        lengths=True."""
         p = self.problem
         g_tau = np.zeros(p.B)
         g_Tw = np.zeros(6)
         g_Q = np.zeros(1)
+        g_L = np.zeros(3) if lengths else None
         st = Stats()
-        rc = self._lib.bte_adjoint(self._h, _addr(dJ_dT), tol, max_iter, _addr(g_tau), _addr(g_Tw),
-                                   _addr(g_Q), ctypes.byref(st))
+        rc = self._lib.bte_adjoint_ex(self._h, _addr(dJ_dT), tol, max_iter, _addr(g_tau), _addr(g_Tw),
+                                      _addr(g_Q), _addr(g_L), ctypes.byref(st))
         if check and rc != BTE_OK:
             raise BTEError(rc, self.error())
+        if lengths:
+            return rc, g_tau, g_Tw, float(g_Q[0]), st.as_dict(), g_L
         return rc, g_tau, g_Tw, float(g_Q[0]), st.as_dict()
 
     def profile_sweep(self, reps=20):
@@ -291,6 +330,13 @@ class Plan:
         iteration with CUDA events (0 = off); stats then carry sweep_seconds /
         sweep_launches."""
         rc = self._lib.bte_set_sweep_timing(self._h, int(every))
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
+
+    def set_wait_limit(self, polls):
+        """bte_debug_set_wait_limit (test hook): polls before a row-pipeline
+        wait gives up (0: the default)."""
+        rc = self._lib.bte_debug_set_wait_limit(self._h, int(polls))
         if rc != BTE_OK:
             raise BTEError(rc, self.error())
 

@@ -33,9 +33,11 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 //   bits 0..3  region id (0 = void, r >= 1 solid of region r)
 //   bits 4..9  side s (0:x- 1:x+ 2:y- 3:y+ 4:z- 5:z+) is a boundary face
 //              (outside the domain or next to a void cell)
+//   bits 10..15 side s is an isothermal domain face
 // ---------------------------------------------------------------------------
 constexpr int kRegionMask = 0xF;
 constexpr int kSideShift = 4;
+constexpr int kIsoShift = 10;
 constexpr int kMaxRegions = 15;
 
 __host__ __device__ inline int face_of(int base, int flags, int side) {
@@ -80,6 +82,7 @@ struct Subset {
 template <typename real>
 struct SweepParams {
     int nx, ny, nz;
+    int dim;                          // resolved axes
     int B, D, F, S, R;
     int Spad;                         // S rounded up to a multiple of 4
     int WY, WZ;                       // warps along y, warp groups along z
@@ -103,6 +106,20 @@ struct SweepParams {
     int store_e;                      // fwd: write e
     int read_e;                       // adj: accumulate (mu-w Theta)(e-e0) into gpart
     int ein_smem;                     // stage this band's boundary values in shared memory
+    // specularly reflecting domain faces (null sidx: the problem has none)
+    const int *__restrict__ sidx;     // [F] index of a face among the specular faces, -1 otherwise
+    const int *__restrict__ mirror;   // [3][D] direction with the axis-a component reversed
+    const real *__restrict__ spec_in; // [B][Fs][D] inflow at specular faces (previous iterate)
+    real *__restrict__ spec_out;      // [B][Fs][D] outgoing values stored under the mirror direction
+    int Fs;
+    // extra source of forward sweeps: xscale * xsrc[c][b][d] (null: none)
+    const real *__restrict__ xsrc;
+    real xscale;
+    // adjoint gradient pass: per-axis cell-size partials (null: none)
+    //   glpart[a][b][Spad][N] += sum_d mu_d a^a_d (e_d - e_in,a,d)
+    real *__restrict__ glpart;
+    const real *__restrict__ ein_fwd;   // [B][F] forward inflow values of the converged state
+    const real *__restrict__ spec_fwd;  // [B][Fs][D] forward specular inflow of the converged state
 };
 
 // Parameters of the row-block sweep for unmasked 1D/2D grids with one region
@@ -154,9 +171,14 @@ struct Sweep2DParams {
     int stage;                        // stage per-cell inputs in shared memory (TMA bulk copy)
     int groups;                       // row-pipeline kernel: direction groups per CTA
     int adj;                          // row-pipeline kernel: 1 = adjoint sweep
+    long long spin_limit;             // row-pipeline kernel: polls of a wait for the warp below
     FinalizeParams fin;               // row-pipeline kernel: finalize the previous iteration
                                       // (fin.pending null: nothing to finalize)
 };
+
+// Default poll limit of the row-pipeline kernel's waits for the warp below
+// (each poll sleeps ~32 ns: about 35 ms at most).
+constexpr long long kPipeSpinLimit = 1LL << 20;
 
 template <typename real>
 cudaError_t launch_sweep2d(const Sweep2DParams<real> &p, int dirs_per_warp, int row_blocks, bool adjoint,
@@ -239,7 +261,7 @@ struct UpdateParams {
     const double *__restrict__ Kinv;  // [R]   1 / sum_b C_b/tau_rb
     const int *__restrict__ face_cell;
     const int *__restrict__ face_side;
-    const int *__restrict__ face_kind;   // 0 isothermal domain face, 1 diffuse
+    const int *__restrict__ face_kind;   // 0 isothermal domain face, 1 diffuse, 2 specular domain face
     const real *__restrict__ ein_fixed;  // [B][F] isothermal inflow (fwd)
     real *__restrict__ ein_out;          // [B][F]
     double *__restrict__ fsum_total;     // [B][F] raw face sums (adj, for gradients) or null
@@ -275,6 +297,9 @@ cudaError_t launch_sweep(const SweepParams<real> &p, int dirs_per_lane, int laye
 
 // Largest CTA (threads) the sweep tile supports, or 0 if not instantiated.
 int sweep_max_threads(int dirs_per_lane, int layers_per_lane, bool three_d);
+// Directions per lane of the general kernel's extended variant (specular
+// faces, extra source, cell-size gradient partials).
+constexpr int kSpecDW = 4;
 
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st);
@@ -295,6 +320,32 @@ template <typename real>
 cudaError_t launch_permute_e(long long N, int B, int D, const int2 *cell, const real *e_int, const int *perm,
                              const double *shift /*[B]*/, real *e_user, cudaStream_t st);
 
+// Second-order faces as a deferred correction (order2.cu).
+template <typename real>
+struct Order2Params {
+    long long N, NBD;                 // cells, N * B * D
+    int nx, ny, dim, B, D, F, Fs;
+    const int2 *__restrict__ cell;
+    const real *__restrict__ e;       // [N][B][D] previous iterate
+    const real *__restrict__ coef;    // [B][D][8]
+    const int *__restrict__ dneg;     // [D] bit a: s_a < 0
+    const int *__restrict__ face_kind;
+    const int *__restrict__ sidx;     // [F] or null
+    const int *__restrict__ mirror;   // [3][D] or null
+    const real *__restrict__ ein_fixed;   // [B][F] isothermal inflow
+    const double *__restrict__ side_scale; // [6][B] 1 / diffuse normaliser
+    real *__restrict__ del;           // [3][N][B][D] reconstruction increments
+    real *__restrict__ corr;          // [N][B][D] source of the next sweep
+    real *__restrict__ ein_out;       // [B][F] next sweep's inflow (diffuse entries rewritten)
+    real *__restrict__ spec_out;      // [B][Fs][D] next sweep's specular inflow, or null
+    const int *__restrict__ done;     // stop flag (null: none)
+};
+template <typename real>
+cudaError_t launch_order2(const Order2Params<real> &p, cudaStream_t st);
+template <typename real>
+cudaError_t launch_equilibrium(long long N, int B, int D, const int2 *cell, const real *tdev, const real *cb4pi, real *e,
+                               cudaStream_t st);
+
 // Gradient reduction after the final adjoint sweep (all FP64 accumulation).
 template <typename real>
 struct GradParams {
@@ -311,9 +362,11 @@ struct GradParams {
     const int *__restrict__ face_side;
     const int *__restrict__ face_kind;  // 0 isothermal domain face
     const double *__restrict__ msum;    // [B][F] raw adjoint face sums sum_d a_d mu_d
-    double *__restrict__ blockpart;     // [gridDim][B+7]
+    const real *__restrict__ glpart;    // [3][B][Spad][N] cell-size partials, or null
+    double *__restrict__ blockpart;     // [gridDim][B+10]
     unsigned int *__restrict__ counter;
-    double *__restrict__ out;           // [B + 6 + 1]: dJ/dtau_b, dJ/dT_wall[6], dJ/dQ_amp
+    double *__restrict__ out;           // [B + 10]: dJ/dtau_b, dJ/dT_wall[6], dJ/dQ_amp,
+                                        //   sum mu a^a (e - e_in) per axis (x3)
 };
 
 template <typename real>

@@ -84,6 +84,13 @@ struct Workspace {
     DevBuf fin_fwd, fin_adj;  // UpdateParams<real> read by the finalize kernel (forward / adjoint)
     DevBuf gradpart;  // gradient reduction block partials
     DevBuf wrap;      // plane-pipeline 3D sweep: last plane of a pass, per CTA
+    DevBuf spec[2], mspec[2];  // [B][Fs][D] specular-face inflow (forward / adjoint state sets)
+    // extra source of the general kernel's forward sweeps (transient steps:
+    // the previous step's e over dt; second-order faces: the deferred
+    // correction), and the buffers behind it
+    const real *xsrc = nullptr;
+    real xscale = real(0);
+    DevBuf eprev, del, corr, glpart, ttmp, Tstep;
     // plane-pipeline 3D sweep: skewed copies of the cell records, the source
     // profile and the forward / adjoint sweep sources (both parities)
     // (one set per row axis: [0] rows along y, [1] rows along z)
@@ -120,9 +127,23 @@ struct bte_plan {
     std::vector<int2> cellinfo;
     int F = 0;
     std::vector<int> face_cell, face_side, face_kind;
+    int xmode = 0;                    // the current solve: 0 steady step faces, 1 transient step,
+                                      // 2 second-order faces (deferred correction)
+    double cur_inv_dt = 0.0;          // 1/dt of a transient step (0: steady)
+    double forced_T_ref = NAN;        // T_ref kept over the steps of a transient run (NaN: from T_init)
+    int solved_order = 1;             // face order of the last solve
+    bool want_glen = false;           // the running adjoint forms dJ/dL
+    long long spin_limit = kPipeSpinLimit;  // row-pipeline waits (test hook: bte_debug_set_wait_limit)
+    double g_L[3] = {0, 0, 0};        // dJ/dL_a of the last bte_adjoint_ex
+    std::vector<int> dneg;            // [D] bit a: s_a < 0 (internal order)
+    int Fs = 0;                       // specular domain faces
+    std::vector<int> sidx;            // [F] specular index of a face (-1: not specular)
+    std::vector<int> spec_faces;      // [Fs] face of each specular index
+    std::vector<int> mirror;          // [3][D] internal direction with the axis-a component reversed (-1: none)
     double side_norm[6], side_out[6];  // sum over entering / leaving dirs of w |s.n|
     // device, precision independent
     DevBuf d_cell, d_face_cell, d_face_side, d_face_kind, d_perm, d_status, d_counter, d_blockpart, d_hist;
+    DevBuf d_sidx, d_mirror, d_dneg;
     int hist_cap = 0;
     Status *h_status = nullptr;  // pinned
     Workspace<float> ws32;
@@ -373,6 +394,17 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
                                  int cw_req = 0, int staging_req = 0, int wz_req = 0, int axis_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
+    if (p->Fs > 0 || p->xmode != 0) {
+        // specular faces, transient steps, second-order faces: the general
+        // kernel's extended variant
+        const int mt = sweep_max_threads(kSpecDW, lz, p->dim == 3);
+        const int WY = (p->ny + 31) / 32;
+        const int WZ = p->dim == 3 && lz ? (p->nz + lz - 1) / lz : 1;
+        if (lz != 0 && (kind_req == 0 || kind_req == 1) && (!dw_req || dw_req == kSpecDW) && mt > 0 &&
+            WY * WZ * 32 <= mt)
+            out.push_back(tile_id(0, kSpecDW, kSpecDW));
+        return out;
+    }
     if (lz != 0 && (kind_req == 0 || kind_req == 1)) {
         const bool z = p->dim == 3;
         const int WY = (p->ny + 31) / 32;
@@ -550,7 +582,7 @@ int upload_tables(bte_plan *p, Workspace<real> &ws) {
             cf[7] = 0;
             for (int r = 0; r < R; ++r) {
                 const double trb = tau[b] * p->tau_scale[r];
-                invd[((size_t)r * B + b) * D + d] = (real)(1.0 / (1.0 / trb + a[0] + a[1] + a[2]));
+                invd[((size_t)r * B + b) * D + d] = (real)(1.0 / (1.0 / trb + p->cur_inv_dt + a[0] + a[1] + a[2]));
             }
             for (int ax = 0; ax < 3; ++ax) vws[((size_t)b * D + d) * 3 + ax] = p->v[b] * p->w[d] * p->s[3 * d + ax];
         }
@@ -618,6 +650,8 @@ int ensure_workspace(bte_plan *p, Workspace<real> &ws) {
         CK(p, ws.ein[i].ensure(sizeof(real) * B * F));
         CK(p, ws.T[i].ensure(sizeof(double) * N));
     }
+    if (p->Fs > 0)
+        for (int i = 0; i < 2; ++i) CK(p, ws.spec[i].ensure(sizeof(real) * B * (size_t)p->Fs * p->D));
     // the partial sets are sized by the tiles in use (ensure_subsets)
     std::vector<real> ph(N + 16, (real)0);
     for (size_t c = 0; c < N && !p->phi.empty(); ++c) ph[c] = (real)p->phi[c];
@@ -635,6 +669,7 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int tid, bool a
     sp.nx = p->nx;
     sp.ny = p->ny;
     sp.nz = p->nz;
+    sp.dim = p->dim;
     sp.B = p->B;
     sp.D = p->D;
     sp.F = std::max(p->F, 1);
@@ -662,6 +697,11 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int tid, bool a
     const size_t ein_bytes = sizeof(real) * (size_t)sp.F;
     const size_t xchg = sizeof(real) * (size_t)sp.WY * sp.WZ * (2 * lz * 16 + (p->dim == 3 ? 2 * 32 * 16 : 0));
     sp.ein_smem = (ein_bytes + xchg <= 200 * 1024) ? 1 : 0;
+    if (p->Fs > 0) {
+        sp.sidx = p->d_sidx.as<int>();
+        sp.mirror = p->d_mirror.as<int>();
+        sp.Fs = p->Fs;
+    }
     return sp;
 }
 
@@ -754,6 +794,7 @@ Sweep2DParams<real> sweep2d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     sp.wall_stride = p->wall_stride;
     sp.done = p->d_status.as<int>();
     sp.status = &p->d_status.as<Status>()->status;
+    sp.spin_limit = p->spin_limit;
     int stage = 0;
     rowblock_ok(p, (int)sizeof(real), &stage, sp.warps_per_cta, sp.ring);
     sp.stage = stage;
@@ -805,7 +846,8 @@ Sweep3DParams<real> sweep3d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
 template <typename real>
 cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool adj, const real *tsrc,
                               const real *ein, bool store_e, bool use_done, cudaStream_t stream,
-                              const FinalizeParams *fin = nullptr) {
+                              const FinalizeParams *fin = nullptr, const real *spec_in = nullptr,
+                              real *spec_out = nullptr) {
     const Tile tl = tile_of(tid);
     if (is_pipe3(tl.kind)) {
         Sweep3DParams<real> sp = sweep3d_params(p, ws, tid, adj);
@@ -833,6 +875,12 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
     sp.ein = ein;
     sp.store_e = store_e ? 1 : 0;
     sp.e = ws.e.template as<real>();
+    sp.spec_in = spec_in;
+    sp.spec_out = spec_out;
+    if (!adj && p->xmode != 0) {
+        sp.xsrc = ws.xsrc;
+        sp.xscale = ws.xscale;
+    }
     if (!use_done) sp.done = nullptr;
     return launch_sweep<real>(sp, tl.dw, tile_layers(p), p->dim == 3, adj, stream);
 }
@@ -847,14 +895,52 @@ inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t stream) {
     return cudaEventRecord(ev, stream);
 }
 
+// Second-order faces: reconstruction increments of the previous iterate
+// (ws.e), the next sweep's inflow values rebuilt from them, and its
+// deferred-correction source (ws.corr).
+template <typename real>
+cudaError_t enqueue_order2(bte_plan *p, Workspace<real> &ws, int parity, bool use_done, cudaStream_t stream) {
+    Order2Params<real> o{};
+    o.N = p->N;
+    o.NBD = (long long)p->N * p->B * p->D;
+    o.nx = p->nx;
+    o.ny = p->ny;
+    o.dim = p->dim;
+    o.B = p->B;
+    o.D = p->D;
+    o.F = std::max(p->F, 1);
+    o.Fs = p->Fs;
+    o.cell = p->d_cell.as<int2>();
+    o.e = ws.e.template as<real>();
+    o.coef = ws.coef.template as<real>();
+    o.dneg = p->d_dneg.as<int>();
+    o.face_kind = p->d_face_kind.as<int>();
+    o.sidx = p->Fs ? p->d_sidx.as<int>() : nullptr;
+    o.mirror = p->Fs ? p->d_mirror.as<int>() : nullptr;
+    o.ein_fixed = ws.ein_fixed.template as<real>();
+    o.side_scale = ws.scale_f.template as<double>();
+    o.del = ws.del.template as<real>();
+    o.corr = ws.corr.template as<real>();
+    o.ein_out = ws.ein[parity].template as<real>();
+    o.spec_out = p->Fs ? ws.spec[parity].template as<real>() : nullptr;
+    o.done = use_done ? p->d_status.as<int>() : nullptr;
+    return launch_order2<real>(o, stream);
+}
+
 template <typename real>
 cudaError_t enqueue_forward(bte_plan *p, Workspace<real> &ws, int tid, int parity, double tol, bool store_e,
                             bool replay, cudaStream_t stream, cudaEvent_t ta = nullptr, cudaEvent_t tb = nullptr) {
+    if (p->xmode == 2 && !replay) {
+        const cudaError_t e2 = enqueue_order2(p, ws, parity, true, stream);
+        if (e2 != cudaSuccess) return e2;
+        store_e = true;   // the next iteration reconstructs from this one
+    }
     cudaError_t e = ta ? record_timing_event(ta, stream) : cudaSuccess;
     const FinalizeParams fin = fin_params(p, tol, false);
     if (e == cudaSuccess)
         e = launch_tile_sweep(p, ws, tid, false, ws.tdev[parity].template as<real>(), ws.ein[parity].template as<real>(),
-                              store_e, !replay, stream, &fin);
+                              store_e, !replay, stream, &fin, ws.spec[parity].template as<real>(),
+                              ws.spec[parity ^ 1].template as<real>());
     if (e == cudaSuccess && tb) e = record_timing_event(tb, stream);
     if (e != cudaSuccess || replay) return e;
     UpdateParams<real> u = update_params(p, ws, tid, false, tol);
@@ -888,7 +974,7 @@ int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaS
         if (!(T0[c] > 0.0) || !std::isfinite(T0[c])) return fail(p, BTE_EINVAL, "T_init must be finite and > 0 in solid cells");
         sum += T0[c];
     }
-    p->T_ref = sum / (double)p->n_active;
+    p->T_ref = std::isnan(p->forced_T_ref) ? sum / (double)p->n_active : p->forced_T_ref;
     std::vector<real> td(N);
     for (long long c = 0; c < N; ++c) td[c] = p->mask[c] ? (real)(T0[c] - p->T_ref) : (real)0;
     const int B = p->B, F = std::max(p->F, 1);
@@ -912,6 +998,18 @@ int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaS
             CK(p, launch_skew<real>(N, ws.skew[map], ws.tdev[0].template as<real>(), ws.skt[map][0].template as<real>(),
                                     stream));
     CK(p, cudaMemcpyAsync(ws.ein[0].p, e0.data(), sizeof(real) * e0.size(), cudaMemcpyHostToDevice, stream));
+    std::vector<real> s0;
+    if (p->Fs > 0) {
+        // the initial e = e0(T_init) is isotropic: every mirror direction carries it
+        s0.resize((size_t)B * p->Fs * p->D);
+        for (int b = 0; b < B; ++b)
+            for (int k = 0; k < p->Fs; ++k) {
+                const long long c = p->face_cell[p->spec_faces[k]];
+                const real v = (real)(p->C[b] * (T0[c] - p->T_ref) / kFourPi);
+                std::fill(s0.begin() + ((size_t)b * p->Fs + k) * p->D, s0.begin() + ((size_t)b * p->Fs + k + 1) * p->D, v);
+            }
+        CK(p, cudaMemcpyAsync(ws.spec[0].p, s0.data(), sizeof(real) * s0.size(), cudaMemcpyHostToDevice, stream));
+    }
     CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
     CK(p, cudaStreamSynchronize(stream));
@@ -1010,7 +1108,8 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
                                             o->source_staging, o->warps_z, o->lane_axis);
     if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
     const int tkey =
-        ((((o->lane_axis * 20 + o->warps_z) * 10 + o->source_staging) * 10 + o->tile_kind) * 100 + o->dirs_per_lane) *
+        (((((p->xmode * 3 + o->lane_axis) * 20 + o->warps_z) * 10 + o->source_staging) * 10 + o->tile_kind) * 100 +
+         o->dirs_per_lane) *
             1000 +
         o->dirs_per_cta;
     int tid;
@@ -1025,18 +1124,32 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     if ((rc = ensure_subsets(p, ws, dw))) return rc;
     // e of the final iterate is always regenerated on the device (outputs and
     // the adjoint read it)
-    CK(p, ws.e.ensure(sizeof(real) * (size_t)p->N * p->B * p->D));
+    const size_t NBD = (size_t)p->N * p->B * p->D;
+    CK(p, ws.e.ensure(sizeof(real) * NBD));
+    if (p->xmode == 2) {
+        CK(p, ws.del.ensure(sizeof(real) * 3 * NBD));
+        CK(p, ws.corr.ensure(sizeof(real) * NBD));
+        CK(p, cudaMemsetAsync(ws.corr.p, 0, sizeof(real) * NBD, stream));
+        ws.xsrc = ws.corr.template as<real>();
+        ws.xscale = real(1);
+    }
     const double tol = o->tol;
     // one launch outside any capture sets the kernel's shared-memory attribute
     CK(p, enqueue_forward(p, ws, dw, 0, tol, false, true, stream));
     // re-initialise after autotuning / the warm launch touched the work buffers
     if ((rc = begin_state(p, o, ws, stream))) return rc;
+    if (p->xmode == 2) {
+        // the previous iterate of the first iteration: the equilibrium at T_init
+        CK(p, launch_equilibrium<real>(p->N, p->B, p->D, p->d_cell.as<int2>(), ws.tdev[0].template as<real>(),
+                                       ws.cb4pi.template as<real>(), ws.e.template as<real>(), stream));
+    }
     int poll = o->poll_every > 0 ? o->poll_every : 32;
     poll = std::max(2, poll + (poll & 1));
     const bool store_every = o->store_e_every_iter != 0;
     if (p->time_every) CK(p, ensure_timing_events(p, poll));
     // graph of `poll` iterations (even, so every replay starts at parity 0)
-    auto key = std::make_tuple(dw, poll, tol, (store_every ? 1 : 0) | (p->time_every << 1));
+    auto key = std::make_tuple(dw, poll, tol + 1e3 * p->cur_inv_dt,
+                               (store_every ? 1 : 0) | (p->xmode << 1) | (p->time_every << 3));
     // the finalize kernel that closes every replay / eager chunk (a no-op
     // unless the tile defers finalization)
     {
@@ -1100,6 +1213,22 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     const bool bad = sflag != 0;
     const bool converged = tol > 0.0 && p->h_status->done && !bad;
     if (sflag == 2) return fail(p, BTE_ETIMEOUT, "a bounded device wait (bulk copy) expired");
+    // eps_q (solution procedure, step 4; reported, not used to stop): the
+    // change of |q| over one more iteration from the returned state, from the
+    // e of iteration n + 1 (swept from the kept inputs of iteration n; not
+    // with specular faces, whose inflow arrays that sweep would overwrite)
+    double eps_q = NAN;
+    const bool want_eps_q = q_out && st && n > 0 && p->Fs == 0 && p->xmode == 0;
+    std::vector<double> q_next;
+    if (want_eps_q) {
+        CK(p, ws.q.ensure(sizeof(double) * 3 * p->N));
+        CK(p, enqueue_forward(p, ws, dw, n & 1, tol, true, true, stream));
+        CK(p, launch_flux<real>(p->N, p->B, p->D, p->d_cell.as<int2>(), ws.e.template as<real>(), ws.vws.template as<double>(),
+                                ws.qshift.template as<double>(), ws.q.template as<double>(), stream));
+        launches += 2;
+        q_next.resize(3 * (size_t)p->N);
+        CK(p, cudaMemcpyAsync(q_next.data(), ws.q.p, sizeof(double) * 3 * p->N, cudaMemcpyDeviceToHost, stream));
+    }
     // regenerate e^n from the inputs of the last iteration
     if (n > 0) CK(p, enqueue_forward(p, ws, dw, (n - 1) & 1, tol, true, true, stream));
     if (n > 0) launches += 1;
@@ -1112,6 +1241,21 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
                                 ws.qshift.template as<double>(), ws.q.template as<double>(), stream));
         launches += 1;
         CK(p, cudaMemcpyAsync(q_out, ws.q.p, sizeof(double) * 3 * p->N, cudaMemcpyDefault, stream));
+        if (want_eps_q) {
+            std::vector<double> q_now(3 * (size_t)p->N);
+            CK(p, cudaMemcpyAsync(q_now.data(), ws.q.p, sizeof(double) * 3 * p->N, cudaMemcpyDeviceToHost, stream));
+            CK(p, cudaStreamSynchronize(stream));
+            double ss = 0.0, qmax = 0.0;
+            for (long long c = 0; c < p->N; ++c) {
+                if (!p->mask[c]) continue;
+                const double *a = &q_now[3 * c], *b2 = &q_next[3 * c];
+                const double m0 = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                const double m1 = std::sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+                ss += (m0 - m1) * (m0 - m1);
+                qmax = std::max(qmax, m1);
+            }
+            eps_q = qmax > 0.0 ? std::sqrt(ss / (double)p->n_active) / qmax : 0.0;
+        }
     }
     if (e_out && n > 0) {
         const size_t ne = (size_t)p->N * p->B * p->D;
@@ -1136,6 +1280,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     CK(p, cudaStreamSynchronize(stream));
     p->solved = true;
     p->stream = stream;
+    p->solved_order = p->xmode == 2 ? 2 : 1;
     p->solved_precision = (sizeof(real) == 4) ? BTE_FP32 : BTE_FP64;
     p->solved_iters = n;
     p->solved_tile = tid;
@@ -1155,6 +1300,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         st->source_staged = source_staged_kind(tile_of(tid).kind);
         st->warps_z = is_pipe3(tile_of(tid).kind) ? pipe3_h(tile_of(tid)) : 0;
         st->lane_axis = is_pipe3(tile_of(tid).kind) ? 1 + pipe3_map(tile_of(tid)) : 0;
+        st->eps_q = eps_q;
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the temperature update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "max_iter reached before eps_T < tol");
@@ -1172,7 +1318,8 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
         const FinalizeParams fin = fin_params(p, tol, true);
         if (e == cudaSuccess)
             e = launch_tile_sweep(p, ws, dw, true, ws.thdev[parity].template as<real>(), ws.mein[parity].template as<real>(),
-                                  false, true, stream, &fin);
+                                  false, true, stream, &fin, ws.mspec[parity].template as<real>(),
+                                  ws.mspec[parity ^ 1].template as<real>());
         if (e == cudaSuccess && tb) e = record_timing_event(tb, stream);
         if (e != cudaSuccess) return e;
         UpdateParams<real> u = update_params(p, ws, dw, true, tol);
@@ -1191,6 +1338,15 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
     sp.gpart = ws.gpart.template as<real>();
     sp.read_e = final_pass ? 1 : 0;
     sp.tfwd = ws.tdev[p->solved_iters & 1].template as<real>();
+    sp.spec_in = ws.mspec[parity].template as<real>();
+    sp.spec_out = ws.mspec[parity ^ 1].template as<real>();
+    if (final_pass && p->want_glen) {
+        // cell-size partials against the inflow the final forward e was made from
+        const int fpar = (p->solved_iters - 1) & 1;
+        sp.glpart = ws.glpart.template as<real>();
+        sp.ein_fwd = ws.ein[fpar].template as<real>();
+        sp.spec_fwd = p->Fs ? ws.spec[fpar].template as<real>() : nullptr;
+    }
     if (final_pass) sp.done = nullptr;
     cudaError_t e = launch_sweep<real>(sp, tile_of(dw).dw, tile_layers(p), p->dim == 3, true, stream);
     if (e != cudaSuccess) return e;
@@ -1210,12 +1366,13 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
 
 template <typename real>
 int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Tw, double *g_Q,
-              bte_stats *st) {
+              double *g_L, bte_stats *st) {
     cudaStream_t stream = p->stream;
     Workspace<real> &ws = ws_of<real>(p);
     const int dw = p->solved_tile;
-    // the final gradient pass reads e and runs on a general tile
-    std::vector<int> gen = tile_candidates(p, (int)sizeof(real), 1, 0);
+    // the final gradient pass reads e and runs on a general tile (the
+    // extended variant when it also forms the cell-size partials)
+    std::vector<int> gen = tile_candidates(p, (int)sizeof(real), 1, g_L ? kSpecDW : 0);
     if (gen.empty()) return fail(p, BTE_EINVAL, "no general sweep tile for the gradient pass");
     const int gtile = gen[0];
     if (int rc2 = ensure_subsets(p, ws, gtile)) return rc2;
@@ -1227,10 +1384,14 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         CK(p, ws.mein[i].ensure(sizeof(real) * (size_t)B * F));
         CK(p, ws.theta[i].ensure(sizeof(double) * N));
     }
+    if (p->Fs > 0) {
+        for (int i = 0; i < 2; ++i) CK(p, ws.mspec[i].ensure(sizeof(real) * (size_t)B * p->Fs * p->D));
+    }
     CK(p, ws.gpart.ensure(sizeof(real) * ((S + 3) & ~(size_t)3) * B * N));
+    if (g_L) CK(p, ws.glpart.ensure(sizeof(real) * 3 * ((S + 3) & ~(size_t)3) * B * N));
     CK(p, ws.msum.ensure(sizeof(double) * (size_t)B * F));
     CK(p, ws.g.ensure(sizeof(double) * N));
-    CK(p, ws.grad_out.ensure(sizeof(double) * (B + 7)));
+    CK(p, ws.grad_out.ensure(sizeof(double) * (B + 10)));
     std::vector<double> g(N);
     if (is_device_ptr(dJ_dT)) {
         CK(p, cudaMemcpyAsync(g.data(), dJ_dT, sizeof(double) * N, cudaMemcpyDeviceToHost, stream));
@@ -1264,6 +1425,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
             CK(p, launch_skew<real>(N, ws.skew[map], ws.thdev[0].template as<real>(), ws.ska[map][0].template as<real>(),
                                     stream));
     CK(p, cudaMemsetAsync(ws.mein[0].p, 0, sizeof(real) * (size_t)B * F, stream));
+    if (p->Fs > 0) CK(p, cudaMemsetAsync(ws.mspec[0].p, 0, sizeof(real) * (size_t)B * p->Fs * p->D, stream));
     CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
     CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
     if (!p->e_current) {
@@ -1357,14 +1519,15 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     gp.face_side = p->d_face_side.as<int>();
     gp.face_kind = p->d_face_kind.as<int>();
     gp.msum = ws.msum.template as<double>();
+    gp.glpart = g_L ? ws.glpart.template as<real>() : nullptr;
     const int nblk = (int)((N + 255) / 256) + (p->F + 255) / 256;
-    CK(p, ws.gradpart.ensure(sizeof(double) * (size_t)nblk * (B + 7)));
+    CK(p, ws.gradpart.ensure(sizeof(double) * (size_t)nblk * (B + 10)));
     gp.blockpart = ws.gradpart.template as<double>();
     gp.counter = p->d_counter.as<unsigned int>();
     gp.out = ws.grad_out.template as<double>();
     CK(p, launch_grad<real>(gp, stream));
-    std::vector<double> out(B + 7);
-    CK(p, cudaMemcpyAsync(out.data(), ws.grad_out.p, sizeof(double) * (B + 7), cudaMemcpyDeviceToHost, stream));
+    std::vector<double> out(B + 10);
+    CK(p, cudaMemcpyAsync(out.data(), ws.grad_out.p, sizeof(double) * (B + 10), cudaMemcpyDeviceToHost, stream));
     CK(p, cudaEventRecord(p->ev1, stream));
     CK(p, cudaEventSynchronize(p->ev1));
     float ms = 0.f;
@@ -1374,7 +1537,13 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         for (int f = 0; f < 6; ++f) g_Tw[f] = (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL) ? out[B + f] : 0.0;
     }
     if (g_Q) *g_Q = out[B + 6];
+    if (g_L) {
+        // dJ/dL_a = (1/L_a) sum mu a^a (e - e_in): a^a = v |s_a| / h_a, h_a = L_a / n_a
+        const int nn[3] = {p->nx, p->ny, p->nz};
+        for (int a = 0; a < 3; ++a) g_L[a] = a < p->dim ? out[B + 7 + a] / (p->h[a] * nn[a]) : 0.0;
+    }
     if (st) {
+        st->eps_q = NAN;
         st->iterations = n;
         st->converged = converged;
         st->eps_T = p->h_status->last[0];
@@ -1393,6 +1562,90 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     }
     if (bad) return fail(p, BTE_ENUMERIC, "NaN or Inf in the adjoint update");
     if (tol > 0.0 && !converged) return fail(p, BTE_ENOTCONVERGED, "adjoint: max_iter reached before tol");
+    return BTE_OK;
+}
+
+// Transient: n_steps implicit-Euler steps of length dt, every one a solve of
+// the steady machinery with 1/dt on the diagonal (upload_tables) and the
+// previous step's e over dt as the extra source of the general kernel's
+// extended variant; T_ref stays that of the initial state over the run.
+template <typename real>
+int transient_t(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, double *T_out, double *T_hist,
+                bte_stats *st) {
+    Workspace<real> &ws = ws_of<real>(p);
+    cudaStream_t stream = (cudaStream_t)o->stream;
+    int rc = ensure_workspace(p, ws);
+    if (rc) return rc;
+    const long long N = p->N;
+    const size_t NBD = (size_t)N * p->B * p->D;
+    std::vector<double> T0(N);
+    if (o->T_init) {
+        if (is_device_ptr(o->T_init)) {
+            CK(p, cudaMemcpy(T0.data(), o->T_init, sizeof(double) * N, cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(T0.data(), o->T_init, sizeof(double) * N);
+        }
+    } else {
+        std::fill(T0.begin(), T0.end(), o->T_init_uniform);
+    }
+    double sum = 0.0;
+    std::vector<real> td(N, (real)0);
+    for (long long c = 0; c < N; ++c) {
+        if (!p->mask[c]) {
+            T0[c] = 0.0;
+            continue;
+        }
+        if (!(T0[c] > 0.0) || !std::isfinite(T0[c])) return fail(p, BTE_EINVAL, "T_init must be finite and > 0 in solid cells");
+        sum += T0[c];
+    }
+    const double T_ref = sum / (double)p->n_active;
+    for (long long c = 0; c < N; ++c) td[c] = p->mask[c] ? (real)(T0[c] - T_ref) : (real)0;
+    CK(p, ws.eprev.ensure(sizeof(real) * NBD));
+    CK(p, ws.ttmp.ensure(sizeof(real) * (N + 16)));
+    CK(p, ws.Tstep.ensure(sizeof(double) * N));
+    std::vector<real> cb(p->B);
+    for (int b = 0; b < p->B; ++b) cb[b] = (real)(p->C[b] / kFourPi);
+    CK(p, upload(ws.cb4pi, cb));
+    CK(p, cudaMemcpyAsync(ws.ttmp.p, td.data(), sizeof(real) * N, cudaMemcpyHostToDevice, stream));
+    // the initial state is the equilibrium at T_init
+    CK(p, launch_equilibrium<real>(N, p->B, p->D, p->d_cell.as<int2>(), ws.ttmp.template as<real>(),
+                                   ws.cb4pi.template as<real>(), ws.eprev.template as<real>(), stream));
+    CK(p, cudaMemcpyAsync(ws.Tstep.p, T0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream));
+    CK(p, cudaStreamSynchronize(stream));
+    p->forced_T_ref = T_ref;
+    p->xmode = 1;
+    p->cur_inv_dt = 1.0 / dt;
+    ws.xsrc = ws.eprev.template as<real>();
+    ws.xscale = (real)(1.0 / dt);
+    bte_solve_opts so = *o;
+    so.T_init = ws.Tstep.template as<double>();
+    int total = 0, all_conv = 1;
+    long long launches = 0;
+    double secs = 0.0;
+    bte_stats sm{};
+    for (int m = 0; m < n_steps; ++m) {
+        rc = solve_t<real>(p, &so, ws.Tstep.template as<double>(), nullptr, nullptr, &sm);
+        if (rc != BTE_OK && rc != BTE_ENOTCONVERGED) return rc;
+        if (rc == BTE_ENOTCONVERGED) all_conv = 0;
+        total += sm.iterations;
+        secs += sm.seconds;
+        launches += sm.kernel_launches + 1;
+        if (T_hist)
+            CK(p, cudaMemcpyAsync(T_hist + (size_t)m * N, ws.Tstep.p, sizeof(double) * N, cudaMemcpyDefault, stream));
+        // this step's e (regenerated by the solve) is the next step's previous state
+        CK(p, cudaMemcpyAsync(ws.eprev.p, ws.e.p, sizeof(real) * NBD, cudaMemcpyDeviceToDevice, stream));
+    }
+    CK(p, cudaMemcpyAsync(T_out, ws.Tstep.p, sizeof(double) * N, cudaMemcpyDefault, stream));
+    CK(p, cudaStreamSynchronize(stream));
+    if (st) {
+        *st = sm;
+        st->iterations = total;
+        st->converged = all_conv;
+        st->seconds = secs;
+        st->updates_per_s = secs > 0 ? (double)total * p->n_active * p->B * p->D / secs : 0.0;
+        st->kernel_launches = launches;
+    }
+    if (!all_conv) return fail(p, BTE_ENOTCONVERGED, "a time step reached max_iter before eps_T < tol");
     return BTE_OK;
 }
 
@@ -1471,6 +1724,10 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
         p->w[d] = quad->w[order[d]];
         p->perm[d] = order[d];
     }
+    p->dneg.assign(p->D, 0);
+    for (int d = 0; d < p->D; ++d)
+        for (int a = 0; a < 3; ++a)
+            if (p->s[3 * d + a] < 0.0) p->dneg[d] |= 1 << a;
     for (int d = 0; d < p->D;) {
         int e = d;
         while (e < p->D && key[order[e]] == key[order[d]]) ++e;
@@ -1495,7 +1752,7 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
         p->side_out[side] = nout;
     }
     for (int f = 0; f < 6; ++f) {
-        if (bcs->type[f] != BTE_BC_ISOTHERMAL && bcs->type[f] != BTE_BC_DIFFUSE)
+        if (bcs->type[f] != BTE_BC_ISOTHERMAL && bcs->type[f] != BTE_BC_DIFFUSE && bcs->type[f] != BTE_BC_SPECULAR)
             return fail(nullptr, BTE_EINVAL, "bcs: unknown face type");
         if (bcs->type[f] == BTE_BC_ISOTHERMAL && f / 2 < p->dim && (!(bcs->T[f] > 0) || !std::isfinite(bcs->T[f])))
             return fail(nullptr, BTE_EINVAL, "bcs: wall temperature must be > 0");
@@ -1528,7 +1785,14 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
                             p->face_cell.push_back((int)c);
                             p->face_side.push_back(side);
                             const bool iso = outside && p->bc_type[side] == BTE_BC_ISOTHERMAL;
-                            p->face_kind.push_back(iso ? 0 : 1);
+                            const bool spec = outside && p->bc_type[side] == BTE_BC_SPECULAR;
+                            p->face_kind.push_back(iso ? 0 : (spec ? 2 : 1));
+                            if (iso) flags |= 1 << (kIsoShift + side);
+                            p->sidx.push_back(spec ? p->Fs : -1);
+                            if (spec) {
+                                p->spec_faces.push_back(p->F);
+                                ++p->Fs;
+                            }
                             if (iso) anchored = true;
                             ++p->F;
                         }
@@ -1552,6 +1816,23 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
         p->wall_face[(size_t)side * p->wall_stride + pos] = f;
     }
     if (!anchored) return fail(nullptr, BTE_EINVAL, "no isothermal face touches the solid (temperature undetermined)");
+    // mirror directions (internal order) for the specular faces
+    p->mirror.assign((size_t)3 * p->D, -1);
+    for (int d = 0; d < p->D; ++d)
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < p->D; ++k) {
+                double err = 0.0;
+                for (int q = 0; q < 3; ++q) err += std::fabs(p->s[3 * k + q] - (q == a ? -p->s[3 * d + q] : p->s[3 * d + q]));
+                if (err < 1e-12) {
+                    p->mirror[(size_t)a * p->D + d] = k;
+                    break;
+                }
+            }
+    for (int f = 0; f < 2 * p->dim; ++f)
+        if (p->bc_type[f] == BTE_BC_SPECULAR)
+            for (int d = 0; d < p->D; ++d)
+                if (p->mirror[(size_t)(f / 2) * p->D + d] < 0)
+                    return fail(nullptr, BTE_EINVAL, "quad: a specular face needs the mirror of every direction");
     if (q_profile) {
         p->phi.assign(q_profile, q_profile + p->N);
         for (long long c = 0; c < p->N; ++c)
@@ -1873,6 +2154,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
         if (st) {
             bte_stats &s = st[i];
             std::memset(&s, 0, sizeof(s));
+            s.eps_q = NAN;
             s.iterations = it;
             s.converged = conv ? 1 : 0;
             s.eps_T = hs[i].last[0];
@@ -1955,6 +2237,11 @@ int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands, c
     CKC(upload(p->d_face_side, p->face_side));
     CKC(upload(p->d_face_kind, p->face_kind));
     CKC(upload(p->d_perm, p->perm));
+    if (p->Fs > 0) {
+        CKC(upload(p->d_sidx, p->sidx));
+        CKC(upload(p->d_mirror, p->mirror));
+    }
+    CKC(upload(p->d_dneg, p->dneg));
     CKC(upload(p->ws32.wall, p->wall_face));
     CKC(upload(p->ws64.wall, p->wall_face));
     CKC(p->d_status.ensure(sizeof(Status)));
@@ -1982,20 +2269,72 @@ int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out
         for (int f = 0; f < 6; ++f)
             if (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL && (!(o->T_wall[f] > 0) || !std::isfinite(o->T_wall[f])))
                 return fail(p, BTE_EINVAL, "T_wall override must be > 0");
+    if (o->face_order < 0 || o->face_order > 2) return fail(p, BTE_EINVAL, "face_order must be 0, 1 or 2");
     p->solved = false;
-    if (o->precision == BTE_FP32) return solve_t<float>(p, o, T_out, q_out, e_out, st);
-    if (o->precision == BTE_FP64) return solve_t<double>(p, o, T_out, q_out, e_out, st);
-    return fail(p, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+    p->xmode = o->face_order == 2 ? 2 : 0;
+    p->cur_inv_dt = 0.0;
+    p->forced_T_ref = NAN;
+    int rc;
+    if (o->precision == BTE_FP32)
+        rc = solve_t<float>(p, o, T_out, q_out, e_out, st);
+    else if (o->precision == BTE_FP64)
+        rc = solve_t<double>(p, o, T_out, q_out, e_out, st);
+    else
+        rc = fail(p, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+    p->xmode = 0;
+    return rc;
 }
 
-int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Twall,
-                double *g_Qamp, bte_stats *st) {
+int bte_adjoint_ex(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Twall,
+                   double *g_Qamp, double *g_L, bte_stats *st) {
     if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
     if (!dJ_dT) return fail(p, BTE_EINVAL, "dJ_dT is required");
     if (max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
     if (!p->solved || p->solved_iters < 1) return fail(p, BTE_ESTATE, "bte_adjoint needs a preceding bte_solve");
-    if (p->solved_precision == BTE_FP32) return adjoint_t<float>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, st);
-    return adjoint_t<double>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, st);
+    if (p->solved_order != 1)
+        return fail(p, BTE_ESTATE, "bte_adjoint differentiates step-face solves (face_order 1) only");
+    p->want_glen = g_L != nullptr;
+    const int rc = p->solved_precision == BTE_FP32
+                       ? adjoint_t<float>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, g_L, st)
+                       : adjoint_t<double>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, g_L, st);
+    p->want_glen = false;
+    return rc;
+}
+
+int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Twall,
+                double *g_Qamp, bte_stats *st) {
+    return bte_adjoint_ex(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, nullptr, st);
+}
+
+int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, double *T_out, double *T_hist,
+                  bte_stats *st) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (!o || !T_out) return fail(p, BTE_EINVAL, "opts and T_out are required");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, BTE_EINVAL, "dt must be finite and > 0");
+    if (n_steps < 1) return fail(p, BTE_EINVAL, "n_steps must be >= 1");
+    if (o->max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
+    if (o->face_order == 2) return fail(p, BTE_EINVAL, "transient steps use step faces (face_order 0 or 1)");
+    if (o->face_order < 0 || o->face_order > 2) return fail(p, BTE_EINVAL, "face_order must be 0, 1 or 2");
+    if (o->tile_kind != 0 && o->tile_kind != 1) return fail(p, BTE_EINVAL, "transient steps use the general kernel");
+    if (!o->T_init && !(o->T_init_uniform > 0.0)) return fail(p, BTE_EINVAL, "T_init_uniform must be > 0");
+    if (!std::isfinite(o->Q_amp)) return fail(p, BTE_EINVAL, "Q_amp must be finite");
+    if (o->T_wall)
+        for (int f = 0; f < 6; ++f)
+            if (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL && (!(o->T_wall[f] > 0) || !std::isfinite(o->T_wall[f])))
+                return fail(p, BTE_EINVAL, "T_wall override must be > 0");
+    p->solved = false;
+    int rc;
+    if (o->precision == BTE_FP32)
+        rc = transient_t<float>(p, o, dt, n_steps, T_out, T_hist, st);
+    else if (o->precision == BTE_FP64)
+        rc = transient_t<double>(p, o, dt, n_steps, T_out, T_hist, st);
+    else
+        rc = fail(p, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+    p->xmode = 0;
+    p->cur_inv_dt = 0.0;
+    p->forced_T_ref = NAN;
+    p->solved = false;   // no adjoint-ready state after a transient run
+    return rc;
 }
 
 int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep) {
@@ -2004,6 +2343,24 @@ int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep) {
     if (!p->solved || p->solved_iters < 1) return fail(p, BTE_ESTATE, "bte_profile_sweep needs a preceding bte_solve");
     if (p->solved_precision == BTE_FP32) return profile_t<float>(p, reps, ms_per_sweep);
     return profile_t<double>(p, reps, ms_per_sweep);
+}
+
+int bte_debug_set_wait_limit(bte_plan *p, long long polls) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (polls < 0) return fail(p, BTE_EINVAL, "bte_debug_set_wait_limit: polls must be >= 0");
+    p->spin_limit = polls == 0 ? kPipeSpinLimit : polls;
+    // captured graphs hold the old limit in their kernel parameters
+    for (Workspace<float> *w : {&p->ws32}) {
+        if (w->graph) cudaGraphExecDestroy(w->graph);
+        if (w->agraph) cudaGraphExecDestroy(w->agraph);
+        w->graph = w->agraph = nullptr;
+    }
+    for (Workspace<double> *w : {&p->ws64}) {
+        if (w->graph) cudaGraphExecDestroy(w->graph);
+        if (w->agraph) cudaGraphExecDestroy(w->agraph);
+        w->graph = w->agraph = nullptr;
+    }
+    return BTE_OK;
 }
 
 int bte_set_sweep_timing(bte_plan *p, int every) {
@@ -2035,8 +2392,9 @@ int bte_batch_create(int n, bte_plan *const *plans, bte_batch **out) {
         const bte_plan *q = plans[0];
         if (p->B != q->B || p->D != q->D)
             return bfail(nullptr, BTE_EINVAL, "bte_batch_create: every instance needs the same band and direction counts");
-        if (p->dim > 2 || p->n_active != p->N || p->R != 1 || (p->ny + 31) / 32 > 16)
-            return bfail(nullptr, BTE_EINVAL, "bte_batch_create: instances must be unmasked 1D/2D grids with one region");
+        if (p->dim > 2 || p->n_active != p->N || p->R != 1 || (p->ny + 31) / 32 > 16 || p->Fs > 0)
+            return bfail(nullptr, BTE_EINVAL,
+                         "bte_batch_create: instances must be unmasked 1D/2D grids with one region and no specular face");
         for (int j = 0; j < i; ++j)
             if (plans[j] == p) return bfail(nullptr, BTE_EINVAL, "bte_batch_create: a plan appears twice");
     }
@@ -2092,6 +2450,7 @@ int bte_batch_solve(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_s
     if (!o || !T_out) return bfail(bt, BTE_EINVAL, "opts and T_out are required");
     if (o->max_iter < 1) return bfail(bt, BTE_EINVAL, "max_iter must be >= 1");
     if (o->T_init) return bfail(bt, BTE_EINVAL, "bte_batch_solve: use T_init_uniform");
+    if (o->face_order == 2) return bfail(bt, BTE_EINVAL, "bte_batch_solve: step faces only (face_order 0 or 1)");
     if (o->precision == BTE_FP32) return batch_solve_t<float>(bt, o, T_out, st, bs);
     if (o->precision == BTE_FP64) return batch_solve_t<double>(bt, o, T_out, st, bs);
     return bfail(bt, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");

@@ -21,6 +21,20 @@
 //     layer register (layer 0: from the warp group below through shared
 //     memory).  One barrier per step; exchange buffers are double-buffered.
 //
+// Extended variant (EXT): specularly reflecting domain faces and a per-
+// (cell, band, direction) source term.  Specular faces: the inflow through a
+// specular face on the upwind side of cell c along axis a is, per
+// direction d, the previous iterate's value of the mirror direction of d (the
+// axis-a component reversed) in the same cell.  The sweep itself provides it:
+// where a cell's downwind side along a is specular, the cell's value of
+// direction d is stored under mirror_a(d) in the next iterate's specular
+// array.  The adjoint uses the same two rules on mu (the transposed coupling
+// of a specular face is a_d mu_old(mirror d) at the face d leaves by, which is
+// the face the flipped traversal enters by).  The extra source (forward
+// sweeps): xscale * xsrc[c][b][d] is added to the right-hand side of each
+// direction -- e_prev/dt of an implicit-Euler time step, or the deferred
+// correction of second-order faces.
+//
 // The same kernel runs the transposed (adjoint) sweep: the host passes the
 // octant signs flipped, so cells are visited downwind-first and couple to
 // their forward-downwind neighbours; the source is w_d Theta_c / tau_cb and
@@ -40,7 +54,7 @@ struct SweepTile {
     static constexpr int kMaxThreads = (DW * LZ >= 16) ? ((LZ > 1) ? 1024 : 256) : 1024;
 };
 
-template <typename real, int DW, int LZ, bool Z, bool ADJ>
+template <typename real, int DW, int LZ, bool Z, bool ADJ, bool EXT = false>
 __global__ void __launch_bounds__(SweepTile<DW, LZ, Z>::kMaxThreads)
 sweep_kernel(const __grid_constant__ SweepParams<real> P) {
     {
@@ -147,6 +161,15 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
             if (bx) Ex = einb[face_of(ci.x, ci.y, up_x)];
             if (by) Ey = einb[face_of(ci.x, ci.y, up_y)];
             if (Z && bz) Ez = einb[face_of(ci.x, ci.y, up_z)];
+            // specular upwind faces: per-direction inflow rows (-1: none)
+            long long sx_row = -1, sy_row = -1, sz_row = -1;
+            if (EXT && P.sidx) {
+                const long long rb0 = (long long)b * P.Fs;
+                int si;
+                if (bx && (si = P.sidx[face_of(ci.x, ci.y, up_x)]) >= 0) sx_row = (rb0 + si) * D + sub.d0;
+                if (by && (si = P.sidx[face_of(ci.x, ci.y, up_y)]) >= 0) sy_row = (rb0 + si) * D + sub.d0;
+                if (Z && bz && (si = P.sidx[face_of(ci.x, ci.y, up_z)]) >= 0) sz_row = (rb0 + si) * D + sub.d0;
+            }
             real base = real(0);
             real thc = real(0);
             if (act) {
@@ -175,7 +198,15 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
                     vy = by ? Ey : vy;
                     if (Z) vz = bz ? Ez : vz;
                 }
+                if (EXT && P.sidx && dd < sub.cnt) {
+                    // mirror-direction inflow (e, or mu in the adjoint: no w factor)
+                    if (sx_row >= 0) vx = P.spec_in[sx_row + dd];
+                    if (sy_row >= 0) vy = P.spec_in[sy_row + dd];
+                    if (Z && sz_row >= 0) vz = P.spec_in[sz_row + dd];
+                }
                 real r0 = ADJ ? base * w[dd] : base;
+                if (EXT && !ADJ && P.xsrc && act && dd < sub.cnt)
+                    r0 = fma(P.xscale, P.xsrc[(c * B + b) * (long long)D + sub.d0 + dd], r0);
                 r0 = fma(ax[dd], vx, r0);
                 r0 = fma(ay[dd], vy, r0);
                 if (Z) r0 = fma(az[dd], vz, r0);
@@ -214,6 +245,40 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
                     for (int dd = 0; dd < DW; ++dd)
                         if (dd < sub.cnt) g = fma(old[l][dd] - w[dd] * thc, ep[dd] - e0, g);
                     gpart_sb[c] = g;
+                    if (EXT && P.glpart) {
+                        // cell-size derivative: sum_d mu_d a^a_d (e_d - e_in,a,d), the
+                        // forward inflow e_in of axis a coming through the side
+                        // this (flipped) traversal leaves by
+                        for (int a = 0; a < P.dim; ++a) {
+                            const int fside = (a == 0 ? up_x : (a == 1 ? up_y : up_z)) ^ 1;
+                            const bool fb_bnd = (bm >> fside) & 1u;
+                            long long nrow = 0, srow = -1;
+                            real einv = real(0);
+                            if (fb_bnd) {
+                                const int f = face_of(ci.x, ci.y, fside);
+                                const int si = P.sidx ? P.sidx[f] : -1;
+                                if (si >= 0)
+                                    srow = ((long long)b * P.Fs + si) * D + sub.d0;
+                                else
+                                    einv = P.ein_fwd[(long long)b * P.F + f];
+                            } else {
+                                const long long stride =
+                                    a == 0 ? 1LL : (a == 1 ? (long long)P.nx : (long long)P.nx * P.ny);
+                                const long long cn = (fside & 1) ? c + stride : c - stride;
+                                nrow = (cn * B + b) * (long long)D + sub.d0;
+                            }
+                            real gl = real(0);
+#pragma unroll
+                            for (int dd = 0; dd < DW; ++dd) {
+                                if (dd >= sub.cnt) continue;
+                                const real ein_d =
+                                    fb_bnd ? (srow >= 0 ? P.spec_fwd[srow + dd] : einv) : P.e[nrow + dd];
+                                const real cf = a == 0 ? ax[dd] : (a == 1 ? ay[dd] : az[dd]);
+                                gl = fma(old[l][dd] * cf, ep[dd] - ein_d, gl);
+                            }
+                            P.glpart[(((long long)a * B + b) * P.Spad + s) * N + c] = gl;
+                        }
+                    }
                 }
                 // face sums at the boundary sides the traversal leaves by
                 if (bm & ((1u << (up_x ^ 1)) | (1u << (up_y ^ 1)) | (Z ? (1u << (up_z ^ 1)) : 0u))) {
@@ -222,6 +287,17 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
                         const int upa = a == 0 ? up_x : (a == 1 ? up_y : up_z);
                         const int dn = upa ^ 1;
                         if (!((bm >> dn) & 1u)) continue;
+                        if (EXT && P.sidx) {
+                            const int si = P.sidx[face_of(ci.x, ci.y, dn)];
+                            if (si >= 0) {
+                                // this cell's outgoing values, stored under the mirror directions
+                                real *so = P.spec_out + ((long long)b * P.Fs + si) * D;
+#pragma unroll
+                                for (int dd = 0; dd < DW; ++dd)
+                                    if (dd < sub.cnt) so[P.mirror[a * D + sub.d0 + dd]] = old[l][dd];
+                                continue;
+                            }
+                        }
                         real fs = real(0);
 #pragma unroll
                         for (int dd = 0; dd < DW; ++dd) {
@@ -259,13 +335,14 @@ size_t sweep_smem_bytes(int R, int nwarps, int F, int ein_smem) {
     return n * sizeof(real);
 }
 
-template <typename real, int DW, int LZ, bool Z, bool ADJ>
+template <typename real, int DW, int LZ, bool Z, bool ADJ, bool EXT = false>
 cudaError_t launch_sweep_t(const SweepParams<real> &p, cudaStream_t st) {
     const int nwarps = p.WY * p.WZ;
     const int threads = nwarps * 32;
     if (threads > SweepTile<DW, LZ, Z>::kMaxThreads) return cudaErrorInvalidConfiguration;
+    if (!EXT && (p.sidx != nullptr || p.xsrc != nullptr || p.glpart != nullptr)) return cudaErrorInvalidConfiguration;
     const size_t smem = sweep_smem_bytes<real, DW, LZ, Z>(p.R, nwarps, p.F, p.ein_smem);
-    auto kern = sweep_kernel<real, DW, LZ, Z, ADJ>;
+    auto kern = sweep_kernel<real, DW, LZ, Z, ADJ, EXT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

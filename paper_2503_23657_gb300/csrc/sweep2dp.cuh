@@ -49,12 +49,13 @@
 
 namespace bte {
 
-constexpr long long kPipeSpinLimit = 1LL << 20;  // polls (with a short sleep) before giving up
-
-// Wait until *prog >= need.  False if the CTA has aborted or the wait ran out
-// (the caller then records the failure and carries on without waiting).
-__device__ __forceinline__ bool pipe_wait(const int *prog, int need, volatile int *abort_flag) {
-    for (long long it = 0; it < kPipeSpinLimit; ++it) {
+// Wait until *prog >= need, at most `limit` polls (with a short sleep; the
+// plan's limit, kPipeSpinLimit by default).  False if the CTA has aborted or
+// the wait ran out (the caller then records the failure and carries on
+// without waiting: the values it reads are then wrong, every access stays in
+// bounds, and the solve reports BTE_ETIMEOUT).
+__device__ __forceinline__ bool pipe_wait(const int *prog, int need, volatile int *abort_flag, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         if (ld_acquire_cta(prog) >= need) return true;
         if (*abort_flag) return false;
         __nanosleep(32);
@@ -247,7 +248,7 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
         }
         if (waited_ok) {
             // columns [t0, t0 + K) of row 32 R - 1 (row -1: the wall) must be final
-            waited_ok = pipe_wait(prog_in, min(t0 + K, nx), &s_abort);
+            waited_ok = pipe_wait(prog_in, min(t0 + K, nx), &s_abort, P.spin_limit);
             if (!waited_ok) {
                 s_abort = 1;
                 if (lane == 0) atomicExch(P.status, 2);

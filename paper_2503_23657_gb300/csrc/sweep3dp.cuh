@@ -61,6 +61,7 @@ constexpr int kP3RY = 4 * kPipe3Chunk;  // y-ring depth
 
 __host__ __device__ constexpr int p3_round4(int n) { return (n + 3) & ~3; }
 
+
 // DW consecutive values (16-byte aligned groups of 4, 8-byte aligned pairs)
 // to and from registers; CG = through L2 only (data written in this launch)
 template <bool CG>
@@ -266,22 +267,29 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     real *const fs_sb = P.fsum + ((long long)s * P.B + b) * P.F;
     real *const wrap_c = (M > 1) ? P.wrap + ((long long)s * P.B + b) * (long long)nx * ld_wrap * DW : nullptr;
     real *const tile = sm + L.tile + warp * 32 * 33;
-    real *const zr_out = sm + L.zr + warp * RZ * 32 * DW;
-    const real *const zr_in = sm + L.zr + (warp - WY) * RZ * 32 * DW;   // h > 0
+    real *const tile_l = tile + lane * 33;
+    // z rings: slot (local step mod RZ) of this lane; the writer (warp below
+    // in z) and the reader handle a given column at the same local step
+    real *const zr_out = sm + L.zr + warp * RZ * 32 * DW + lane * DW;
+    const real *const zr_in = sm + L.zr + (warp - WY) * RZ * 32 * DW + lane * DW;   // h > 0
     real *const yr_out = sm + L.yr + warp * RY * DW;
     const real *const yr_in = sm + L.yr + (warp - 1) * RY * DW;         // wy > 0
 
     // record slots (local step mod 4) and data slots (local step mod 2)
     int rs[4], rc[STORE_E ? 4 : 1], rx[4], ry[4], riw[4];
     real dt[2], dp[2], dex[2], dey[2], dez[2], dwz[2][DW];
-    // tracker of the record read next (local step tau + 4): column ui of
-    // pass um and its skewed index (valid once ui >= 0)
-    int ui = -lane, um = 0;
+    // tracker of the record read next (local step tau + 4): its virtual
+    // column uf (= ui + nx um, column ui of pass um), the steps cnt until it
+    // leaves the current pass, and its skewed index (valid once uf >= 0)
+    int uf = -lane, cnt = nx + lane, um = 0;
     int sk_t = sk0 - lane * dsk;
+    const unsigned Uh = (unsigned)(Mh * nx);        // columns whose plane lies in the grid
+    const unsigned Uw = (unsigned)((M - 1) * nx);   // columns of passes that have a next pass
     auto fetch_record = [&](int q) {
-        const bool v = rowv && ui >= 0 && um < Mh;
+        const bool v = rowv && (unsigned)uf < Uh;
         const int sk = v ? sk_t : sk_pad;
         rs[q] = sk;
+        const int ui = nx - cnt;
         if (STORE_E) {
             const int X = negx ? nx - 1 - ui : ui;
             const int k = h + H * um;
@@ -290,14 +298,17 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         }
         // wrap buffer column: read by the first warp of a pass (the value is
         // used only past the first pass), written by the last one
-        riw[q] = wrap_wr ? ((v && um + 1 < M) ? ui : -1) : max(ui, 0);
+        if (wrap_wr)
+            riw[q] = (v && (unsigned)uf < Uw) ? ui : -1;
+        else if (wrap_rd)
+            riw[q] = max(ui, 0);
         const int2 ci = __ldg(P.cell + sk);
         rx[q] = ci.x;
         ry[q] = ci.y;
-        ++ui;
+        ++uf;
         sk_t += dsk;
-        if (ui == nx) {
-            ui = 0;
+        if (--cnt == 0) {
+            cnt = nx;
             ++um;
             sk_t += dsk_pass - dsk;
         }
@@ -368,7 +379,8 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 if (PHI) base += phv * qb;
                 real invd[DW], yin[DW];
                 p3_load<DW>(s_invd + r * DW, invd);
-                if (h > 0) p3_load<DW>(zr_in + ((u & (RZ - 1)) * 32 + lane) * DW, zin);
+                const int zslot = (tau & (RZ - 1)) * 32 * DW;
+                if (h > 0) p3_load<DW>(zr_in + zslot, zin);
                 if (wy > 0) {
                     p3_load<DW>(yr_in + (tau & (RY - 1)) * DW, yin);  // lane 0: u == tau
                 } else {
@@ -393,20 +405,25 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                     old[dd] = en;
                     acc = fma(w[dd], en, acc);
                 }
-                tile[lane * 33 + (tau & 31)] = acc;
-                if (feed_z) p3_store<DW>(zr_out + ((u & (RZ - 1)) * 32 + lane) * DW, old);
-                if (feed_y && lane == 31) p3_store<DW>(yr_out + (u & (RY - 1)) * DW, old);
+                tile_l[tau & 31] = acc;
+                if (feed_z) p3_store<DW>(zr_out + zslot, old);
+                if (feed_y && lane == 31) p3_store<DW>(yr_out + ((tau - 31) & (RY - 1)) * DW, old);
                 if (wrap_wr && iw >= 0) p3_store<DW>(wrap_c + ((long long)iw * ld_wrap + j) * DW, old);
                 // face sums at the boundary sides the traversal leaves by
-                if (act && (bm & dn_mask)) {
+                // (not at isothermal domain faces: the iterations never read
+                // them there)
+                const unsigned fsm = bm & dn_mask & ~(((unsigned)fl >> kIsoShift) & 63u);
+                if (act && fsm) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int dn = (a == 0 ? up_x : (a == 1 ? up_1 : up_2)) ^ 1;
                         const int pa = a == 0 ? 0 : (a == 1 ? a1 : a2);   // physical axis
-                        if (!((bm >> dn) & 1u)) continue;
+                        if (!((fsm >> dn) & 1u)) continue;
+                        real fw[DW];
+                        p3_load<DW>(s_fw + pa * DW, fw);
                         real fs = real(0);
 #pragma unroll
-                        for (int dd = 0; dd < DW; ++dd) fs = fma(s_fw[pa * DW + dd], old[dd], fs);
+                        for (int dd = 0; dd < DW; ++dd) fs = fma(fw[dd], old[dd], fs);
                         fs_sb[face_of(fb, fl, dn)] = fs;
                     }
                 }

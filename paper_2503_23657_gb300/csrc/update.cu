@@ -88,7 +88,11 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
             const int side = P.face_side[f];
             const int a = side >> 1;
             const bool plus = side & 1;
-            if (P.face_kind[f] == 0 && !P.adjoint) {
+            if (P.face_kind[f] == 2) {
+                // specular faces: the sweeps carry their per-direction inflow
+                P.ein_out[fb] = (real)0;
+                if (P.fsum_total) P.fsum_total[fb] = 0.0;
+            } else if (P.face_kind[f] == 0 && !P.adjoint) {
                 P.ein_out[fb] = P.ein_fixed[fb];
             } else {
                 // sets leaving the cell through this face: those running
@@ -216,7 +220,7 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
         if (!P.ignore_done) {
             *P.iter = it + 1;
             const bool stop_now = !isfinite(eps) || (P.tol > 0.0 && eps < P.tol);
-            if (!isfinite(eps)) *P.status = 1;
+            if (!isfinite(eps)) atomicCAS(P.status, 0, 1);   // keeps an expired-wait status (2)
             if (stop_now) {
                 *P.done = 1;
                 if (P.batch_done) atomicAdd(P.batch_done, 1);
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
                                                             int cell_blocks) {
     __shared__ double sh[kGradThreads / 32];
     __shared__ int is_last;
-    const int NO = G.B + 7;
+    const int NO = G.B + 10;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool is_cell = (int)blockIdx.x < cell_blocks;
     const long long fi = (long long)(blockIdx.x - cell_blocks) * blockDim.x + threadIdx.x;
@@ -391,6 +395,16 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
         }
         v = block_sum(v, sh);
         if (threadIdx.x == 0) G.blockpart[(long long)blockIdx.x * NO + G.B + f6] = v;
+    }
+    for (int a = 0; a < 3; ++a) {
+        double v = 0.0;
+        if (G.glpart && is_cell && r != 0) {
+            for (int b = 0; b < G.B; ++b)
+                for (int s = 0; s < G.S; ++s)
+                    v += (double)G.glpart[(((long long)a * G.B + b) * G.Spad + s) * G.N + i];
+        }
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) G.blockpart[(long long)blockIdx.x * NO + G.B + 7 + a] = v;
     }
     gq = block_sum(gq, sh);
     if (threadIdx.x == 0) {

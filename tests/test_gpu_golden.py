@@ -1,0 +1,96 @@
+"""GPU parity at the workloads' full sizes against results the FP64 oracle
+wrote to tests/golden/ (by tests/golden/make_goldens.py, which imports only
+the oracle and the input generators):
+
+* T after exactly 20 source iterations from T = 300 K of the full 64^3
+  hotspot (15 bands x 128 directions) and of the full 160x80x64 FinFET;
+* the half-resolution FinFET (80x40x32, all 15 bands x 128 directions)
+  converged to eps_T < 1e-8 -- its iteration count and T -- and the
+  discrete-adjoint gradients of the probe misfit w.r.t. tau_b, the
+  substrate temperature and the source amplitude.
+
+Tolerances: FP64 1e-12 relative on T, FP32 1e-5; gradients with FP64 sweeps
+1e-7 relative to the oracle's (both adjoints stopped on the same relative
+change of Theta, 1e-10), with FP32 sweeps 1e-3."""
+import os
+
+import numpy as np
+import pytest
+
+import bte_inputs as bi
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def bte():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_23657_gb300 as m
+    m.load()
+    return m
+
+
+def golden(name):
+    path = os.path.join(HERE, name)
+    if not os.path.exists(path):
+        pytest.fail(f"missing golden file {name}: run tests/golden/make_goldens.py")
+    return np.load(path)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hotspot_full_size_k20(bte, prec):
+    g = golden("hotspot64_k20.npz")
+    p = bi.hotspot_3d()
+    plan = bte.Plan(p)
+    T = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+    rc, st = plan.solve(T, precision=bte.BTE_FP64 if prec == "fp64" else bte.BTE_FP32, tol=0.0, max_iter=20)
+    T = T.cpu().numpy()
+    assert int(g["iters"]) == 20 and st["iterations"] == 20
+    err = np.abs(T - g["T"]).max() / np.abs(g["T"]).max()
+    assert err < (1e-12 if prec == "fp64" else 1e-5), err
+    # the iterate has moved off the initial state (the source and walls act)
+    assert np.ptp(g["T"]) > 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_finfet_full_size_k20(bte, prec):
+    g = golden("finfet_k20.npz")
+    p = bi.finfet_3d()
+    plan = bte.Plan(p)
+    T = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+    rc, st = plan.solve(T, precision=bte.BTE_FP64 if prec == "fp64" else bte.BTE_FP32, tol=0.0, max_iter=20)
+    T = T.cpu().numpy()[g["cells"]]
+    err = np.abs(T - g["T"]).max() / np.abs(g["T"]).max()
+    assert err < (1e-12 if prec == "fp64" else 1e-5), err
+    assert np.ptp(g["T"]) > 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_finfet_half_resolution_converged_adjoint(bte, prec):
+    g = golden("finfet_s2_adjoint.npz")
+    p = bi.finfet_3d(scale=2)
+    plan = bte.Plan(p)
+    fp64 = prec == "fp64"
+    T = np.zeros(p.n_cells)
+    # the same number of iterations as the oracle needed for eps_T < 1e-8
+    rc, st = plan.solve(T, precision=bte.BTE_FP64 if fp64 else bte.BTE_FP32, tol=0.0, max_iter=int(g["iters"]))
+    act = p.mask > 0
+    err = np.abs(T - g["T"])[act].max() / np.abs(g["T"][act]).max()
+    assert err < (1e-12 if fp64 else 1e-5), err
+    if fp64:
+        # and the solve to the tolerance stops at the same iteration
+        T2 = np.zeros(p.n_cells)
+        rc, st2 = plan.solve(T2, precision=bte.BTE_FP64, tol=1e-8, max_iter=100000)
+        assert st2["iterations"] == int(g["iters"])
+        T = T2
+    probes = g["probes"]
+    gv = np.zeros(p.n_cells)
+    np.add.at(gv, probes, T[probes] - g["T_obs"])
+    rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(gv, tol=1e-10, max_iter=100000)
+    tol = 1e-7 if fp64 else 1e-3
+    np.testing.assert_allclose(g_tau, g["g_tau"], rtol=tol, atol=tol * np.abs(g["g_tau"]).max())
+    assert g_Tw[4] == pytest.approx(float(g["g_Tw"][4]), rel=tol)
+    assert g_Q == pytest.approx(float(g["g_Q"]), rel=tol)

@@ -212,15 +212,6 @@ def test_row_kernels_rejected_for_masked_grid(bte, kind):
     assert rc == -1
 
 
-def test_specular_faces_refused(bte):
-    """The oracle already has specularly reflecting faces; the library refuses
-    the type (EINVAL) instead of treating it as another kind of face."""
-    p = bi.tiny(2, n=(5, 4, 1), B=2, specular=(2,))
-    with pytest.raises(bte.BTEError) as err:
-        bte.Plan(p)
-    assert err.value.code == -1
-
-
 def test_store_every_iteration_same_result(bte):
     p = bi.tiny(3, n=(5, 4, 4), B=2, diffuse=(3,), source=True)
     plan = bte.Plan(p)
