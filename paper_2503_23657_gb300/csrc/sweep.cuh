@@ -240,10 +240,34 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
                 if (ADJ && P.read_e) {
                     // (mu - w Theta)(e - e0) with e0 = C_b (T - T_ref)/(4 pi)
                     const real e0 = cb4pi * P.tfwd[c];
+                    real ev[DW];
+                    if (vec_ok) {
+                        // DW consecutive values of e, aligned: vector loads
+#pragma unroll
+                        for (int q = 0; q < DW; q += 4) {
+                            if constexpr (sizeof(real) == 4) {
+                                const float4 x = *reinterpret_cast<const float4 *>(ep + q);
+                                ev[q] = x.x;
+                                ev[q + 1] = x.y;
+                                ev[q + 2] = x.z;
+                                ev[q + 3] = x.w;
+                            } else {
+                                const double2 x = *reinterpret_cast<const double2 *>(ep + q);
+                                const double2 y = *reinterpret_cast<const double2 *>(ep + q + 2);
+                                ev[q] = x.x;
+                                ev[q + 1] = x.y;
+                                ev[q + 2] = y.x;
+                                ev[q + 3] = y.y;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int dd = 0; dd < DW; ++dd) ev[dd] = dd < sub.cnt ? ep[dd] : real(0);
+                    }
                     real g = real(0);
 #pragma unroll
                     for (int dd = 0; dd < DW; ++dd)
-                        if (dd < sub.cnt) g = fma(old[l][dd] - w[dd] * thc, ep[dd] - e0, g);
+                        if (dd < sub.cnt) g = fma(old[l][dd] - w[dd] * thc, ev[dd] - e0, g);
                     gpart_sb[c] = g;
                     if (EXT && P.glpart) {
                         // cell-size derivative: sum_d mu_d a^a_d (e_d - e_in,a,d), the
@@ -274,7 +298,7 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
                                 const real ein_d =
                                     fb_bnd ? (srow >= 0 ? P.spec_fwd[srow + dd] : einv) : P.e[nrow + dd];
                                 const real cf = a == 0 ? ax[dd] : (a == 1 ? ay[dd] : az[dd]);
-                                gl = fma(old[l][dd] * cf, ep[dd] - ein_d, gl);
+                                gl = fma(old[l][dd] * cf, ev[dd] - ein_d, gl);
                             }
                             P.glpart[(((long long)a * B + b) * P.Spad + s) * N + c] = gl;
                         }

@@ -184,6 +184,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const Subset sub = P.sub[s];
     const int d0 = sub.d0;
     const int ndir = min(DW, sub.cnt);
+    // a full subset at an aligned offset is written with vector stores (the
+    // element count of one vector store of p3_store must divide D and d0)
+    constexpr int kVA = sizeof(real) == 4 ? (DW >= 4 ? 4 : DW) : (DW >= 2 ? 2 : 1);
+    const bool vec_e = ndir == DW && (P.D % kVA) == 0 && (d0 % kVA) == 0;
     const bool adj = P.adj != 0;
     for (int q = threadIdx.x; q < R * DW; q += blockDim.x) {
         const int r = q / DW, dd = q - r * DW;
@@ -429,9 +433,16 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 }
                 if (STORE_E && act && c >= 0) {
                     real *ep = P.e + ((long long)c * P.B + b) * P.D + d0;
+                    real ev[DW];
 #pragma unroll
-                    for (int dd = 0; dd < DW; ++dd)
-                        if (dd < ndir) ep[dd] = adj ? old[dd] * w[dd] : old[dd];
+                    for (int dd = 0; dd < DW; ++dd) ev[dd] = adj ? old[dd] * w[dd] : old[dd];
+                    if (vec_e) {
+                        p3_store<DW>(ep, ev);   // DW consecutive values, aligned: vector stores
+                    } else {
+#pragma unroll
+                        for (int dd = 0; dd < DW; ++dd)
+                            if (dd < ndir) ep[dd] = ev[dd];
+                    }
                 }
             }
             {
