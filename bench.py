@@ -124,6 +124,11 @@ class ClockSampler:
 # otherwise a capture with fewer bands, scaled to all bands (traffic grows in
 # proportion to the bands: every band is an independent set of CTAs).
 NCU_TRAFFIC = {
+    # FinFET 160x80x64, 15 bands, forward launch, full size (one-pass capture):
+    # 457.6 MB read + 1293.7 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 1>", "3:8:8:2:8:2", "aab7c325aea6"): 1751316224,
+    # 64^3 hotspot, 15 bands, forward launch, full size: 66.6 MB read + 251.5 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4:1", "aab7c325aea6"): 318085888,
 }
 KERNEL_SOURCES = {
     "sweep3dp_kernel": ["sweep3dp.cuh", "bte_internal.cuh", "finalize.cuh", "tma.cuh"],
