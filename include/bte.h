@@ -165,6 +165,10 @@ typedef struct {
                                a neighbour; outgoing boundary values are reconstructed, also in the
                                reflections.  face_order 2 runs the general kernel, stores e every
                                iteration and needs 4 N B D extra values of device memory */
+    const double *Q_amp_each; /* bte_batch_solve only: n source amplitudes (host), one per instance
+                               in plan order, each multiplying its own plan's q_profile; NULL =
+                               Q_amp for every instance.  Must be NULL for bte_solve and
+                               bte_transient (BTE_EINVAL otherwise) */
 } bte_solve_opts;
 
 typedef struct {
@@ -291,24 +295,30 @@ int bte_set_sweep_timing(bte_plan *p, int every);
 
 /*
  * Batched solves (the paper has none; many independent 2D problems on one
- * GPU).  A batch borrows N plans made by bte_create -- unmasked 1D/2D grids
- * with one region, all with the same band and direction counts, any sizes --
- * and solves all of them together: every outer iteration is one graph node
- * per size class (instances grouped by their number of 32-row blocks; the
- * classes run concurrently) plus one update launch over every instance, and
- * the iterations are replayed from a captured CUDA graph.  Each instance
- * keeps its own convergence test (eps_T < tol) and stops iterating when it
- * converges; the solve ends when all have converged or after max_iter.
- * Results are those of bte_solve on each plan with the same tile.
+ * GPU).  A batch borrows N plans made by bte_create -- 1D/2D grids of at most
+ * 1024 rows (y cells) without specular faces, all with the same band and
+ * direction counts, any sizes, masks and region counts -- and solves all of
+ * them together: every outer iteration is one sweep launch per size class
+ * plus one update launch over every instance, and the iterations are
+ * replayed from a captured CUDA graph.  A size class holds the instances
+ * with the same kernel and number of 32-row blocks: unmasked single-region
+ * instances of at most 512 rows run the row-pipeline kernel, the others
+ * (masks, several regions, more rows) the general wavefront kernel; the
+ * classes run concurrently.  Each instance keeps its own convergence test
+ * (eps_T < tol) and stops iterating when it converges; the solve ends when
+ * all have converged or after max_iter.  Results are those of bte_solve on
+ * each plan with the same tile.
  *
  * bte_batch_create -- n >= 1 distinct plans (the batch keeps the pointers;
  *   destroy the batch before the plans).  BTE_EINVAL for null or mismatched
  *   plans, BTE_ECUDA if device state cannot be allocated; the message is
  *   read with bte_batch_last_error(NULL).
- * bte_batch_solve -- o: as for bte_solve, except that T_init must be NULL
+ * bte_batch_solve -- o: as for bte_solve, except that T_init must be NULL,
+ *   Q_amp_each may give each instance its own source amplitude
  *   (T_init_uniform applies to all), T_wall must be NULL (each plan's walls
- *   apply), and tile_kind is 0 or 3 (the row-pipeline kernel; the tile is
- *   autotuned per size class unless dirs_per_lane / dirs_per_cta pin it).
+ *   apply), and tile_kind is 0 or 3 (the batch picks each class's kernel;
+ *   the tile is autotuned per size class unless dirs_per_lane /
+ *   dirs_per_cta pin it).
  *   T_out: sum of the instances' cell counts doubles (host or device), the
  *   instances' temperatures concatenated in plan order.  st: n entries or
  *   NULL.  bs: batch totals or NULL.  Returns BTE_OK, BTE_EINVAL,

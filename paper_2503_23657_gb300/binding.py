@@ -63,7 +63,8 @@ class SolveOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("poll_every", ctypes.c_int),
                 ("dirs_per_lane", ctypes.c_int), ("store_e_every_iter", ctypes.c_int),
                 ("tile_kind", ctypes.c_int), ("dirs_per_cta", ctypes.c_int), ("source_staging", ctypes.c_int),
-                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int), ("face_order", ctypes.c_int)]
+                ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int), ("face_order", ctypes.c_int),
+                ("Q_amp_each", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -384,18 +385,30 @@ class Batch:
         if rc != BTE_OK:
             raise BTEError(rc, self.error())
 
-    def solve(self, T_out, precision=BTE_FP32, tol=1e-6, max_iter=100000, T_init_uniform=300.0, Q_amp=0.0,
+    def solve(self, T_out, precision=BTE_FP32, tol=1e-6, max_iter=100000, T_init_uniform=300.0, Q_amp=None,
               tau=None, stream=None, poll_every=32, dirs_per_lane=0, dirs_per_cta=0, check=True):
         """Run bte_batch_solve.  T_out holds sum(n_cells) doubles (numpy or
-        torch, host or CUDA), instances concatenated in plan order.  Returns
-        (rc, [per-instance stats], batch stats)."""
+        torch, host or CUDA), instances concatenated in plan order.  Q_amp:
+        None = each instance's own problem's amplitude, a number = that one
+        for all, a sequence = one per instance.  Returns (rc, [per-instance
+        stats], batch stats)."""
         o = SolveOpts()
         self._lib.bte_default_opts(ctypes.byref(o))
         o.precision = precision
         o.tol = tol
         o.max_iter = max_iter
         o.T_init_uniform = T_init_uniform
-        o.Q_amp = Q_amp
+        if Q_amp is None:
+            Q_amp = [pl.problem.Q_amp for pl in self.plans]
+        q_a = None
+        if np.ndim(Q_amp) == 0:
+            o.Q_amp = float(Q_amp)
+        else:
+            q_a = np.ascontiguousarray(Q_amp, dtype=np.float64)
+            if q_a.shape != (len(self.plans),):
+                raise ValueError("Q_amp: one amplitude per instance")
+            o.Q_amp = 0.0
+            o.Q_amp_each = _addr(q_a)
         tau_a = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
         o.tau = _addr(tau_a)
         o.stream = stream

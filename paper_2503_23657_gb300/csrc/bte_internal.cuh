@@ -297,6 +297,17 @@ cudaError_t launch_sweep(const SweepParams<real> &p, int dirs_per_lane, int laye
 
 // Largest CTA (threads) the sweep tile supports, or 0 if not instantiated.
 int sweep_max_threads(int dirs_per_lane, int layers_per_lane, bool three_d);
+
+// A batched launch of the general kernel over the instances of one class of
+// 2D problems (same warps along y): grid chunks x B x instances.
+template <typename real>
+struct SweepBatch {
+    const SweepParams<real> *params;  // device [all instances]
+    const int *inst;                  // device [n_inst] instance indices of this class
+    int n_inst, chunks, B, WY, R_max;
+};
+template <typename real>
+cudaError_t launch_sweep_batch(const SweepBatch<real> &bt, int dirs_per_lane, cudaStream_t st);
 // Directions per lane of the general kernel's extended variant (specular
 // faces, extra source, cell-size gradient partials).
 constexpr int kSpecDW = 4;

@@ -181,6 +181,7 @@ namespace {
 template <typename real>
 struct BatchState {
     DevBuf sweep[2], update[2];  // Sweep2DParams<real>[n], UpdateParams<real>[n] per parity
+    DevBuf gsweep[2];            // SweepParams<real>[n] per parity (general-kernel classes)
     cudaGraphExec_t graph = nullptr;
     std::vector<int> graph_key;
     std::map<std::vector<int>, std::vector<int>> tuned;  // tile request -> tile per class
@@ -196,8 +197,10 @@ struct bte_batch {
     int n = 0;
     struct Cls {
         int nrb, begin, count, nx_max, ny_max;
+        int general;                // 0: row-pipeline kernel; 1: general kernel (masks, regions)
+        int R_max;
     };
-    std::vector<Cls> classes;       // instances with the same 32-row block count
+    std::vector<Cls> classes;       // instances with the same 32-row block count and kernel
     std::vector<int> inst;          // instance indices, class by class, largest first
     DevBuf d_inst, d_table, d_status, d_done;
     int upd_blocks = 0;
@@ -1873,6 +1876,15 @@ BatchState<double> &bstate_of<double>(bte_batch *bt) { return bt->bs64; }
 // instance needs the most shared memory).
 std::vector<int> batch_class_candidates(bte_batch *bt, const bte_batch::Cls &c, int real_bytes, int dw_req,
                                         int cw_req) {
+    if (c.general) {
+        // the general kernel, 4 or 8 directions per lane
+        std::vector<int> out;
+        for (int dw : {4, 8}) {
+            if (dw_req && dw != dw_req) continue;
+            if (sweep_max_threads(dw, 1, false) >= c.nrb * 32) out.push_back(tile_id(0, dw, dw));
+        }
+        return out;
+    }
     std::vector<int> all = tile_candidates(bt->plans[bt->inst[c.begin]], real_bytes, 3, dw_req, cw_req);
     if (dw_req) return all;
     // one direction per warp is never the fastest with this much parallelism
@@ -1905,10 +1917,34 @@ Sweep2DBatch<real> batch_launch_desc(bte_batch *bt, BatchState<real> &bs, const 
     return d;
 }
 
+template <typename real>
+SweepBatch<real> gbatch_launch_desc(bte_batch *bt, BatchState<real> &bs, const bte_batch::Cls &c, int tid, int parity) {
+    SweepBatch<real> d{};
+    d.params = bs.gsweep[parity].template as<SweepParams<real>>();
+    d.inst = bt->d_inst.as<int>() + c.begin;
+    d.n_inst = c.count;
+    d.chunks = (int)ws_of<real>(bt->plans[bt->inst[c.begin]]).subsets.at(tid).first.size();
+    for (int q = 1; q < c.count; ++q)
+        d.chunks = std::max(d.chunks, (int)ws_of<real>(bt->plans[bt->inst[c.begin + q]]).subsets.at(tid).first.size());
+    d.B = bt->plans[bt->inst[c.begin]]->B;
+    d.WY = c.nrb;
+    d.R_max = c.R_max;
+    return d;
+}
+
+// one class's sweep launch
+template <typename real>
+cudaError_t batch_class_sweep(bte_batch *bt, BatchState<real> &bs, const bte_batch::Cls &c, int tid, int parity,
+                              cudaStream_t s) {
+    if (c.general) return launch_sweep_batch<real>(gbatch_launch_desc(bt, bs, c, tid, parity), tile_of(tid).dw, s);
+    return launch_sweep2dp_batch<real>(batch_launch_desc(bt, bs, c, tid, parity), tile_of(tid).dw, s);
+}
+
 // Per-instance launch parameters of every class's tile, both parities.
 template <typename real>
 int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<int> &tiles, double tol) {
     std::vector<Sweep2DParams<real>> sw((size_t)bt->n);
+    std::vector<SweepParams<real>> gsw((size_t)bt->n);
     std::vector<UpdateParams<real>> up((size_t)bt->n);
     Status *st_all = bt->d_status.as<Status>();
     for (int par = 0; par < 2; ++par) {
@@ -1920,6 +1956,16 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 Workspace<real> &ws = ws_of<real>(p);
                 const int tid = tiles[c];
                 if (int rc = ensure_subsets(p, ws, tid)) return bfail(bt, rc, p->err);
+                if (cl.general) {
+                    SweepParams<real> gp = sweep_params(p, ws, tid, false);
+                    gp.tsrc = ws.tdev[par].template as<real>();
+                    gp.ein = ws.ein[par].template as<real>();
+                    gp.ein_smem = 0;
+                    gp.store_e = 0;
+                    gp.e = nullptr;
+                    gp.done = &st_all[i].done;
+                    gsw[i] = gp;
+                }
                 Sweep2DParams<real> sp = sweep2d_params(p, ws, tid, false);
                 sp.tsrc = ws.tdev[par].template as<real>();
                 sp.ein = ws.ein[par].template as<real>();
@@ -1947,13 +1993,17 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 u.last = st_all[i].last;
                 u.batch_done = bt->d_done.as<int>();
                 u.fin = sp.fin;
-                u.defer = 1;
+                // row-pipeline sweeps finalize in their prologue; the general
+                // kernel's instances finalize in the update itself
+                u.defer = cl.general ? 0 : 1;
                 up[i] = u;
             }
         }
         BCK(bt, bs.sweep[par].ensure(sizeof(Sweep2DParams<real>) * bt->n));
+        BCK(bt, bs.gsweep[par].ensure(sizeof(SweepParams<real>) * bt->n));
         BCK(bt, bs.update[par].ensure(sizeof(UpdateParams<real>) * bt->n));
         BCK(bt, cudaMemcpy(bs.sweep[par].p, sw.data(), sizeof(Sweep2DParams<real>) * bt->n, cudaMemcpyHostToDevice));
+        BCK(bt, cudaMemcpy(bs.gsweep[par].p, gsw.data(), sizeof(SweepParams<real>) * bt->n, cudaMemcpyHostToDevice));
         BCK(bt, cudaMemcpy(bs.update[par].p, up.data(), sizeof(UpdateParams<real>) * bt->n, cudaMemcpyHostToDevice));
     }
     return BTE_OK;
@@ -1969,9 +2019,7 @@ cudaError_t batch_enqueue(bte_batch *bt, BatchState<real> &bs, const std::vector
     for (size_t c = 0; c < bt->classes.size() && e == cudaSuccess; ++c) {
         cudaStream_t s = bt->side[c];
         e = cudaStreamWaitEvent(s, bt->fork, 0);
-        if (e == cudaSuccess)
-            e = launch_sweep2dp_batch<real>(batch_launch_desc(bt, bs, bt->classes[c], tiles[c], parity),
-                                           tile_of(tiles[c]).dw, s);
+        if (e == cudaSuccess) e = batch_class_sweep<real>(bt, bs, bt->classes[c], tiles[c], parity, s);
         if (e == cudaSuccess) e = cudaEventRecord(bt->join[c], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, bt->join[c], 0);
     }
@@ -1987,7 +2035,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
     BatchState<real> &bs = bstate_of<real>(bt);
     if (o->T_wall) return bfail(bt, BTE_EINVAL, "bte_batch_solve: wall temperatures come from each instance's plan");
     if (o->tile_kind != 0 && o->tile_kind != 3)
-        return bfail(bt, BTE_EINVAL, "bte_batch_solve: batched solves use the row-pipeline kernel (tile_kind 0 or 3)");
+        return bfail(bt, BTE_EINVAL, "bte_batch_solve: the batch picks its kernels (tile_kind 0 or 3)");
     // per-instance state
     for (int i = 0; i < bt->n; ++i) {
         bte_plan *p = bt->plans[i];
@@ -2000,7 +2048,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
             p->cur_tau.assign(o->tau, o->tau + p->B);
         }
         p->cur_Tw.assign(p->bc_T, p->bc_T + 6);
-        p->cur_Q = o->Q_amp;
+        p->cur_Q = o->Q_amp_each ? o->Q_amp_each[i] : o->Q_amp;
         if (int rc = begin_state(p, o, ws, stream)) return bfail(bt, rc, p->err);
         if (int rc = upload_tables(p, ws)) return bfail(bt, rc, p->err);
         p->solved = false;  // a batch solve leaves no adjoint-ready state in the plans
@@ -2017,7 +2065,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
         for (size_t c = 0; c < bt->classes.size(); ++c) {
             std::vector<int> cand = batch_class_candidates(bt, bt->classes[c], (int)sizeof(real), o->dirs_per_lane,
                                                            o->dirs_per_cta);
-            if (cand.empty()) return bfail(bt, BTE_EINVAL, "no row-pipeline tile fits a size class of the batch");
+            if (cand.empty()) return bfail(bt, BTE_EINVAL, "no sweep tile fits a size class of the batch");
             tiles.push_back(cand[0]);
         }
         for (size_t c = 0; c < bt->classes.size(); ++c) {
@@ -2032,8 +2080,7 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
                 float tmin = 1e30f;
                 for (int rep = 0; rep < 4; ++rep) {
                     cudaEventRecord(bt->ev0, stream);
-                    cudaError_t e = launch_sweep2dp_batch<real>(batch_launch_desc(bt, bs, bt->classes[c], tid, 0),
-                                                                tile_of(tid).dw, stream);
+                    cudaError_t e = batch_class_sweep<real>(bt, bs, bt->classes[c], tid, 0, stream);
                     cudaEventRecord(bt->ev1, stream);
                     cudaEventSynchronize(bt->ev1);
                     float ms = 0.f;
@@ -2161,13 +2208,16 @@ int batch_solve_t(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_sta
             s.T_max = hs[i].last[1];
             s.seconds = ms * 1e-3;
             const int ci = [&] {
-                for (size_t c = 0; c < bt->classes.size(); ++c)
-                    if (p->ny <= 32 * bt->classes[c].nrb && p->ny > 32 * (bt->classes[c].nrb - 1)) return (int)c;
+                for (size_t c = 0; c < bt->classes.size(); ++c) {
+                    const bte_batch::Cls &cl = bt->classes[c];
+                    for (int q = 0; q < cl.count; ++q)
+                        if (bt->inst[cl.begin + q] == i) return (int)c;
+                }
                 return 0;
             }();
             s.dirs_per_lane = tile_of(tiles[ci]).dw;
             s.dirs_per_cta = tile_of(tiles[ci]).cw;
-            s.tile_kind = 3;
+            s.tile_kind = abi_kind(tile_of(tiles[ci]).kind);
             s.source_staged = tile_of(tiles[ci]).kind == 4 ? 0 : 1;
         }
     }
@@ -2265,6 +2315,7 @@ int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out
     if (o->max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
     if (!o->T_init && !(o->T_init_uniform > 0.0)) return fail(p, BTE_EINVAL, "T_init_uniform must be > 0");
     if (!std::isfinite(o->Q_amp)) return fail(p, BTE_EINVAL, "Q_amp must be finite");
+    if (o->Q_amp_each) return fail(p, BTE_EINVAL, "Q_amp_each is for batched solves");
     if (o->T_wall)
         for (int f = 0; f < 6; ++f)
             if (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL && (!(o->T_wall[f] > 0) || !std::isfinite(o->T_wall[f])))
@@ -2318,6 +2369,7 @@ int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, 
     if (o->tile_kind != 0 && o->tile_kind != 1) return fail(p, BTE_EINVAL, "transient steps use the general kernel");
     if (!o->T_init && !(o->T_init_uniform > 0.0)) return fail(p, BTE_EINVAL, "T_init_uniform must be > 0");
     if (!std::isfinite(o->Q_amp)) return fail(p, BTE_EINVAL, "Q_amp must be finite");
+    if (o->Q_amp_each) return fail(p, BTE_EINVAL, "Q_amp_each is for batched solves");
     if (o->T_wall)
         for (int f = 0; f < 6; ++f)
             if (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL && (!(o->T_wall[f] > 0) || !std::isfinite(o->T_wall[f])))
@@ -2392,25 +2444,30 @@ int bte_batch_create(int n, bte_plan *const *plans, bte_batch **out) {
         const bte_plan *q = plans[0];
         if (p->B != q->B || p->D != q->D)
             return bfail(nullptr, BTE_EINVAL, "bte_batch_create: every instance needs the same band and direction counts");
-        if (p->dim > 2 || p->n_active != p->N || p->R != 1 || (p->ny + 31) / 32 > 16 || p->Fs > 0)
+        if (p->dim > 2 || p->Fs > 0 || (p->ny + 31) / 32 > 32)
             return bfail(nullptr, BTE_EINVAL,
-                         "bte_batch_create: instances must be unmasked 1D/2D grids with one region and no specular face");
+                         "bte_batch_create: instances must be 1D/2D grids of at most 1024 rows without specular faces");
         for (int j = 0; j < i; ++j)
             if (plans[j] == p) return bfail(nullptr, BTE_EINVAL, "bte_batch_create: a plan appears twice");
     }
     std::unique_ptr<bte_batch> bt(new bte_batch());
     bt->plans.assign(plans, plans + n);
     bt->n = n;
-    // size classes by 32-row block count; inside a class, largest first
-    std::map<int, std::vector<int>> by;
-    for (int i = 0; i < n; ++i) by[(plans[i]->ny + 31) / 32].push_back(i);
+    // size classes by kernel and 32-row block count: unmasked single-region
+    // instances of at most 16 row blocks run the row-pipeline kernel, the
+    // others (masks, several regions) the general kernel; inside a class,
+    // largest first
+    auto rowpipe_ok_b = [](const bte_plan *p) { return p->n_active == p->N && p->R == 1 && (p->ny + 31) / 32 <= 16; };
+    std::map<std::pair<int, int>, std::vector<int>> by;
+    for (int i = 0; i < n; ++i) by[{rowpipe_ok_b(plans[i]) ? 0 : 1, (plans[i]->ny + 31) / 32}].push_back(i);
     for (auto &kv : by) {
         std::vector<int> v = kv.second;
         std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return plans[a]->N > plans[b]->N; });
-        bte_batch::Cls c{kv.first, (int)bt->inst.size(), (int)v.size(), 0, 0};
+        bte_batch::Cls c{kv.first.second, (int)bt->inst.size(), (int)v.size(), 0, 0, kv.first.first, 1};
         for (int i : v) {
             c.nx_max = std::max(c.nx_max, plans[i]->nx);
             c.ny_max = std::max(c.ny_max, plans[i]->ny);
+            c.R_max = std::max(c.R_max, plans[i]->R);
             bt->inst.push_back(i);
         }
         bt->classes.push_back(c);
@@ -2451,6 +2508,10 @@ int bte_batch_solve(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_s
     if (o->max_iter < 1) return bfail(bt, BTE_EINVAL, "max_iter must be >= 1");
     if (o->T_init) return bfail(bt, BTE_EINVAL, "bte_batch_solve: use T_init_uniform");
     if (o->face_order == 2) return bfail(bt, BTE_EINVAL, "bte_batch_solve: step faces only (face_order 0 or 1)");
+    if (!std::isfinite(o->Q_amp)) return bfail(bt, BTE_EINVAL, "Q_amp must be finite");
+    if (o->Q_amp_each)
+        for (int i = 0; i < bt->n; ++i)
+            if (!std::isfinite(o->Q_amp_each[i])) return bfail(bt, BTE_EINVAL, "Q_amp_each must be finite");
     if (o->precision == BTE_FP32) return batch_solve_t<float>(bt, o, T_out, st, bs);
     if (o->precision == BTE_FP64) return batch_solve_t<double>(bt, o, T_out, st, bs);
     return bfail(bt, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");

@@ -54,9 +54,9 @@ struct SweepTile {
     static constexpr int kMaxThreads = (DW * LZ >= 16) ? ((LZ > 1) ? 1024 : 256) : 1024;
 };
 
-template <typename real, int DW, int LZ, bool Z, bool ADJ, bool EXT = false>
-__global__ void __launch_bounds__(SweepTile<DW, LZ, Z>::kMaxThreads)
-sweep_kernel(const __grid_constant__ SweepParams<real> P) {
+// The sweep of direction subset s of band b of problem P, by one CTA.
+template <typename real, int DW, int LZ, bool Z, bool ADJ, bool EXT>
+__device__ __forceinline__ void sweep_body(const SweepParams<real> &P, const int s, const int b) {
     {
         // one thread reads the stop flag: every warp of the CTA decides alike
         __shared__ int s_done;
@@ -73,8 +73,6 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
     real *s_z = s_y + 2 * nwarps * LZ * DW;                              // [2][nwarps][DW][32] (lane fastest)
     real *s_ein = s_z + (Z ? 2 * nwarps * 32 * DW : 0);                  // [F] (ein_smem)
 
-    const int s = blockIdx.x;
-    const int b = blockIdx.y;
     const Subset sub = P.sub[s];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -349,6 +347,23 @@ sweep_kernel(const __grid_constant__ SweepParams<real> P) {
         }
         __syncthreads();
     }
+}
+
+template <typename real, int DW, int LZ, bool Z, bool ADJ, bool EXT = false>
+__global__ void __launch_bounds__(SweepTile<DW, LZ, Z>::kMaxThreads)
+sweep_kernel(const __grid_constant__ SweepParams<real> P) {
+    sweep_body<real, DW, LZ, Z, ADJ, EXT>(P, blockIdx.x, blockIdx.y);
+}
+
+// Batched form for 2D instances (forward): blockIdx.z = the instance among
+// those of one class (same warps per CTA), whose parameters are read from
+// device memory; subsets beyond an instance's own count do nothing.
+template <typename real, int DW>
+__global__ void __launch_bounds__(SweepTile<DW, 1, false>::kMaxThreads)
+sweep_batch_kernel(const SweepParams<real> *__restrict__ params, const int *__restrict__ inst) {
+    const SweepParams<real> &P = params[inst[blockIdx.z]];
+    if ((int)blockIdx.x >= P.S || (int)blockIdx.y >= P.B) return;
+    sweep_body<real, DW, 1, false, false, false>(P, blockIdx.x, blockIdx.y);
 }
 
 template <typename real, int DW, int LZ, bool Z>
