@@ -184,7 +184,9 @@ typedef struct {
     int dirs_per_cta;       /* tile used: directions per CTA */
     double sweep_seconds;   /* with sweep timing on (bte_set_sweep_timing): summed device
                                time of the call's timed source-iteration sweep launches,
-                               each bracketed by CUDA events on its stream; else 0 */
+                               each bracketed by CUDA events on its stream, over the
+                               iterations the solve ran (a graph replay's iterations after
+                               convergence return at once and are not counted); else 0 */
     long long sweep_launches; /* number of sweep launches summed in sweep_seconds */
     int source_staged;      /* row-pipeline tile: 1 = per-cell source staged in shared memory,
                                0 = read ahead from global memory (other kernels: 1) */

@@ -1069,12 +1069,15 @@ bool timed_iter(const bte_plan *p, int i) { return p->time_every > 0 && i % p->t
 cudaEvent_t tev_a(bte_plan *p, int i) { return timed_iter(p, i) ? p->tev[2 * (i / p->time_every)] : nullptr; }
 cudaEvent_t tev_b(bte_plan *p, int i) { return timed_iter(p, i) ? p->tev[2 * (i / p->time_every) + 1] : nullptr; }
 
-// after the stream reached the last of k iterations: add the durations of
-// their timed sweeps (ms) and count them; cudaSuccess only if every pair was
-// recorded
-cudaError_t sum_timing_events(bte_plan *p, int k, double *ms, long long *n) {
+// after the stream reached the last of k iterations (global indices base ..
+// base + k - 1): add the durations of their timed sweeps (ms) and count them,
+// leaving out the iterations at or past `ran` (the iterations the solve has
+// finished): a replay's iterations after convergence return at once and
+// would pull the mean sweep time down; cudaSuccess only if every counted
+// pair was recorded
+cudaError_t sum_timing_events(bte_plan *p, int k, int base, int ran, double *ms, long long *n) {
     for (int i = 0; i < k; ++i) {
-        if (!timed_iter(p, i)) continue;
+        if (!timed_iter(p, i) || base + i >= ran) continue;
         float t = 0.f;
         const cudaError_t e = cudaEventElapsedTime(&t, tev_a(p, i), tev_b(p, i));
         if (e != cudaSuccess) return e;
@@ -1204,7 +1207,7 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
         launches += 2LL * k + 1;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
         CK(p, cudaStreamSynchronize(stream));
-        if (p->time_every) CK(p, sum_timing_events(p, k, &sweep_ms, &n_timed));
+        if (p->time_every) CK(p, sum_timing_events(p, k, enq - k, p->h_status->iter, &sweep_ms, &n_timed));
         if (p->h_status->done || p->h_status->status) break;
     }
     CK(p, cudaEventRecord(p->ev1, stream));
@@ -1490,7 +1493,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         enq += k;
         CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
         CK(p, cudaStreamSynchronize(stream));
-        if (p->time_every) CK(p, sum_timing_events(p, k, &sweep_ms, &n_timed));
+        if (p->time_every) CK(p, sum_timing_events(p, k, enq - k, p->h_status->iter, &sweep_ms, &n_timed));
         if (p->h_status->done || p->h_status->status) break;
     }
     const int n = p->h_status->iter;

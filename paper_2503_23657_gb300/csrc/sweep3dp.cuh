@@ -128,6 +128,31 @@ __device__ __forceinline__ void p3_store(real *p, const real (&v)[DW]) {
     }
 }
 
+// Asynchronous global -> shared copy of DW consecutive values (cp.async in
+// 16-byte pieces, through L2 only: the source was written by this CTA in this
+// launch); a copy shorter than 16 bytes goes through registers instead.
+// The caller commits the group.
+template <int DW, typename real>
+__device__ __forceinline__ void p3_cp_async(real *dst, const real *src) {
+    constexpr int kBytes = DW * (int)sizeof(real);
+    if constexpr (kBytes % 16 == 0) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+        const char *g = reinterpret_cast<const char *>(src);
+#pragma unroll
+        for (int o = 0; o < kBytes; o += 16)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + o), "l"(g + o) : "memory");
+    } else {
+        real v[DW];
+        p3_load<DW, true>(src, v);
+        p3_store<DW>(dst, v);
+    }
+}
+__device__ __forceinline__ void p3_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void p3_cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Shared-memory carve-up, in elements of real.
 struct P3Smem {
     int invd, srck, fw, zr, yr, tile, total;
@@ -138,9 +163,9 @@ __host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW) {
     s.invd = 0;                                        // [R][DW] 1 / diagonal
     s.srck = s.invd + p3_round4(R * DW);               // [R] source factor
     s.fw = s.srck + p3_round4(R);                      // [3][DW] face-sum weights
-    s.zr = s.fw + p3_round4(3 * DW);                   // [NW][RZ][32][DW] z rings
-    s.yr = s.zr + NW * kP3RZ * 32 * DW;                // [NW][RY][DW] y rings
-    s.tile = s.yr + NW * kP3RY * DW;                   // [NW][32][33] partial-sum tiles
+    s.zr = s.fw + p3_round4(3 * DW);                   // [NW + WY][RZ][32][DW] z rings
+    s.yr = s.zr + (NW + WY) * kP3RZ * 32 * DW;         // [NW + 2][RY][DW] y rings
+    s.tile = s.yr + (NW + 2) * kP3RY * DW;             // [NW][32][33] partial-sum tiles
     s.total = s.tile + NW * 32 * 33;
     return s;
 }
@@ -194,6 +219,16 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         s_invd[q] = dd < ndir ? P.invdiag[((long long)r * P.B + b) * P.D + d0 + dd] : real(0);
     }
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_srck[r] = P.srck[r * P.B + b];
+    {
+        // the bottom row warps' y ring (never written) and the first plane
+        // warps' z rings (filled from the previous pass from the second pass
+        // on) start as zeros
+        const int NW = WY * H;
+        real *yz = sm + L.yr + NW * RY * DW;
+        for (int q = threadIdx.x; q < RY * DW; q += blockDim.x) yz[q] = real(0);
+        real *zz = sm + L.zr;
+        for (int q = threadIdx.x; q < WY * RZ * 32 * DW; q += blockDim.x) zz[q] = real(0);
+    }
     for (int q = threadIdx.x; q < 3 * DW; q += blockDim.x) {
         const int a = q / DW, dd = q - a * DW;
         real v = real(0);
@@ -266,22 +301,27 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const bool wrap_rd = (h == 0) && M > 1;       // reads the previous pass's last plane
     const bool wrap_wr = (h == H - 1) && M > 1;   // writes this pass's last plane
     const bool feed_y = wy + 1 < WY;
-    const bool feed_z = h + 1 < H;
     real *const part_b = P.part + ((long long)b * P.Spad + s) * P.N;
     real *const fs_sb = P.fsum + ((long long)s * P.B + b) * P.F;
     real *const wrap_c = (M > 1) ? P.wrap + ((long long)s * P.B + b) * (long long)nx * ld_wrap * DW : nullptr;
     real *const tile = sm + L.tile + warp * 32 * 33;
     real *const tile_l = tile + lane * 33;
     // z rings: slot (local step mod RZ) of this lane; the writer (warp below
-    // in z) and the reader handle a given column at the same local step
-    real *const zr_out = sm + L.zr + warp * RZ * 32 * DW + lane * DW;
-    const real *const zr_in = sm + L.zr + (warp - WY) * RZ * 32 * DW + lane * DW;   // h > 0
-    real *const yr_out = sm + L.yr + warp * RY * DW;
-    const real *const yr_in = sm + L.yr + (warp - 1) * RY * DW;         // wy > 0
+    // in z) and the reader handle a given column at the same local step.
+    // Warp w reads ring w and writes ring w + WY: the first plane warps read
+    // rings they fill themselves from the wrap buffer (two steps ahead), the
+    // last plane warps write rings nobody reads, so every warp runs the same
+    // code.  y rings: warp w writes ring w for the warp above it in y (the top
+    // row warps write ring NW + 1, read by nobody), the bottom row warps read
+    // ring NW (zeros).
+    real *const zr_out = sm + L.zr + (warp + WY) * RZ * 32 * DW + lane * DW;
+    real *const zr_in = sm + L.zr + warp * RZ * 32 * DW + lane * DW;
+    real *const yr_out = sm + L.yr + (feed_y ? warp : WY * H + 1) * RY * DW;
+    const real *const yr_in = sm + L.yr + (wy > 0 ? warp - 1 : WY * H) * RY * DW;
 
     // record slots (local step mod 4) and data slots (local step mod 2)
     int rs[4], rc[STORE_E ? 4 : 1], rx[4], ry[4], riw[4];
-    real dt[2], dp[2], dex[2], dey[2], dez[2], dwz[2][DW];
+    real dt[2], dp[2], dex[2], dey[2], dez[2];
     // tracker of the record read next (local step tau + 4): its virtual
     // column uf (= ui + nx um, column ui of pass um), the steps cnt until it
     // leaves the current pass, and its skewed index (valid once uf >= 0)
@@ -317,10 +357,11 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
             sk_t += dsk_pass - dsk;
         }
     };
-    // source, boundary values and wrapped plane of the cell in record slot q;
-    // every load is unconditional (a cell without a boundary on a side reads
-    // face 0, a cell outside the grid the zero pad entry) and the step selects
-    auto fetch_data = [&](int q, int slot) {
+    // source, boundary values and wrapped plane of the cell in record slot q,
+    // used at local step tt; every load is unconditional (a side without a
+    // boundary reads face 0, the same address for every such lane; a cell
+    // outside the grid reads the zero pad entry) and the step selects
+    auto fetch_data = [&](int q, int slot, int tt) {
         const int sk = rs[q];
         const int fb = rx[q], fl = ry[q];
         const unsigned bm = ((unsigned)fl >> kSideShift) & 63u;
@@ -333,8 +374,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         dey[slot] = __ldg(einb + fy);
         dez[slot] = __ldg(einb + fz);
         if (wrap_rd) {
-            // written by this CTA earlier in this launch: read through L2
-            p3_load<DW, true>(wrap_c + ((long long)riw[q] * ld_wrap + j) * DW, dwz[slot]);
+            // the previous pass's last plane (written by this CTA earlier in
+            // this launch) into this warp's own z ring slot of step tt
+            p3_cp_async<DW>(zr_in + (tt & (RZ - 1)) * 32 * DW, wrap_c + ((long long)riw[q] * ld_wrap + j) * DW);
+            p3_cp_commit();
         }
     };
     // before its rows enter the grid a lane's registers hold zeros; the first
@@ -344,13 +387,9 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
 #pragma unroll
     for (int dd = 0; dd < DW; ++dd) old[dd] = real(0);
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int dd = 0; dd < DW; ++dd) dwz[q][dd] = real(0);
-#pragma unroll
     for (int q = 0; q < 4; ++q) fetch_record(q);
-    fetch_data(0, 0);
-    fetch_data(1, 1);
+    fetch_data(0, 0, 0);
+    fetch_data(1, 1, 1);
 
     for (int t0 = 0; t0 < T; t0 += K) {
         const int tau0 = t0 - delta;
@@ -365,12 +404,16 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 const real tsv = dt[k & 1];
                 const real phv = PHI ? dp[k & 1] : real(0);
                 const real Ex = dex[k & 1], Ey = dey[k & 1], Ez = dez[k & 1];
-                real zin[DW];
-#pragma unroll
-                for (int dd = 0; dd < DW; ++dd) zin[dd] = dwz[k & 1][dd];
+                // this step's z and y inputs (the first plane warps' own z
+                // ring slot was filled by the copy issued two steps ago)
+                const int zslot = (tau & (RZ - 1)) * 32 * DW;
+                real zin[DW], yin[DW];
+                if (wrap_rd) p3_cp_wait<1>();
+                p3_load<DW>(zr_in + zslot, zin);
+                p3_load<DW>(yr_in + (tau & (RY - 1)) * DW, yin);  // lane 0: u == tau
                 // reads for later steps
                 fetch_record(k);
-                fetch_data((k + 2) & 3, k & 1);
+                fetch_data((k + 2) & 3, k & 1, tau + 2);
 
                 const int region = fl & kRegionMask;
                 const bool act = region != 0;   // solid cell of the grid
@@ -381,37 +424,47 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 const int r = act ? region - 1 : 0;
                 real base = tsv * s_srck[r];
                 if (PHI) base += phv * qb;
-                real invd[DW], yin[DW];
+                real invd[DW];
                 p3_load<DW>(s_invd + r * DW, invd);
-                const int zslot = (tau & (RZ - 1)) * 32 * DW;
-                if (h > 0) p3_load<DW>(zr_in + zslot, zin);
-                if (wy > 0) {
-                    p3_load<DW>(yr_in + (tau & (RY - 1)) * DW, yin);  // lane 0: u == tau
-                } else {
-#pragma unroll
-                    for (int dd = 0; dd < DW; ++dd) yin[dd] = real(0);
-                }
                 // cells that are not solid cells of the grid update garbage
                 // that no solid cell reads (their downwind neighbours take
                 // boundary values) and that the update kernel ignores
                 real acc = real(0);
+                // x and z boundaries are met in few warp steps (a row's first
+                // column, a pass's first plane, void neighbours): the selects
+                // for them only run when a lane of the warp needs them
+                if (__any_sync(0xffffffffu, bx || bz)) {
 #pragma unroll
-                for (int dd = 0; dd < DW; ++dd) {
-                    real vy = __shfl_up_sync(0xffffffffu, old[dd], 1);
-                    if (lane == 0) vy = yin[dd];
-                    const real vx = bx ? Ex : old[dd];
-                    vy = by ? Ey : vy;
-                    const real vz = bz ? Ez : zin[dd];
-                    real r0 = fma(ax[dd], vx, base);
-                    r0 = fma(ay[dd], vy, r0);
-                    r0 = fma(az[dd], vz, r0);
-                    const real en = r0 * invd[dd];
-                    old[dd] = en;
-                    acc = fma(w[dd], en, acc);
+                    for (int dd = 0; dd < DW; ++dd) {
+                        real vy = __shfl_up_sync(0xffffffffu, old[dd], 1);
+                        if (lane == 0) vy = yin[dd];
+                        const real vx = bx ? Ex : old[dd];
+                        vy = by ? Ey : vy;
+                        const real vz = bz ? Ez : zin[dd];
+                        real r0 = fma(ax[dd], vx, base);
+                        r0 = fma(ay[dd], vy, r0);
+                        r0 = fma(az[dd], vz, r0);
+                        const real en = r0 * invd[dd];
+                        old[dd] = en;
+                        acc = fma(w[dd], en, acc);
+                    }
+                } else {
+#pragma unroll
+                    for (int dd = 0; dd < DW; ++dd) {
+                        real vy = __shfl_up_sync(0xffffffffu, old[dd], 1);
+                        if (lane == 0) vy = yin[dd];
+                        vy = by ? Ey : vy;
+                        real r0 = fma(ax[dd], old[dd], base);
+                        r0 = fma(ay[dd], vy, r0);
+                        r0 = fma(az[dd], zin[dd], r0);
+                        const real en = r0 * invd[dd];
+                        old[dd] = en;
+                        acc = fma(w[dd], en, acc);
+                    }
                 }
                 tile_l[tau & 31] = acc;
-                if (feed_z) p3_store<DW>(zr_out + zslot, old);
-                if (feed_y && lane == 31) p3_store<DW>(yr_out + ((tau - 31) & (RY - 1)) * DW, old);
+                p3_store<DW>(zr_out + zslot, old);
+                if (lane == 31) p3_store<DW>(yr_out + ((tau - 31) & (RY - 1)) * DW, old);
                 if (wrap_wr && iw >= 0) p3_store<DW>(wrap_c + ((long long)iw * ld_wrap + j) * DW, old);
                 // face sums at the boundary sides the traversal leaves by
                 // (not at isothermal domain faces: the iterations never read
@@ -483,6 +536,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         }
         __syncthreads();
     }
+    if (wrap_rd) p3_cp_wait<0>();   // no copy outlives the kernel
 }
 
 template <typename real>
