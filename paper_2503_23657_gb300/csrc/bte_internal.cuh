@@ -258,6 +258,7 @@ struct UpdateParams {
     SkewLayout skew;
     const double *__restrict__ g;     // adj: dJ/dT [N]
     const double *__restrict__ wgt;   // [R][B] fwd 1/tau_rb ; adj C_b/(4 pi tau_rb)
+    const real *__restrict__ wgtr;    // the same in the sweep precision
     const double *__restrict__ Kinv;  // [R]   1 / sum_b C_b/tau_rb
     const int *__restrict__ face_cell;
     const int *__restrict__ face_side;
@@ -280,6 +281,7 @@ struct UpdateParams {
     int ignore_done;                  // final replay passes
     int *batch_done;                  // batched solves: instances converged so far (or null)
     int defer;                        // 1: write the block partials, set *fin.pending, no ticket
+    int vec;                          // 1: 128-cell vector cell blocks (N a multiple of 4)
     FinalizeParams fin;               // (defer) where the partials go
 };
 
@@ -320,7 +322,8 @@ cudaError_t launch_skew(long long N, const SkewLayout &L, const T *src, T *dst, 
 // batched update: table[i] = {instance, block of that instance}, `blocks` entries
 template <typename real>
 cudaError_t launch_update_batch(const UpdateParams<real> *params, const int2 *table, int blocks, cudaStream_t st);
-int update_blocks(long long N, int F, int B);  // blocks of one instance's update launch
+int update_blocks(long long N, int F, int B);  // blocks of one instance's update launch (scalar cell blocks)
+int update_cell_block_count(long long N, bool vec);  // cell blocks of an update (vector or scalar form)
 
 template <typename real>
 cudaError_t launch_flux(long long N, int B, int D, const int2 *cell, const real *e,

@@ -708,12 +708,16 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int tid, bool a
     return sp;
 }
 
+// A one-plan update runs 128-cell vector blocks when the cell count is a
+// multiple of 4 (batched instances always run scalar blocks).
+inline bool upd_vec(const bte_plan *p) { return p->N % 4 == 0; }
+
 // Convergence bookkeeping of the plan's solve (forward: with eps history).
 FinalizeParams fin_params(bte_plan *p, double tol, bool adj) {
     FinalizeParams f{};
     Status *st = p->d_status.as<Status>();
     f.blockpart = p->d_blockpart.as<double>();
-    f.nblocks = (int)((p->N + 31) / 32);  // the update's cell blocks (32 cells each)
+    f.nblocks = update_cell_block_count(p->N, upd_vec(p));  // the update's cell blocks
     f.n_active = p->n_active;
     f.tol = tol;
     f.done = &st->done;
@@ -746,6 +750,10 @@ UpdateParams<real> update_params(bte_plan *p, Workspace<real> &ws, int tid, bool
     u.fsum = ws.fsum.template as<real>();
     u.g = ws.g.template as<double>();
     u.wgt = adj ? ws.wgt_a.template as<double>() : ws.wgt_f.template as<double>();
+    // the same weights in the sweep precision: C_b/(4 pi tau_rb) is the
+    // forward source factor, 1/tau_rb the adjoint one
+    u.wgtr = adj ? ws.srck_f.template as<real>() : ws.srck_a.template as<real>();
+    u.vec = upd_vec(p) ? 1 : 0;
     u.Kinv = ws.Kinv.template as<double>();
     u.face_cell = p->d_face_cell.as<int>();
     u.face_side = p->d_face_side.as<int>();
@@ -1977,6 +1985,7 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 sp.done = &st_all[i].done;
                 sp.status = &st_all[i].status;
                 FinalizeParams fin = fin_params(p, tol, false);
+                fin.nblocks = update_cell_block_count(p->N, false);   // batched updates: scalar cell blocks
                 fin.done = &st_all[i].done;
                 fin.iter = &st_all[i].iter;
                 fin.status = &st_all[i].status;
@@ -1986,6 +1995,7 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 sp.fin = fin;
                 sw[i] = sp;
                 UpdateParams<real> u = update_params(p, ws, tid, false, tol);
+                u.vec = 0;
                 u.x_in = ws.T[par].template as<double>();
                 u.x_out = ws.T[par ^ 1].template as<double>();
                 u.xdev_out = ws.tdev[par ^ 1].template as<real>();

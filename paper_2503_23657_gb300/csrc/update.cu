@@ -42,73 +42,176 @@ __device__ __forceinline__ void skew_store(const SkewLayout &L, long long c, T v
     dst[skew_index(L, 1, X, R, P)] = v;
 }
 
+// The sum over the S partial sets of one (band, cell): sets are N apart
+// ([B][Spad][N] layout), taken in batches of eight, each batch summed as a
+// fixed tree and added to the running sum, in the sweep precision.  Both cell
+// paths below form every cell's sum in exactly this order.
 template <typename real>
-__device__ __forceinline__ real sum_sets(const real *pp, int S, long long N) {
-    real a[8] = {real(0), real(0), real(0), real(0), real(0), real(0), real(0), real(0)};
-    int s = 0;
-    for (; s + 8 <= S; s += 8) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) a[q] += pp[(long long)(s + q) * N];
-    }
-    for (int q = 0; s < S; ++s, ++q) a[q] += pp[(long long)s * N];
+__device__ __forceinline__ real tree8(const real (&a)[8]) {
     return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
+template <typename real>
+__device__ __forceinline__ real sum_sets(const real *pp, int S, long long N) {
+    real sum = real(0);
+    for (int s = 0; s < S; s += 8) {
+        real a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = (s + q < S) ? __ldcg(pp + (long long)(s + q) * N) : real(0);
+        sum += tree8(a);
+    }
+    return sum;
+}
 
-// Face blocks come first (they start with the cell blocks instead of after
-// them); a cell block is 32 cells x 8 band slots: each thread sums the
-// partial sets of its bands (within a band in the sweep precision, i.e. over
-// directions), warp 0 combines the weighted band sums in FP64 in a fixed
-// order, updates its 32 cells and reduces the residual over them.  FP64
-// arithmetic is kept to what the result needs (a warp-wide FP64 operation is
-// slow on this GPU), so only warp 0 of a block reduces.
+// Per cell, the update combines its bands in a fixed order: band b belongs to
+// slot b mod 8, a slot accumulates S_b times the band weight of the cell's
+// region in increasing b (fma chain, sweep precision), the eight slot sums
+// are added in slot order (sweep precision), and only that total is taken to
+// FP64: T is held as the deviation from T_ref, so the rounding of the band
+// sums is far below the resolution of T, while T itself, the residual and
+// every reduction across cells are FP64 (a warp-wide FP64 operation is slow
+// on this GPU).  Face blocks come first; then the cell blocks, in one of two
+// forms with the same per-cell arithmetic:
+//   * scalar: 32 cells x 8 band slots per block, thread (cell, slot);
+//   * vector (cell counts that are multiples of 4, so every partial set
+//     starts on a 16-byte boundary): 128 consecutive cells per block, warp w
+//     holds slot w for all of them, lane l cells 4 l .. 4 l + 3 (one 16-byte
+//     load per set and band), which keeps four times the bytes in flight per
+//     load and per register.
 constexpr int kCellsPerBlock = 32;
 constexpr int kBandSlots = kUpdThreads / kCellsPerBlock;
+constexpr int kVecCells = 128;
 
-__host__ __device__ inline int update_cell_blocks(long long N) { return (int)((N + kCellsPerBlock - 1) / kCellsPerBlock); }
+__host__ __device__ inline int update_cell_blocks(long long N, bool vec) {
+    return vec ? (int)((N + kVecCells - 1) / kVecCells) : (int)((N + kCellsPerBlock - 1) / kCellsPerBlock);
+}
 __host__ __device__ inline int update_face_blocks(int F, int B) {
     return (int)(((long long)F * B + kUpdThreads - 1) / kUpdThreads);
 }
 
-// Block `blk` of the update of problem P (face blocks, then cell blocks).
+// Face block `blk`: the next inflow of diffuse faces from the face sums.
 template <typename real>
-__device__ __forceinline__ void update_body(const UpdateParams<real> &P, const int blk) {
-    __shared__ double sband[kBandSlots][kCellsPerBlock];
-    __shared__ int is_last;
-    // the next kernel may be launched now; wait for the sweep's results
-    pdl_launch_dependents();
-    pdl_wait();
-    const int face_blocks = update_face_blocks(P.F, P.B);
-    const int cell_blocks = update_cell_blocks(P.N);
-    if (blk < face_blocks) {
-        if (!P.ignore_done && *((volatile int *)P.done) != 0) return;
-        const long long fb = (long long)blk * kUpdThreads + threadIdx.x;
-        if (fb < (long long)P.F * P.B) {
-            const int b = (int)(fb / P.F);
-            const int f = (int)(fb % P.F);
-            const int side = P.face_side[f];
-            const int a = side >> 1;
-            const bool plus = side & 1;
-            if (P.face_kind[f] == 2) {
-                // specular faces: the sweeps carry their per-direction inflow
-                P.ein_out[fb] = (real)0;
-                if (P.fsum_total) P.fsum_total[fb] = 0.0;
-            } else if (P.face_kind[f] == 0 && !P.adjoint) {
-                P.ein_out[fb] = P.ein_fixed[fb];
-            } else {
-                // sets leaving the cell through this face: those running
-                // upward on axis a for a plus face, downward otherwise
-                double sum = 0.0;
-                for (int s = 0; s < P.Sf; ++s) {
-                    const bool neg = (P.sub[s].neg >> a) & 1;
-                    if (neg != plus) sum += (double)P.fsum[((long long)s * P.B + b) * P.F + f];
-                }
-                if (P.fsum_total) P.fsum_total[fb] = sum;
-                P.ein_out[fb] = (P.face_kind[f] == 0) ? (real)0 : (real)(sum * P.side_scale[side * P.B + b]);
-            }
+__device__ __forceinline__ void update_faces(const UpdateParams<real> &P, const int blk) {
+    if (!P.ignore_done && *((volatile int *)P.done) != 0) return;
+    const long long fb = (long long)blk * kUpdThreads + threadIdx.x;
+    if (fb >= (long long)P.F * P.B) return;
+    const int b = (int)(fb / P.F);
+    const int f = (int)(fb % P.F);
+    const int side = P.face_side[f];
+    const int a = side >> 1;
+    const bool plus = side & 1;
+    if (P.face_kind[f] == 2) {
+        // specular faces: the sweeps carry their per-direction inflow
+        P.ein_out[fb] = (real)0;
+        if (P.fsum_total) P.fsum_total[fb] = 0.0;
+    } else if (P.face_kind[f] == 0 && !P.adjoint) {
+        P.ein_out[fb] = P.ein_fixed[fb];
+    } else {
+        // sets leaving the cell through this face: those running upward on
+        // axis a for a plus face, downward otherwise
+        double sum = 0.0;
+        for (int s = 0; s < P.Sf; ++s) {
+            const bool neg = (P.sub[s].neg >> a) & 1;
+            if (neg != plus) sum += (double)P.fsum[((long long)s * P.B + b) * P.F + f];
+        }
+        if (P.fsum_total) P.fsum_total[fb] = sum;
+        P.ein_out[fb] = (P.face_kind[f] == 0) ? (real)0 : (real)(sum * P.side_scale[side * P.B + b]);
+    }
+}
+
+// The new value of cell c (region r, slot total tot, old value x_old): writes
+// it and returns its contribution to the residual (squared change, maximum).
+template <typename real>
+__device__ __forceinline__ void update_cell_value(const UpdateParams<real> &P, long long c, int r, real tot,
+                                                  double x_old, double &ss, double &mx) {
+    ss = 0.0;
+    mx = -INFINITY;
+    if (r != 0) {
+        double xn;
+        real xd;
+        if (!P.adjoint) {
+            const double dev = (double)tot * P.Kinv[r - 1];
+            xn = P.T_ref + dev;
+            xd = (real)dev;
+            mx = xn;
+        } else {
+            xn = (P.g[c] + (double)tot) * P.Kinv[r - 1];
+            xd = (real)xn;
+            mx = fabs(xn);
+        }
+        P.xdev_out[c] = xd;
+        if (P.xskew_out) skew_store(P.skew, c, xd, P.xskew_out);
+        const double d = xn - x_old;
+        ss = d * d;
+        if (!isfinite(xn)) {
+            // a NaN sum of squares and an infinite maximum: eps_T is NaN
+            // whatever the other cells hold (fmax would skip a NaN maximum)
+            ss = NAN;
+            mx = INFINITY;
+        }
+        P.x_out[c] = xn;
+    } else {
+        P.x_out[c] = 0.0;
+        P.xdev_out[c] = (real)0;
+        if (P.xskew_out) skew_store(P.skew, c, (real)0, P.xskew_out);
+    }
+}
+
+// Warp 0 of cell block cb, lane 0 holding the block's residual partials:
+// record them, then either mark the iteration pending (deferred
+// finalization) or take a ticket; the last block reduces every block's
+// partials in a fixed order and records the iteration.
+template <typename real>
+__device__ __forceinline__ void update_block_tail(const UpdateParams<real> &P, int cb, int cell_blocks, double ss,
+                                                  double mx, int it_prev, int *is_last) {
+    const int lane = threadIdx.x & 31;
+    if (P.defer) {
+        // deferred finalization: the block partials and the pending mark;
+        // the next pipeline sweep (or the finalize kernel) reduces them
+        if (lane == 0) {
+            P.blockpart[2 * cb] = ss;
+            P.blockpart[2 * cb + 1] = mx;
+            if (cb == 0) *P.fin.pending = 1;
         }
         return;
     }
-    const int cb = blk - face_blocks;
+    if (lane == 0) {
+        P.blockpart[2 * cb] = ss;
+        P.blockpart[2 * cb + 1] = mx;
+        __threadfence();
+        const unsigned ticket = atomicAdd(P.counter, 1u);
+        *is_last = (ticket == (unsigned)cell_blocks - 1);
+    }
+    __syncwarp();
+    if (!*is_last) return;
+    __threadfence();
+    // last cell block, warp 0: the deterministic reduction of the block
+    // partials (fixed slices, fixed shuffle tree)
+    double eps, tmx, tss;
+    fin_reduce(P.fin, eps, tmx, tss);
+    if (lane == 0) {
+        *P.counter = 0u;
+        const int it = it_prev;
+        if (P.eps_hist && it < P.max_hist) P.eps_hist[it] = eps;
+        P.last[0] = eps;
+        P.last[1] = tmx;
+        P.last[2] = tss;
+        if (!P.ignore_done) {
+            *P.iter = it + 1;
+            const bool stop_now = !isfinite(eps) || (P.tol > 0.0 && eps < P.tol);
+            if (!isfinite(eps)) atomicCAS(P.status, 0, 1);   // keeps an expired-wait status (2)
+            if (stop_now) {
+                *P.done = 1;
+                if (P.batch_done) atomicAdd(P.batch_done, 1);
+            }
+        }
+    }
+}
+
+// Scalar cell block cb: 32 cells x 8 band slots.
+template <typename real>
+__device__ __forceinline__ void update_cells(const UpdateParams<real> &P, const int cb, const int cell_blocks) {
+    __shared__ real sband[kBandSlots][kCellsPerBlock];
+    __shared__ int is_last;
     const int tx = threadIdx.x % kCellsPerBlock;
     const int ty = threadIdx.x / kCellsPerBlock;
     const long long c = (long long)cb * kCellsPerBlock + tx;
@@ -133,113 +236,169 @@ __device__ __forceinline__ void update_body(const UpdateParams<real> &P, const i
             a0[q] = (in_s && b0 < P.B) ? __ldcg(pp0 + (long long)(s + q) * P.N) : real(0);
             a1[q] = (in_s && b1 < P.B) ? __ldcg(pp1 + (long long)(s + q) * P.N) : real(0);
         }
-        s0 += ((a0[0] + a0[1]) + (a0[2] + a0[3])) + ((a0[4] + a0[5]) + (a0[6] + a0[7]));
-        s1 += ((a1[0] + a1[1]) + (a1[2] + a1[3])) + ((a1[4] + a1[5]) + (a1[6] + a1[7]));
+        s0 += tree8(a0);
+        s1 += tree8(a1);
     }
     if (stop) return;  // converged earlier: this replayed iteration does nothing
-    double acc = 0.0;
+    real acc = real(0);
     if (r != 0) {
-        const double *wr = P.wgt + (r - 1) * P.B;
-        if (b0 < P.B) acc += (double)s0 * wr[b0];
-        if (b1 < P.B) acc += (double)s1 * wr[b1];
-        for (int b = ty + 2 * kBandSlots; b < P.B; b += kBandSlots) {
-            const real *pp = P.part + (long long)b * P.Spad * P.N + c;
-            acc += (double)sum_sets(pp, P.S, P.N) * wr[b];
-        }
+        const real *wr = P.wgtr + (r - 1) * P.B;
+        if (b0 < P.B) acc = fma(s0, wr[b0], acc);
+        if (b1 < P.B) acc = fma(s1, wr[b1], acc);
+        for (int b = ty + 2 * kBandSlots; b < P.B; b += kBandSlots)
+            acc = fma(sum_sets(P.part + (long long)b * P.Spad * P.N + c, P.S, P.N), wr[b], acc);
     }
     sband[ty][tx] = acc;
     __syncthreads();
     if (ty != 0) return;
     double ss = 0.0, mx = -INFINITY;
     if (cin) {
-        if (r != 0) {
-            double tot = 0.0;
+        real tot = real(0);
 #pragma unroll
-            for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
-            double xn;
-            real xd;
-            if (!P.adjoint) {
-                const double dev = tot * P.Kinv[r - 1];
-                xn = P.T_ref + dev;
-                xd = (real)dev;
-                mx = xn;
-            } else {
-                xn = (P.g[c] + tot) * P.Kinv[r - 1];
-                xd = (real)xn;
-                mx = fabs(xn);
-            }
-            P.xdev_out[c] = xd;
-            if (P.xskew_out) skew_store(P.skew, c, xd, P.xskew_out);
-            const double d = xn - x_old;
-            ss = d * d;
-            if (!isfinite(xn)) {
-                // a NaN sum of squares and an infinite maximum: eps_T is NaN
-                // whatever the other cells hold (fmax would skip a NaN maximum)
-                ss = NAN;
-                mx = INFINITY;
-            }
-            P.x_out[c] = xn;
-        } else {
-            P.x_out[c] = 0.0;
-            P.xdev_out[c] = (real)0;
-            if (P.xskew_out) skew_store(P.skew, c, (real)0, P.xskew_out);
-        }
+        for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
+        update_cell_value(P, c, r, tot, x_old, ss, mx);
     }
     fin_warp_reduce(ss, mx);
-    if (P.defer) {
-        // deferred finalization: the block partials and the pending mark;
-        // the next row-pipeline sweep (or the finalize kernel) reduces them
-        if (tx == 0) {
-            P.blockpart[2 * cb] = ss;
-            P.blockpart[2 * cb + 1] = mx;
-            if (cb == 0) *P.fin.pending = 1;
+    update_block_tail(P, cb, cell_blocks, ss, mx, it_prev, &is_last);
+}
+
+// Four consecutive values of a partial set, through L2 only.
+__device__ __forceinline__ void ld_cells4(const float *p, float (&v)[4]) {
+    const float4 x = __ldcg(reinterpret_cast<const float4 *>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+}
+__device__ __forceinline__ void ld_cells4(const double *p, double (&v)[4]) {
+    const double2 x = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 y = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = y.x;
+    v[3] = y.y;
+}
+
+__device__ __forceinline__ void st_cells4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st_cells4(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Vector cell block cb: 128 cells; warp w = band slot w.
+template <typename real>
+__device__ __forceinline__ void update_cells_vec(const UpdateParams<real> &P, const int cb, const int cell_blocks) {
+    __shared__ __align__(16) real sslot[kBandSlots][kVecCells];
+    __shared__ double sred[2][kVecCells / 32];
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    if (!P.ignore_done && *((volatile int *)P.done) != 0) return;  // converged earlier: nothing to do
+    const long long c0 = (long long)cb * kVecCells + 4 * lane;
+    const bool lin = c0 < P.N;   // N is a multiple of 4: all four cells or none
+    int reg[4];
+    if (lin) {
+        const int4 q0 = *reinterpret_cast<const int4 *>(P.cell + c0);
+        const int4 q1 = *reinterpret_cast<const int4 *>(P.cell + c0 + 2);
+        reg[0] = q0.y & kRegionMask;
+        reg[1] = q0.w & kRegionMask;
+        reg[2] = q1.y & kRegionMask;
+        reg[3] = q1.w & kRegionMask;
+    } else {
+        reg[0] = reg[1] = reg[2] = reg[3] = 0;
+    }
+    real acc[4] = {real(0), real(0), real(0), real(0)};
+    for (int b = warp; b < P.B; b += kBandSlots) {
+        const real *pp = P.part + (long long)b * P.Spad * P.N + (lin ? c0 : 0);
+        real sb[4] = {real(0), real(0), real(0), real(0)};
+        for (int s = 0; s < P.S; s += 8) {
+            // a batch of eight sets as two halves of four (the same tree:
+            // ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7)))
+            real hs[2][4];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                real a[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int sq = s + 4 * half + q;
+                    if (lin && sq < P.S) {
+                        ld_cells4(pp + (long long)sq * P.N, a[q]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) a[q][v] = real(0);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) hs[half][v] = (a[0][v] + a[1][v]) + (a[2][v] + a[3][v]);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sb[v] += hs[0][v] + hs[1][v];
         }
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (reg[v] != 0) acc[v] = fma(sb[v], P.wgtr[(reg[v] - 1) * P.B + b], acc[v]);
+    }
+    st_cells4(&sslot[warp][4 * lane], acc);
+    __syncthreads();
+    // one thread per cell for the FP64 part (warps 0 .. 3)
+    const int t = threadIdx.x;
+    if (t >= kVecCells) return;
+    const long long c = (long long)cb * kVecCells + t;
+    double ss = 0.0, mx = -INFINITY;
+    if (c < P.N) {
+        real tot = real(0);
+#pragma unroll
+        for (int y = 0; y < kBandSlots; ++y) tot += sslot[y][t];
+        update_cell_value(P, c, P.cell[c].y & kRegionMask, tot, P.x_in[c], ss, mx);
+    }
+    fin_warp_reduce(ss, mx);
+    if (lane == 0) {
+        sred[0][warp] = ss;
+        sred[1][warp] = mx;
+    }
+    // the four warps' partials, in warp order (named barrier of warps 0 .. 3)
+    asm volatile("bar.sync 1, %0;" ::"n"(kVecCells) : "memory");
+    if (warp != 0) return;
+    const int it_prev = (lane == 0) ? *P.iter : 0;
+    ss = ((sred[0][0] + sred[0][1]) + (sred[0][2] + sred[0][3]));
+    mx = fmax(fmax(sred[1][0], sred[1][1]), fmax(sred[1][2], sred[1][3]));
+    update_block_tail(P, cb, cell_blocks, ss, mx, it_prev, &is_last);
+}
+
+// Block `blk` of the update of problem P (face blocks, then cell blocks).
+template <typename real, bool VEC>
+__device__ __forceinline__ void update_body(const UpdateParams<real> &P, const int blk) {
+    // the next kernel may be launched now; wait for the sweep's results
+    pdl_launch_dependents();
+    pdl_wait();
+    const int face_blocks = update_face_blocks(P.F, P.B);
+    if (blk < face_blocks) {
+        update_faces(P, blk);
         return;
     }
-    if (tx == 0) {
-        P.blockpart[2 * cb] = ss;
-        P.blockpart[2 * cb + 1] = mx;
-        __threadfence();
-        const unsigned ticket = atomicAdd(P.counter, 1u);
-        is_last = (ticket == (unsigned)cell_blocks - 1);
-    }
-    __syncwarp();
-    if (!is_last) return;
-    __threadfence();
-    // last cell block, warp 0: the deterministic reduction of the block
-    // partials (fixed slices, fixed shuffle tree)
-    double eps, tmx, tss;
-    fin_reduce(P.fin, eps, tmx, tss);
-    if (tx == 0) {
-        *P.counter = 0u;
-        const int it = it_prev;
-        if (P.eps_hist && it < P.max_hist) P.eps_hist[it] = eps;
-        P.last[0] = eps;
-        P.last[1] = tmx;
-        P.last[2] = tss;
-        if (!P.ignore_done) {
-            *P.iter = it + 1;
-            const bool stop_now = !isfinite(eps) || (P.tol > 0.0 && eps < P.tol);
-            if (!isfinite(eps)) atomicCAS(P.status, 0, 1);   // keeps an expired-wait status (2)
-            if (stop_now) {
-                *P.done = 1;
-                if (P.batch_done) atomicAdd(P.batch_done, 1);
-            }
-        }
-    }
+    const int cell_blocks = update_cell_blocks(P.N, VEC);
+    if constexpr (VEC)
+        update_cells_vec(P, blk - face_blocks, cell_blocks);
+    else
+        update_cells(P, blk - face_blocks, cell_blocks);
 }
 
-template <typename real>
-__global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(const __grid_constant__ UpdateParams<real> P) {
-    update_body<real>(P, blockIdx.x);
+// (the FP64 vector form holds twice the bytes per load: three blocks per SM)
+template <typename real, bool VEC>
+__global__ void __launch_bounds__(kUpdThreads, (VEC && sizeof(real) == 8) ? 3 : 4)
+update_kernel(const __grid_constant__ UpdateParams<real> P) {
+    update_body<real, VEC>(P, blockIdx.x);
 }
 
-// Batched form: table[blockIdx.x] = {instance, block of that instance}.
+// Batched form: table[blockIdx.x] = {instance, block of that instance}; the
+// scalar cell blocks (their per-cell arithmetic is that of the vector form).
 template <typename real>
 __global__ void __launch_bounds__(kUpdThreads, 4)
 update_batch_kernel(const UpdateParams<real> *__restrict__ params, const int2 *__restrict__ table) {
     const int2 e = table[blockIdx.x];
-    update_body<real>(params[e.x], e.y);
+    update_body<real, false>(params[e.x], e.y);
 }
 
 // Close a graph replay / an eager chunk under deferred finalization: one
@@ -262,8 +421,12 @@ cudaError_t launch_finalize(const UpdateParams<real> *params, int n, cudaStream_
 
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st) {
-    const int blocks = update_face_blocks(p.F, p.B) + update_cell_blocks(p.N);
-    return launch_pdl(update_kernel<real>, dim3(blocks), dim3(kUpdThreads), 0, st, p);
+    const int blocks = update_face_blocks(p.F, p.B) + update_cell_blocks(p.N, p.vec != 0);
+    if (p.vec) {
+        if (p.N % 4 != 0) return cudaErrorInvalidValue;
+        return launch_pdl(update_kernel<real, true>, dim3(blocks), dim3(kUpdThreads), 0, st, p);
+    }
+    return launch_pdl(update_kernel<real, false>, dim3(blocks), dim3(kUpdThreads), 0, st, p);
 }
 
 template <typename real>
@@ -273,7 +436,8 @@ cudaError_t launch_update_batch(const UpdateParams<real> *params, const int2 *ta
     return cudaGetLastError();
 }
 
-int update_blocks(long long N, int F, int B) { return update_face_blocks(F, B) + update_cell_blocks(N); }
+int update_blocks(long long N, int F, int B) { return update_face_blocks(F, B) + update_cell_blocks(N, false); }
+int update_cell_block_count(long long N, bool vec) { return update_cell_blocks(N, vec); }
 
 // ---------------------------------------------------------------------------
 // heat flux q_c = sum_b v_b sum_d w_d s_d e_cbd (one warp per cell)
