@@ -322,7 +322,7 @@ cudaError_t launch_skew(long long N, const SkewLayout &L, const T *src, T *dst, 
 // batched update: table[i] = {instance, block of that instance}, `blocks` entries
 template <typename real>
 cudaError_t launch_update_batch(const UpdateParams<real> *params, const int2 *table, int blocks, cudaStream_t st);
-int update_blocks(long long N, int F, int B);  // blocks of one instance's update launch (scalar cell blocks)
+int update_blocks(long long N, int F, int B, bool vec);  // blocks of one instance's update launch
 int update_cell_block_count(long long N, bool vec);  // cell blocks of an update (vector or scalar form)
 
 template <typename real>

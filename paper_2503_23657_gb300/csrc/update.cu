@@ -392,13 +392,17 @@ update_kernel(const __grid_constant__ UpdateParams<real> P) {
     update_body<real, VEC>(P, blockIdx.x);
 }
 
-// Batched form: table[blockIdx.x] = {instance, block of that instance}; the
-// scalar cell blocks (their per-cell arithmetic is that of the vector form).
+// Batched form: table[blockIdx.x] = {instance, block of that instance};
+// each instance's blocks take its own form (vector or scalar cell blocks).
 template <typename real>
-__global__ void __launch_bounds__(kUpdThreads, 4)
+__global__ void __launch_bounds__(kUpdThreads, sizeof(real) == 8 ? 3 : 4)
 update_batch_kernel(const UpdateParams<real> *__restrict__ params, const int2 *__restrict__ table) {
     const int2 e = table[blockIdx.x];
-    update_body<real, false>(params[e.x], e.y);
+    const UpdateParams<real> &P = params[e.x];
+    if (P.vec)
+        update_body<real, true>(P, e.y);
+    else
+        update_body<real, false>(P, e.y);
 }
 
 // Close a graph replay / an eager chunk under deferred finalization: one
@@ -436,7 +440,7 @@ cudaError_t launch_update_batch(const UpdateParams<real> *params, const int2 *ta
     return cudaGetLastError();
 }
 
-int update_blocks(long long N, int F, int B) { return update_face_blocks(F, B) + update_cell_blocks(N, false); }
+int update_blocks(long long N, int F, int B, bool vec) { return update_face_blocks(F, B) + update_cell_blocks(N, vec); }
 int update_cell_block_count(long long N, bool vec) { return update_cell_blocks(N, vec); }
 
 // ---------------------------------------------------------------------------
