@@ -230,6 +230,10 @@ struct Sweep3DParams {
     const int *__restrict__ done;
     int store_e;
     int adj;                          // 1: adjoint sweep (carries nu = mu / w)
+    int grad;                         // 1 (adjoint): gradient form, part receives the dJ/dtau partials
+    int iso_fsum;                     // 1: face sums at isothermal domain faces too
+    const real *__restrict__ tfwd;    // (grad) skewed forward T - T_ref
+    const real *__restrict__ cb4pi;   // (grad) [B] C_b / (4 pi)
     FinalizeParams fin;               // finalize the previous iteration (fin.pending null: nothing)
 };
 

@@ -1345,24 +1345,50 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
         u.ein_out = ws.mein[parity ^ 1].template as<real>();
         return launch_update<real>(u, stream);
     }
-    SweepParams<real> sp = sweep_params(p, ws, dw, true);
-    sp.tsrc = ws.thdev[parity].template as<real>();
-    sp.ein = ws.mein[parity].template as<real>();
-    sp.e = ws.e.template as<real>();
-    sp.gpart = ws.gpart.template as<real>();
-    sp.read_e = final_pass ? 1 : 0;
-    sp.tfwd = ws.tdev[p->solved_iters & 1].template as<real>();
-    sp.spec_in = ws.mspec[parity].template as<real>();
-    sp.spec_out = ws.mspec[parity ^ 1].template as<real>();
-    if (final_pass && p->want_glen) {
-        // cell-size partials against the inflow the final forward e was made from
-        const int fpar = (p->solved_iters - 1) & 1;
-        sp.glpart = ws.glpart.template as<real>();
-        sp.ein_fwd = ws.ein[fpar].template as<real>();
-        sp.spec_fwd = p->Fs ? ws.spec[fpar].template as<real>() : nullptr;
+    cudaError_t e;
+    if (is_pipe3(tile_of(dw).kind)) {
+        // the final pass on the plane pipeline: the transposed sweep (partial
+        // sets and face sums), then the same sweep in its gradient form (the
+        // dJ/dtau partials, into gpart), both from Theta^n
+        const int map = pipe3_map(tile_of(dw));
+        Sweep3DParams<real> a3 = sweep3d_params(p, ws, dw, true);
+        a3.tsrc = skewed_source(ws, ws.thdev[parity].template as<real>(), map);
+        if (!a3.tsrc) return cudaErrorInvalidValue;
+        a3.ein = ws.mein[parity].template as<real>();
+        a3.done = nullptr;
+        a3.iso_fsum = 1;   // the wall-temperature gradients read them
+        e = launch_sweep3dp<real>(a3, tile_of(dw).dw, stream);
+        if (e != cudaSuccess) return e;
+        Sweep3DParams<real> g3 = sweep3d_params(p, ws, dw, true);
+        g3.tsrc = skewed_source(ws, ws.thdev[parity].template as<real>(), map);
+        if (!g3.tsrc) return cudaErrorInvalidValue;
+        g3.ein = ws.mein[parity].template as<real>();
+        g3.done = nullptr;
+        g3.grad = 1;
+        g3.part = ws.gpart.template as<real>();
+        g3.tfwd = ws.skt[map][p->solved_iters & 1].template as<real>();   // T^n of the solve
+        g3.cb4pi = ws.cb4pi.template as<real>();
+        e = launch_sweep3dp<real>(g3, tile_of(dw).dw, stream);
+    } else {
+        SweepParams<real> sp = sweep_params(p, ws, dw, true);
+        sp.tsrc = ws.thdev[parity].template as<real>();
+        sp.ein = ws.mein[parity].template as<real>();
+        sp.e = ws.e.template as<real>();
+        sp.gpart = ws.gpart.template as<real>();
+        sp.read_e = final_pass ? 1 : 0;
+        sp.tfwd = ws.tdev[p->solved_iters & 1].template as<real>();
+        sp.spec_in = ws.mspec[parity].template as<real>();
+        sp.spec_out = ws.mspec[parity ^ 1].template as<real>();
+        if (final_pass && p->want_glen) {
+            // cell-size partials against the inflow the final forward e was made from
+            const int fpar = (p->solved_iters - 1) & 1;
+            sp.glpart = ws.glpart.template as<real>();
+            sp.ein_fwd = ws.ein[fpar].template as<real>();
+            sp.spec_fwd = p->Fs ? ws.spec[fpar].template as<real>() : nullptr;
+        }
+        if (final_pass) sp.done = nullptr;
+        e = launch_sweep<real>(sp, tile_of(dw).dw, tile_layers(p), p->dim == 3, true, stream);
     }
-    if (final_pass) sp.done = nullptr;
-    cudaError_t e = launch_sweep<real>(sp, tile_of(dw).dw, tile_layers(p), p->dim == 3, true, stream);
     if (e != cudaSuccess) return e;
     UpdateParams<real> u = update_params(p, ws, dw, true, tol);
     u.eps_hist = nullptr;  // the history belongs to the forward solve
@@ -1386,13 +1412,20 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     const int dw = p->solved_tile;
     // the final gradient pass reads e and runs on a general tile (the
     // extended variant when it also forms the cell-size partials)
-    std::vector<int> gen = tile_candidates(p, (int)sizeof(real), 1, g_L ? kSpecDW : 0);
-    if (gen.empty()) return fail(p, BTE_EINVAL, "no general sweep tile for the gradient pass");
-    const int gtile = gen[0];
-    if (int rc2 = ensure_subsets(p, ws, gtile)) return rc2;
+    // the final pass runs on the solve's own tile where that is the plane
+    // pipeline (its gradient form), else on a general tile
+    const bool pipe_grad = is_pipe3(tile_of(dw).kind) && !g_L && p->Fs == 0;
+    int gtile = dw;
+    if (!pipe_grad) {
+        std::vector<int> gen = tile_candidates(p, (int)sizeof(real), 1, g_L ? kSpecDW : 0);
+        if (gen.empty()) return fail(p, BTE_EINVAL, "no general sweep tile for the gradient pass");
+        gtile = gen[0];
+        if (int rc2 = ensure_subsets(p, ws, gtile)) return rc2;
+    }
     const long long N = p->N;
     const int B = p->B, F = std::max(p->F, 1);
     const size_t S = ws.subsets.at(gtile).first.size();  // the gradient pass: one set per chunk
+    const size_t Spad = ((size_t)cell_sets(gtile, (int)S) + 3) & ~(size_t)3;
     for (int i = 0; i < 2; ++i) {
         CK(p, ws.thdev[i].ensure(sizeof(real) * (N + 16)));
         CK(p, ws.mein[i].ensure(sizeof(real) * (size_t)B * F));
@@ -1401,8 +1434,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     if (p->Fs > 0) {
         for (int i = 0; i < 2; ++i) CK(p, ws.mspec[i].ensure(sizeof(real) * (size_t)B * p->Fs * p->D));
     }
-    CK(p, ws.gpart.ensure(sizeof(real) * ((S + 3) & ~(size_t)3) * B * N));
-    if (g_L) CK(p, ws.glpart.ensure(sizeof(real) * 3 * ((S + 3) & ~(size_t)3) * B * N));
+    CK(p, ws.gpart.ensure(sizeof(real) * Spad * B * N));
+    if (g_L) CK(p, ws.glpart.ensure(sizeof(real) * 3 * Spad * B * N));
     CK(p, ws.msum.ensure(sizeof(double) * (size_t)B * F));
     CK(p, ws.g.ensure(sizeof(double) * N));
     CK(p, ws.grad_out.ensure(sizeof(double) * (B + 10)));
@@ -1514,8 +1547,8 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     GradParams<real> gp{};
     gp.N = N;
     gp.B = B;
-    gp.S = (int)ws.subsets.at(gtile).first.size();
-    gp.Spad = (gp.S + 3) & ~3;
+    gp.S = cell_sets(gtile, (int)S);
+    gp.Spad = (int)Spad;
     gp.F = p->F;
     gp.cell = p->d_cell.as<int2>();
     gp.apart = ws.part.template as<real>();

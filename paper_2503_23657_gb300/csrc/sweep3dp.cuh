@@ -170,7 +170,12 @@ __host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW) {
     return s;
 }
 
-template <typename real, int DW, bool PHI, bool STORE_E, bool ZROWS>
+// EM: 0 = a source-iteration sweep; 1 = the same that also writes e; 2 =
+// the gradient form of the final adjoint pass: the per-cell sums become
+// sum_d w_d (nu_d - Theta)(e_d - e0) = sum_d (mu_d - w_d Theta)(e_d - e0),
+// e the forward solution's values and e0 = C_b (T - T_ref)/(4 pi) (the
+// partials of dJ/dtau), and no face sums are formed
+template <typename real, int DW, bool PHI, int EM, bool ZROWS>
 __global__ void __launch_bounds__(kP3MaxThreads, 1)
 sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     constexpr int K = kPipe3Chunk, RZ = kP3RZ, RY = kP3RY;
@@ -270,6 +275,8 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         }
     }
     const real qb = PHI ? P.qb[b] : real(0);
+    const real cb4pi = (EM == 2) ? P.cb4pi[b] : real(0);
+    const unsigned iso_skip = P.iso_fsum ? 0u : 63u;
     const real *einb = P.ein + (long long)b * P.F;
     const int j = 32 * wy + lane;
     const bool rowv = j < n1;
@@ -320,8 +327,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const real *const yr_in = sm + L.yr + (wy > 0 ? warp - 1 : WY * H) * RY * DW;
 
     // record slots (local step mod 4) and data slots (local step mod 2)
-    int rs[4], rc[STORE_E ? 4 : 1], rx[4], ry[4], riw[4];
+    constexpr bool STORE_E = EM == 1, GRAD = EM == 2;
+    int rs[4], rc[EM ? 4 : 1], rx[4], ry[4], riw[4];
     real dt[2], dp[2], dex[2], dey[2], dez[2];
+    real dtf[GRAD ? 2 : 1], dev[GRAD ? 2 : 1][DW];   // gradient form: forward T - T_ref and e
     // tracker of the record read next (local step tau + 4): its virtual
     // column uf (= ui + nx um, column ui of pass um), the steps cnt until it
     // leaves the current pass, and its skewed index (valid once uf >= 0)
@@ -334,11 +343,11 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         const int sk = v ? sk_t : sk_pad;
         rs[q] = sk;
         const int ui = nx - cnt;
-        if (STORE_E) {
+        if (EM) {
             const int X = negx ? nx - 1 - ui : ui;
             const int k = h + H * um;
             const int Z = neg2 ? n2 - 1 - k : k;
-            rc[STORE_E ? q : 0] = v ? X + s1 * Y + s2 * Z : -1;
+            rc[EM ? q : 0] = v ? X + s1 * Y + s2 * Z : -1;
         }
         // wrap buffer column: read by the first warp of a pass (the value is
         // used only past the first pass), written by the last one
@@ -373,6 +382,18 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         dex[slot] = __ldg(einb + fx);
         dey[slot] = __ldg(einb + fy);
         dez[slot] = __ldg(einb + fz);
+        if constexpr (GRAD) {
+            // the forward state of this cell (a cell outside the grid reads
+            // cell 0's, which no solid cell uses)
+            dtf[slot] = __ldg(P.tfwd + sk);
+            const real *ep = P.e + ((long long)max(rc[q], 0) * P.B + b) * P.D + d0;
+            if (vec_e) {
+                p3_load<DW>(ep, dev[slot]);
+            } else {
+#pragma unroll
+                for (int dd = 0; dd < DW; ++dd) dev[slot][dd] = dd < ndir ? ep[dd] : real(0);
+            }
+        }
         if (wrap_rd) {
             // the previous pass's last plane (written by this CTA earlier in
             // this launch) into this warp's own z ring slot of step tt
@@ -399,11 +420,18 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 const int tau = tau0 + k;
                 const int u = tau - lane;
                 // this step's cell (record read four steps ago, data two)
-                const int c = STORE_E ? rc[STORE_E ? k : 0] : -1;
+                const int c = EM ? rc[EM ? k : 0] : -1;
                 const int fb = rx[k], fl = ry[k], iw = riw[k];
                 const real tsv = dt[k & 1];
                 const real phv = PHI ? dp[k & 1] : real(0);
                 const real Ex = dex[k & 1], Ey = dey[k & 1], Ez = dez[k & 1];
+                // gradient form: e - e0 of the forward solution in this cell
+                real gde[GRAD ? DW : 1];
+                if constexpr (GRAD) {
+                    const real e0 = cb4pi * dtf[k & 1];
+#pragma unroll
+                    for (int dd = 0; dd < DW; ++dd) gde[dd] = dev[k & 1][dd] - e0;
+                }
                 // this step's z and y inputs (the first plane warps' own z
                 // ring slot was filled by the copy issued two steps ago)
                 const int zslot = (tau & (RZ - 1)) * 32 * DW;
@@ -446,7 +474,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                         r0 = fma(az[dd], vz, r0);
                         const real en = r0 * invd[dd];
                         old[dd] = en;
-                        acc = fma(w[dd], en, acc);
+                        if constexpr (GRAD)
+                            acc = fma(w[dd] * (en - tsv), gde[dd], acc);
+                        else
+                            acc = fma(w[dd], en, acc);
                     }
                 } else {
 #pragma unroll
@@ -459,7 +490,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                         r0 = fma(az[dd], zin[dd], r0);
                         const real en = r0 * invd[dd];
                         old[dd] = en;
-                        acc = fma(w[dd], en, acc);
+                        if constexpr (GRAD)
+                            acc = fma(w[dd] * (en - tsv), gde[dd], acc);
+                        else
+                            acc = fma(w[dd], en, acc);
                     }
                 }
                 tile_l[tau & 31] = acc;
@@ -467,10 +501,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 if (lane == 31) p3_store<DW>(yr_out + ((tau - 31) & (RY - 1)) * DW, old);
                 if (wrap_wr && iw >= 0) p3_store<DW>(wrap_c + ((long long)iw * ld_wrap + j) * DW, old);
                 // face sums at the boundary sides the traversal leaves by
-                // (not at isothermal domain faces: the iterations never read
-                // them there)
-                const unsigned fsm = bm & dn_mask & ~(((unsigned)fl >> kIsoShift) & 63u);
-                if (act && fsm) {
+                // (at isothermal domain faces only when asked: the iterations
+                // never read them there, the final adjoint pass does)
+                const unsigned fsm = bm & dn_mask & ~(((unsigned)fl >> kIsoShift) & iso_skip);
+                if (!GRAD && act && fsm) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int dn = (a == 0 ? up_x : (a == 1 ? up_1 : up_2)) ^ 1;
@@ -544,12 +578,12 @@ size_t sweep3dp_smem_bytes(int R, int WY, int H, int dw) {
     return (size_t)p3_smem(R, WY, H, dw).total * sizeof(real);
 }
 
-template <typename real, int DW, bool PHI, bool STORE_E, bool ZROWS>
+template <typename real, int DW, bool PHI, int EM, bool ZROWS>
 cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
     const int threads = p.WY * p.H * 32;
     if (p.H < 1 || p.WY < 1 || threads > kP3MaxThreads) return cudaErrorInvalidConfiguration;
     const size_t smem = sweep3dp_smem_bytes<real>(p.R, p.WY, p.H, DW);
-    auto kern = sweep3dp_kernel<real, DW, PHI, STORE_E, ZROWS>;
+    auto kern = sweep3dp_kernel<real, DW, PHI, EM, ZROWS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -557,15 +591,20 @@ cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
     return launch_pdl(kern, dim3(p.S, p.B), dim3(threads), smem, st, p);
 }
 
-// the source-profile term only in forward sweeps with a source; e only when asked
+// the source-profile term only in forward sweeps with a source; e only when
+// asked; the gradient form only in adjoint sweeps
 template <typename real, int DW, bool ZROWS>
 cudaError_t launch_sweep3dp_z(const Sweep3DParams<real> &p, cudaStream_t st) {
     const bool phi = !p.adj && p.phi != nullptr;
+    if (p.grad) {
+        if (!p.adj || p.store_e || !p.tfwd || !p.cb4pi || !p.e) return cudaErrorInvalidValue;
+        return launch_sweep3dp_v<real, DW, false, 2, ZROWS>(p, st);
+    }
     if (p.store_e)
-        return phi ? launch_sweep3dp_v<real, DW, true, true, ZROWS>(p, st)
-                   : launch_sweep3dp_v<real, DW, false, true, ZROWS>(p, st);
-    return phi ? launch_sweep3dp_v<real, DW, true, false, ZROWS>(p, st)
-               : launch_sweep3dp_v<real, DW, false, false, ZROWS>(p, st);
+        return phi ? launch_sweep3dp_v<real, DW, true, 1, ZROWS>(p, st)
+                   : launch_sweep3dp_v<real, DW, false, 1, ZROWS>(p, st);
+    return phi ? launch_sweep3dp_v<real, DW, true, 0, ZROWS>(p, st)
+               : launch_sweep3dp_v<real, DW, false, 0, ZROWS>(p, st);
 }
 
 // rows along y or along z
