@@ -124,11 +124,12 @@ class ClockSampler:
 # otherwise a capture with fewer bands, scaled to all bands (traffic grows in
 # proportion to the bands: every band is an independent set of CTAs).
 NCU_TRAFFIC = {
-    # FinFET 160x80x64, 15 bands, forward launch, full size (one-pass capture):
-    # 457.6 MB read + 1293.7 MB written
-    ("sweep3dp_kernel<float, 8, 1, 0, 1>", "3:8:8:2:8:2", "aab7c325aea6"): 1751316224,
-    # 64^3 hotspot, 15 bands, forward launch, full size: 66.6 MB read + 251.5 MB written
-    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:4:1", "aab7c325aea6"): 318085888,
+    # FinFET 160x80x64, 15 bands, forward launch, full size (one-pass capture),
+    # mean of two launches: 450.7 MB read + 1290.5 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 1>", "3:8:8:2:8:2", "271c1d0800a0"): 1741248768,
+    # 64^3 hotspot, 15 bands, forward launch, full size, mean of two launches:
+    # 70.0 MB read + 238.8 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:8:1", "271c1d0800a0"): 308844288,
 }
 KERNEL_SOURCES = {
     "sweep3dp_kernel": ["sweep3dp.cuh", "bte_internal.cuh", "finalize.cuh", "tma.cuh"],
