@@ -61,6 +61,8 @@ extern "C" {
 #define BTE_ETIMEOUT (-5)      /* a bounded device-side wait expired */
 #define BTE_ENUMERIC (-6)      /* NaN/Inf in the temperature update */
 #define BTE_ESTATE (-7)        /* call order violated (e.g. adjoint before solve) */
+#define BTE_ECORRUPT (-8)      /* debug mode (BTE_DEBUG set): a device buffer's guard words were
+                                  overwritten, or an index table points outside its extent */
 
 #define BTE_BC_ISOTHERMAL 0
 #define BTE_BC_DIFFUSE 1
@@ -169,6 +171,12 @@ typedef struct {
                                in plan order, each multiplying its own plan's q_profile; NULL =
                                Q_amp for every instance.  Must be NULL for bte_solve and
                                bte_transient (BTE_EINVAL otherwise) */
+    const double *ein_init; /* resume (with T_init): B x F doubles (host or device), the inflow
+                               energy density of every boundary face and band that the first
+                               iteration reads (as bte_get_state returns it), instead of the
+                               diffuse reflection of the equilibrium at T_init; NULL = that
+                               default.  Isothermal faces take their wall values either way.
+                               Not for bte_batch_solve (BTE_EINVAL) */
 } bte_solve_opts;
 
 typedef struct {
@@ -283,6 +291,29 @@ int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, 
 int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep);
 
 /*
+ * bte_get_state -- checkpoint of the outer iteration (solution procedure of
+ * the paper, steps 1-4: an iterate is fully determined by T and the diffuse
+ * inflow its boundary faces carry into the next sweep): after a bte_solve,
+ * T_out (N doubles, host or device, or NULL) receives the last iterate T^n
+ * and ein_out (B x F doubles, host or device, or NULL; b-major) the inflow
+ * energy density e_in of every boundary face and band that iteration n + 1
+ * would read (absolute, J/m^3 per steradian).  A bte_solve with T_init =
+ * T_out and ein_init = ein_out continues the iteration from there, up to
+ * the rounding of the deviation from T_ref (T_ref is the mean of T_init).
+ * Specular faces' per-direction inflow and the second-order correction are
+ * not part of the state (they restart from the isotropic e of T_init).
+ * Returns BTE_OK, BTE_EINVAL (null plan), BTE_ESTATE (no solve yet) or
+ * BTE_ECUDA.
+ */
+int bte_get_state(bte_plan *p, double *T_out, double *ein_out);
+
+/* bte_face_count -- F, the number of boundary faces of the plan (domain faces
+ * of solid cells and faces between solid and void cells, in cell order then
+ * side order): the extent of ein_init / bte_get_state's ein_out per band.
+ * BTE_EINVAL for a null plan. */
+int bte_face_count(const bte_plan *p);
+
+/*
  * bte_set_sweep_timing -- every >= 1: every following bte_solve / bte_adjoint
  * brackets the sweep launch of every `every`-th source iteration (counted
  * within each convergence poll interval, whose first iteration is always
@@ -362,6 +393,25 @@ int bte_batch_set_sweep_timing(bte_batch *b, int on);
  * limit.  Returns BTE_OK or BTE_EINVAL (null plan, polls < 0).
  */
 int bte_debug_set_wait_limit(bte_plan *p, long long polls);
+
+/*
+ * Debug mode (the environment variable BTE_DEBUG set to anything but "0" when
+ * the library first allocates): every device buffer the library allocates
+ * carries 256 guard bytes of a fixed pattern after its end; bte_solve,
+ * bte_adjoint(_ex), bte_transient and bte_batch_solve check the guards of
+ * every live buffer after they ran and return BTE_ECORRUPT if one was
+ * overwritten; bte_create checks every index table of the plan (face cells
+ * and sides, cell face bases, wall faces, direction permutation, specular
+ * tables) against its extent before uploading it and returns BTE_ECORRUPT
+ * for the first violation.  Off by default (the checks synchronise the
+ * device).
+ *
+ * bte_debug_overwrite_guard -- test hook (debug mode only): overwrites one
+ * guard byte of the plan's status buffer from the host (a write inside the
+ * allocation), so that the next solve reports BTE_ECORRUPT.  Returns BTE_OK,
+ * BTE_EINVAL (null plan), BTE_ESTATE (debug mode off) or BTE_ECUDA.
+ */
+int bte_debug_overwrite_guard(bte_plan *p);
 
 /* Copy the eps_T history of the last bte_solve (one value per iteration,
  * at most n, the first 65536 iterations) into out (host).  Returns the

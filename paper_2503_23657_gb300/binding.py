@@ -22,13 +22,14 @@ BTE_ENOTCONVERGED = -4
 BTE_ETIMEOUT = -5
 BTE_ENUMERIC = -6
 BTE_ESTATE = -7
+BTE_ECORRUPT = -8
 BTE_FP32 = 0
 BTE_FP64 = 1
 
 ERROR_NAMES = {
     BTE_EINVAL: "EINVAL", BTE_ENOMEM: "ENOMEM", BTE_ECUDA: "ECUDA",
     BTE_ENOTCONVERGED: "ENOTCONVERGED", BTE_ETIMEOUT: "ETIMEOUT",
-    BTE_ENUMERIC: "ENUMERIC", BTE_ESTATE: "ESTATE",
+    BTE_ENUMERIC: "ENUMERIC", BTE_ESTATE: "ESTATE", BTE_ECORRUPT: "ECORRUPT",
 }
 
 # every entry point declared in include/bte.h
@@ -36,7 +37,8 @@ EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_er
            "bte_version", "bte_default_opts", "bte_eps_history", "bte_profile_sweep",
            "bte_set_sweep_timing", "bte_eps_T_noalloc", "bte_batch_create", "bte_batch_solve",
            "bte_batch_destroy", "bte_batch_last_error", "bte_batch_set_sweep_timing", "bte_adjoint_ex",
-           "bte_transient", "bte_debug_set_wait_limit"]
+           "bte_transient", "bte_debug_set_wait_limit", "bte_get_state", "bte_debug_overwrite_guard",
+           "bte_face_count"]
 
 
 class Grid(ctypes.Structure):
@@ -64,7 +66,7 @@ class SolveOpts(ctypes.Structure):
                 ("dirs_per_lane", ctypes.c_int), ("store_e_every_iter", ctypes.c_int),
                 ("tile_kind", ctypes.c_int), ("dirs_per_cta", ctypes.c_int), ("source_staging", ctypes.c_int),
                 ("warps_z", ctypes.c_int), ("lane_axis", ctypes.c_int), ("face_order", ctypes.c_int),
-                ("Q_amp_each", ctypes.c_void_p)]
+                ("Q_amp_each", ctypes.c_void_p), ("ein_init", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -141,6 +143,12 @@ def load(path: str = LIB_PATH):
     lib.bte_transient.restype = ip
     lib.bte_debug_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.bte_debug_set_wait_limit.restype = ip
+    lib.bte_get_state.argtypes = [vp, vp, vp]
+    lib.bte_get_state.restype = ip
+    lib.bte_debug_overwrite_guard.argtypes = [vp]
+    lib.bte_debug_overwrite_guard.restype = ip
+    lib.bte_face_count.argtypes = [vp]
+    lib.bte_face_count.restype = ip
     _lib = lib
     return lib
 
@@ -240,7 +248,7 @@ class Plan:
 
     def _opts(self, precision, tol, max_iter, T_init, T_init_uniform, Q_amp, tau, T_wall, stream, poll_every,
               dirs_per_lane, store_e_every_iter, tile_kind, dirs_per_cta, source_staging, warps_z, lane_axis,
-              face_order, keep):
+              face_order, keep, ein_init=None):
         p = self.problem
         o = SolveOpts()
         self._lib.bte_default_opts(ctypes.byref(o))
@@ -265,6 +273,7 @@ class Plan:
         o.warps_z = warps_z
         o.lane_axis = lane_axis
         o.face_order = face_order
+        o.ein_init = _addr(ein_init)
         return o
 
     def transient(self, dt, n_steps, T_out, T_hist=None, precision=BTE_FP64, tol=1e-10, max_iter=100000,
@@ -285,14 +294,15 @@ class Plan:
     def solve(self, T_out, q_out=None, e_out=None, precision=BTE_FP32, tol=1e-6, max_iter=100000,
               T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None,
               poll_every=32, dirs_per_lane=0, store_e_every_iter=False, tile_kind=0, dirs_per_cta=0,
-              source_staging=0, warps_z=0, lane_axis=0, face_order=1, check=True):
+              source_staging=0, warps_z=0, lane_axis=0, face_order=1, ein_init=None, check=True):
         """Run bte_solve.  Buffers are numpy arrays (host) or torch tensors
-        (host or CUDA) of the documented sizes.  Returns (rc, stats dict)."""
+        (host or CUDA) of the documented sizes; T_init with ein_init (B x F)
+        resumes a state from get_state().  Returns (rc, stats dict)."""
         p = self.problem
         keep = []
         o = self._opts(precision, tol, max_iter, T_init, T_init_uniform, Q_amp, tau, T_wall, stream, poll_every,
                        dirs_per_lane, store_e_every_iter, tile_kind, dirs_per_cta, source_staging, warps_z,
-                       lane_axis, face_order, keep)
+                       lane_axis, face_order, keep, ein_init)
         st = Stats()
         rc = self._lib.bte_solve(self._h, ctypes.byref(o), _addr(T_out), _addr(q_out), _addr(e_out),
                                  ctypes.byref(st))
@@ -331,6 +341,29 @@ class Plan:
         iteration with CUDA events (0 = off); stats then carry sweep_seconds /
         sweep_launches."""
         rc = self._lib.bte_set_sweep_timing(self._h, int(every))
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
+
+    def n_faces(self):
+        """bte_face_count: the number of boundary faces F."""
+        return int(self._lib.bte_face_count(self._h))
+
+    def get_state(self):
+        """bte_get_state: (T [N], e_in [B, F]) of the last solve's final
+        iterate, the checkpoint that solve(T_init=T, ein_init=e_in) resumes."""
+        p = self.problem
+        T = np.zeros(p.n_cells)
+        F = self.n_faces()
+        ein = np.zeros((p.B, max(F, 0)))
+        rc = self._lib.bte_get_state(self._h, _addr(T), _addr(ein) if F > 0 else None)
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
+        return T, ein
+
+    def debug_overwrite_guard(self):
+        """bte_debug_overwrite_guard (test hook, BTE_DEBUG set): overwrite one
+        guard byte so that the next solve reports BTE_ECORRUPT."""
+        rc = self._lib.bte_debug_overwrite_guard(self._h)
         if rc != BTE_OK:
             raise BTEError(rc, self.error())
 

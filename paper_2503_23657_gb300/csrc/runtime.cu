@@ -20,6 +20,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -34,11 +36,35 @@ namespace {
 constexpr double kFourPi = 4.0 * M_PI;
 thread_local std::string g_create_error;
 
+// Debug mode (environment variable BTE_DEBUG set to anything but 0, read
+// once): every device buffer carries kGuardBytes of a fixed pattern after its
+// end, and the public entry points check every live buffer's guard after
+// they ran (BTE_ECORRUPT names the first overwritten one); plan creation also
+// checks its index tables against their extents.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+bool debug_mode() {
+    static const bool on = [] {
+        const char *v = std::getenv("BTE_DEBUG");
+        return v != nullptr && v[0] != '\0' && !(v[0] == '0' && v[1] == '\0');
+    }();
+    return on;
+}
+struct DevBuf;
+std::mutex g_guard_mu;
+std::set<const DevBuf *> g_guarded;   // live buffers with a guard (debug mode)
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    bool guarded = false;
     ~DevBuf() { release(); }
     void release() {
+        if (guarded) {
+            std::lock_guard<std::mutex> lk(g_guard_mu);
+            g_guarded.erase(this);
+            guarded = false;
+        }
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
@@ -47,17 +73,47 @@ struct DevBuf {
         if (n <= bytes && p) return cudaSuccess;
         release();
         if (n == 0) n = 16;
-        cudaError_t e = cudaMalloc(&p, n);
+        const bool dbg = debug_mode();
+        cudaError_t e = cudaMalloc(&p, dbg ? n + kGuardBytes : n);
         if (e != cudaSuccess) {
             p = nullptr;
             return e;
         }
         bytes = n;
+        if (dbg) {
+            e = cudaMemset(static_cast<char *>(p) + n, kGuardByte, kGuardBytes);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return e;
+            std::lock_guard<std::mutex> lk(g_guard_mu);
+            g_guarded.insert(this);
+            guarded = true;
+        }
         return cudaSuccess;
+    }
+    // debug mode: whether the guard after the buffer still holds its pattern
+    bool guard_intact() const {
+        if (!guarded || !p) return true;
+        unsigned char h[kGuardBytes];
+        if (cudaMemcpy(h, static_cast<const char *>(p) + bytes, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return false;
+        for (size_t i = 0; i < kGuardBytes; ++i)
+            if (h[i] != kGuardByte) return false;
+        return true;
     }
     template <typename T>
     T *as() const { return reinterpret_cast<T *>(p); }
 };
+
+// Debug mode: check every live guarded buffer (all plans and batches of the
+// process); the number of overwritten guards.
+int check_guards() {
+    if (!debug_mode()) return 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    int bad = 0;
+    for (const DevBuf *b : g_guarded) bad += b->guard_intact() ? 0 : 1;
+    return bad;
+}
 
 struct Status {
     int done;
@@ -233,6 +289,17 @@ int fail(bte_plan *p, int code, const std::string &msg) {
     else
         g_create_error = msg;
     return code;
+}
+
+// Debug mode: after a public entry point ran, BTE_ECORRUPT if any device
+// buffer's guard was overwritten (the call's own result otherwise).
+int guard_rc(bte_plan *p, int rc) {
+    if (!debug_mode()) return rc;
+    const int bad = check_guards();
+    if (bad < 0) return fail(p, BTE_ECORRUPT, "debug mode: device synchronisation failed during the guard check");
+    if (bad > 0)
+        return fail(p, BTE_ECORRUPT, "debug mode: " + std::to_string(bad) + " device buffer guard(s) overwritten");
+    return rc;
 }
 
 #define CK(plan, expr)                                                                              \
@@ -990,6 +1057,17 @@ int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaS
     for (long long c = 0; c < N; ++c) td[c] = p->mask[c] ? (real)(T0[c] - p->T_ref) : (real)0;
     const int B = p->B, F = std::max(p->F, 1);
     std::vector<real> e0((size_t)B * F, (real)0);
+    std::vector<double> ein0;
+    if (o->ein_init && p->F > 0) {
+        ein0.resize((size_t)B * p->F);
+        if (is_device_ptr(o->ein_init)) {
+            CK(p, cudaMemcpy(ein0.data(), o->ein_init, sizeof(double) * ein0.size(), cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(ein0.data(), o->ein_init, sizeof(double) * ein0.size());
+        }
+        for (double v : ein0)
+            if (!std::isfinite(v)) return fail(p, BTE_EINVAL, "ein_init must be finite");
+    }
     for (int f = 0; f < p->F; ++f) {
         const long long c = p->face_cell[f];
         const int side = p->face_side[f];
@@ -997,6 +1075,8 @@ int begin_state(bte_plan *p, const bte_solve_opts *o, Workspace<real> &ws, cudaS
             double val;
             if (p->face_kind[f] == 0)
                 val = p->C[b] * (p->cur_Tw[side] - p->T_ref) / kFourPi;
+            else if (!ein0.empty())  // resume: the inflow of the state the caller saved
+                val = ein0[(size_t)b * p->F + f] - p->C[b] * p->T_ref / kFourPi;
             else  // diffuse reflection of the initial equilibrium e0(T_init)
                 val = p->C[b] * (T0[c] - p->T_ref) / kFourPi * p->side_out[side] / p->side_norm[side];
             e0[(size_t)b * F + f] = (real)val;
@@ -2292,6 +2372,27 @@ namespace bte {
 void set_global_error(const std::string &msg) { g_create_error = msg; }
 }  // namespace bte
 
+namespace {
+template <typename real>
+int get_state_t(bte_plan *p, double *T_out, double *ein_out) {
+    Workspace<real> &ws = ws_of<real>(p);
+    const int par = p->solved_iters & 1;   // the state set the next iteration would read
+    CK(p, cudaStreamSynchronize(p->stream));
+    if (T_out) CK(p, cudaMemcpy(T_out, ws.T[par].p, sizeof(double) * p->N, cudaMemcpyDefault));
+    if (ein_out && p->F > 0) {
+        const int B = p->B, F = p->F;
+        std::vector<real> e((size_t)B * F);
+        CK(p, cudaMemcpy(e.data(), ws.ein[par].p, sizeof(real) * e.size(), cudaMemcpyDeviceToHost));
+        std::vector<double> out(e.size());
+        for (int b = 0; b < B; ++b)
+            for (int f = 0; f < F; ++f)
+                out[(size_t)b * F + f] = (double)e[(size_t)b * F + f] + p->C[b] * p->T_ref / kFourPi;
+        CK(p, cudaMemcpy(ein_out, out.data(), sizeof(double) * out.size(), cudaMemcpyDefault));
+    }
+    return BTE_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *bte_version(void) { return "libbte 0.1 (sm_103a)"; }
@@ -2306,6 +2407,43 @@ void bte_default_opts(bte_solve_opts *o) {
     o->Q_amp = 1.0;
     o->poll_every = 32;
 }
+
+namespace {
+// Debug mode: every index table of a plan checked against its extent before
+// upload (the message of the first violation, or null).
+const char *validate_tables(const bte_plan *p) {
+    const long long N = p->N;
+    const int F = p->F, D = p->D;
+    if ((long long)p->face_cell.size() != F || (int)p->face_side.size() != F || (int)p->face_kind.size() != F)
+        return "face table sizes differ from the face count";
+    for (int f = 0; f < F; ++f) {
+        if (p->face_cell[f] < 0 || p->face_cell[f] >= N || !p->mask[p->face_cell[f]]) return "face cell outside the solid";
+        if (p->face_side[f] < 0 || p->face_side[f] >= 2 * p->dim) return "face side outside 0 .. 2 dim";
+        if (p->face_kind[f] < 0 || p->face_kind[f] > 2) return "face kind outside 0 .. 2";
+    }
+    for (long long c = 0; c < N; ++c) {
+        const int base = p->cellinfo[c].x, flags = p->cellinfo[c].y;
+        const unsigned bm = ((unsigned)flags >> kSideShift) & 63u;
+        if (base < 0 || base + __builtin_popcount(bm) > F) return "cell face base outside the face table";
+        for (int side = 0; side < 6; ++side) {
+            if (!((bm >> side) & 1u)) continue;
+            const int f = face_of(base, flags, side);
+            if (p->face_cell[f] != c || p->face_side[f] != side) return "cell face index does not point at its face";
+        }
+    }
+    for (int v : p->wall_face)
+        if (v < -1 || v >= F) return "wall face index outside the face table";
+    std::vector<int> seen(D, 0);
+    for (int d : p->perm) {
+        if (d < 0 || d >= D || seen[d]++) return "direction permutation is not a permutation";
+    }
+    for (int v : p->sidx)
+        if (v < -1 || v >= p->Fs) return "specular face index outside 0 .. Fs";
+    for (int v : p->mirror)
+        if (v < -1 || v >= D) return "mirror direction outside 0 .. D";
+    return nullptr;
+}
+}  // namespace
 
 int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands, const bte_quad *quad,
                const bte_bcs *bcs, const double *q_profile, bte_plan **out) {
@@ -2326,6 +2464,8 @@ int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands, c
             return fail(nullptr, _e == cudaErrorMemoryAllocation ? BTE_ENOMEM : BTE_ECUDA,                      \
                         std::string(#expr) + ": " + cudaGetErrorString(_e));                                    \
     } while (0)
+    if (debug_mode())
+        if (const char *m = validate_tables(p.get())) return fail(nullptr, BTE_ECORRUPT, std::string("debug mode: ") + m);
     CKC(upload(p->d_cell, p->cellinfo));
     CKC(upload(p->d_face_cell, p->face_cell));
     CKC(upload(p->d_face_side, p->face_side));
@@ -2360,6 +2500,7 @@ int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out
     if (!o->T_init && !(o->T_init_uniform > 0.0)) return fail(p, BTE_EINVAL, "T_init_uniform must be > 0");
     if (!std::isfinite(o->Q_amp)) return fail(p, BTE_EINVAL, "Q_amp must be finite");
     if (o->Q_amp_each) return fail(p, BTE_EINVAL, "Q_amp_each is for batched solves");
+    if (o->ein_init && !o->T_init) return fail(p, BTE_EINVAL, "ein_init resumes a state: it needs T_init");
     if (o->T_wall)
         for (int f = 0; f < 6; ++f)
             if (f / 2 < p->dim && p->bc_type[f] == BTE_BC_ISOTHERMAL && (!(o->T_wall[f] > 0) || !std::isfinite(o->T_wall[f])))
@@ -2377,7 +2518,7 @@ int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out
     else
         rc = fail(p, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
     p->xmode = 0;
-    return rc;
+    return guard_rc(p, rc);
 }
 
 int bte_adjoint_ex(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Twall,
@@ -2393,7 +2534,7 @@ int bte_adjoint_ex(bte_plan *p, const double *dJ_dT, double tol, int max_iter, d
                        ? adjoint_t<float>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, g_L, st)
                        : adjoint_t<double>(p, dJ_dT, tol, max_iter, g_tau, g_Twall, g_Qamp, g_L, st);
     p->want_glen = false;
-    return rc;
+    return guard_rc(p, rc);
 }
 
 int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Twall,
@@ -2430,7 +2571,17 @@ int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, 
     p->cur_inv_dt = 0.0;
     p->forced_T_ref = NAN;
     p->solved = false;   // no adjoint-ready state after a transient run
-    return rc;
+    return guard_rc(p, rc);
+}
+
+
+int bte_face_count(const bte_plan *p) { return p ? p->F : BTE_EINVAL; }
+
+int bte_get_state(bte_plan *p, double *T_out, double *ein_out) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (!p->solved || p->solved_iters < 1) return fail(p, BTE_ESTATE, "bte_get_state needs a preceding bte_solve");
+    return p->solved_precision == BTE_FP32 ? get_state_t<float>(p, T_out, ein_out)
+                                           : get_state_t<double>(p, T_out, ein_out);
 }
 
 int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep) {
@@ -2439,6 +2590,15 @@ int bte_profile_sweep(bte_plan *p, int reps, double *ms_per_sweep) {
     if (!p->solved || p->solved_iters < 1) return fail(p, BTE_ESTATE, "bte_profile_sweep needs a preceding bte_solve");
     if (p->solved_precision == BTE_FP32) return profile_t<float>(p, reps, ms_per_sweep);
     return profile_t<double>(p, reps, ms_per_sweep);
+}
+
+int bte_debug_overwrite_guard(bte_plan *p) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (!debug_mode() || !p->d_status.guarded) return fail(p, BTE_ESTATE, "bte_debug_overwrite_guard: debug mode is off");
+    // a host-side write into the allocation, just past the buffer's end
+    const cudaError_t e = cudaMemset(static_cast<char *>(p->d_status.p) + p->d_status.bytes, 0, 1);
+    if (e != cudaSuccess) return fail(p, BTE_ECUDA, cudaGetErrorString(e));
+    return cudaDeviceSynchronize() == cudaSuccess ? BTE_OK : fail(p, BTE_ECUDA, "synchronisation failed");
 }
 
 int bte_debug_set_wait_limit(bte_plan *p, long long polls) {
@@ -2550,15 +2710,22 @@ int bte_batch_solve(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_s
     if (!bt) return bfail(nullptr, BTE_EINVAL, "batch is null");
     if (!o || !T_out) return bfail(bt, BTE_EINVAL, "opts and T_out are required");
     if (o->max_iter < 1) return bfail(bt, BTE_EINVAL, "max_iter must be >= 1");
-    if (o->T_init) return bfail(bt, BTE_EINVAL, "bte_batch_solve: use T_init_uniform");
+    if (o->T_init || o->ein_init) return bfail(bt, BTE_EINVAL, "bte_batch_solve: use T_init_uniform (no T_init, ein_init)");
     if (o->face_order == 2) return bfail(bt, BTE_EINVAL, "bte_batch_solve: step faces only (face_order 0 or 1)");
     if (!std::isfinite(o->Q_amp)) return bfail(bt, BTE_EINVAL, "Q_amp must be finite");
     if (o->Q_amp_each)
         for (int i = 0; i < bt->n; ++i)
             if (!std::isfinite(o->Q_amp_each[i])) return bfail(bt, BTE_EINVAL, "Q_amp_each must be finite");
-    if (o->precision == BTE_FP32) return batch_solve_t<float>(bt, o, T_out, st, bs);
-    if (o->precision == BTE_FP64) return batch_solve_t<double>(bt, o, T_out, st, bs);
-    return bfail(bt, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+    int rc;
+    if (o->precision == BTE_FP32)
+        rc = batch_solve_t<float>(bt, o, T_out, st, bs);
+    else if (o->precision == BTE_FP64)
+        rc = batch_solve_t<double>(bt, o, T_out, st, bs);
+    else
+        return bfail(bt, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+    if (debug_mode() && check_guards() != 0)
+        return bfail(bt, BTE_ECORRUPT, "debug mode: a device buffer's guard words were overwritten");
+    return rc;
 }
 
 int bte_batch_set_sweep_timing(bte_batch *bt, int on) {
