@@ -314,6 +314,41 @@ int bte_get_state(bte_plan *p, double *T_out, double *ein_out);
 int bte_face_count(const bte_plan *p);
 
 /*
+ * Sharded solves of one instance (bands split over ranks, one process per
+ * GPU).  In the paper's outer iteration (Methods, steps 1-4) the sweeps of
+ * different bands are independent given T, and a band's diffuse inflow
+ * depends only on that band's own face sums; the temperature update needs,
+ * per cell, the sum over all bands of the band-weighted direction sums
+ * (Eq. updatee0_t).  So every rank holds a plan of the whole problem, sweeps
+ * its own bands [b0, b1) and forms their weighted sums W (N doubles); the
+ * ranks add their W (one FP64 allreduce per iteration, done by the caller);
+ * every rank then forms the same T.  Iterating bte_shard_sweep, the
+ * allreduce and bte_shard_apply until eps_T < tol reproduces bte_solve up to
+ * rounding (the band sums are combined in another order).
+ *
+ * bte_shard_begin -- o: as for bte_solve (precision, T_init / T_init_uniform,
+ *   ein_init, tau, T_wall, Q_amp, tile options; tol, max_iter and poll_every
+ *   are the caller's loop's).  Sets the initial state (T_ref, the inflow) and
+ *   the tile (a previous solve's autotuned tile in this precision, else the
+ *   first candidate).  Every rank must pass the same options.  Not for
+ *   specular faces or face_order 2 (BTE_EINVAL).  The plan holds no
+ *   adjoint-ready state afterwards.
+ * bte_shard_sweep -- one sweep of bands [b0, b1) (0 <= b0 < b1 <= B) from the
+ *   current state; W_out (N doubles, host or device) receives, per cell, the
+ *   sum over those bands of the band-weighted direction sums (zero in void
+ *   cells); those bands' next inflow is kept in the plan.
+ * bte_shard_apply -- W (N doubles, host or device): the sum of every rank's
+ *   W_out.  Forms T^{n+1} (to T_out, N doubles, host or device, or NULL) and
+ *   eps_T (to *eps_T, or NULL) and makes it the current state.  BTE_ENUMERIC
+ *   for a non-finite eps_T.
+ * Each returns BTE_OK, BTE_EINVAL, BTE_ESTATE (sweep or apply before begin)
+ * or BTE_ECUDA.
+ */
+int bte_shard_begin(bte_plan *p, const bte_solve_opts *o);
+int bte_shard_sweep(bte_plan *p, int b0, int b1, double *W_out);
+int bte_shard_apply(bte_plan *p, const double *W, double *T_out, double *eps_T);
+
+/*
  * bte_set_sweep_timing -- every >= 1: every following bte_solve / bte_adjoint
  * brackets the sweep launch of every `every`-th source iteration (counted
  * within each convergence poll interval, whose first iteration is always

@@ -38,7 +38,7 @@ EXPORTS = ["bte_create", "bte_solve", "bte_adjoint", "bte_destroy", "bte_last_er
            "bte_set_sweep_timing", "bte_eps_T_noalloc", "bte_batch_create", "bte_batch_solve",
            "bte_batch_destroy", "bte_batch_last_error", "bte_batch_set_sweep_timing", "bte_adjoint_ex",
            "bte_transient", "bte_debug_set_wait_limit", "bte_get_state", "bte_debug_overwrite_guard",
-           "bte_face_count"]
+           "bte_face_count", "bte_shard_begin", "bte_shard_sweep", "bte_shard_apply"]
 
 
 class Grid(ctypes.Structure):
@@ -149,6 +149,12 @@ def load(path: str = LIB_PATH):
     lib.bte_debug_overwrite_guard.restype = ip
     lib.bte_face_count.argtypes = [vp]
     lib.bte_face_count.restype = ip
+    lib.bte_shard_begin.argtypes = [vp, ctypes.POINTER(SolveOpts)]
+    lib.bte_shard_begin.restype = ip
+    lib.bte_shard_sweep.argtypes = [vp, ip, ip, vp]
+    lib.bte_shard_sweep.restype = ip
+    lib.bte_shard_apply.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.bte_shard_apply.restype = ip
     _lib = lib
     return lib
 
@@ -343,6 +349,32 @@ class Plan:
         rc = self._lib.bte_set_sweep_timing(self._h, int(every))
         if rc != BTE_OK:
             raise BTEError(rc, self.error())
+
+    def shard_begin(self, precision=BTE_FP32, T_init=None, T_init_uniform=None, Q_amp=None, tau=None,
+                    T_wall=None, stream=None, tile_kind=0, dirs_per_lane=0, dirs_per_cta=0, source_staging=0,
+                    warps_z=0, lane_axis=0, ein_init=None):
+        """bte_shard_begin: the initial state of a band-sharded solve."""
+        keep = []
+        o = self._opts(precision, 0.0, 1, T_init, T_init_uniform, Q_amp, tau, T_wall, stream, 32, dirs_per_lane,
+                       False, tile_kind, dirs_per_cta, source_staging, warps_z, lane_axis, 1, keep, ein_init)
+        rc = self._lib.bte_shard_begin(self._h, ctypes.byref(o))
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
+
+    def shard_sweep(self, b0, b1, W_out):
+        """bte_shard_sweep: sweep bands [b0, b1); W_out [N] receives their
+        band-weighted sums."""
+        rc = self._lib.bte_shard_sweep(self._h, int(b0), int(b1), _addr(W_out))
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
+
+    def shard_apply(self, W, T_out=None):
+        """bte_shard_apply: T^{n+1} from W (every band's sums); returns eps_T."""
+        eps = ctypes.c_double()
+        rc = self._lib.bte_shard_apply(self._h, _addr(W), _addr(T_out), ctypes.byref(eps))
+        if rc != BTE_OK:
+            raise BTEError(rc, self.error())
+        return eps.value
 
     def n_faces(self):
         """bte_face_count: the number of boundary faces F."""

@@ -84,6 +84,7 @@ struct SweepParams {
     int nx, ny, nz;
     int dim;                          // resolved axes
     int B, D, F, S, R;
+    int b0, nb;                       // bands b0 .. b0 + nb - 1 are swept (nb 0: all B; sharded solves)
     int Spad;                         // S rounded up to a multiple of 4
     int WY, WZ;                       // warps along y, warp groups along z
     long long N;                      // nx*ny*nz
@@ -147,6 +148,7 @@ template <typename real>
 struct Sweep2DParams {
     int nx, ny;
     int B, D, F, S;                   // S = number of chunks (face-sum sets)
+    int b0, nb;                       // bands b0 .. b0 + nb - 1 are swept (nb 0: all B; sharded solves)
     int Spad;                         // cell partial sets rounded up to a multiple of 4
     int warps_per_cta;
     int ring;                         // 1: warps of a chunk combine per-cell sums through shared-
@@ -209,6 +211,7 @@ template <typename real>
 struct Sweep3DParams {
     int nx, ny, nz;
     int B, D, F, S, R;                // S = direction subsets (cell and face-sum sets)
+    int b0, nb;                       // bands b0 .. b0 + nb - 1 are swept (nb 0: all B; sharded solves)
     int Spad;                         // S rounded up to a multiple of 4
     int WY, H;                        // warps along the row axis, warps along the plane axis
     int lane_axis;                    // row (lane) axis: 1 = y, 2 = z; planes along the other
@@ -286,6 +289,9 @@ struct UpdateParams {
     int *batch_done;                  // batched solves: instances converged so far (or null)
     int defer;                        // 1: write the block partials, set *fin.pending, no ticket
     int vec;                          // 1: 128-cell vector cell blocks (N a multiple of 4)
+    int ub0, ub1;                     // sharded solves: bands ub0 .. ub1 - 1 only (ub1 0: every band)
+    double *__restrict__ w_out;       // sharded solves: per-cell band-weighted sum over those bands
+                                      //   (sweep precision, as FP64) instead of T; null: a full update
     FinalizeParams fin;               // (defer) where the partials go
 };
 
@@ -320,6 +326,10 @@ constexpr int kSpecDW = 4;
 
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st);
+// Sharded solves: T from the band-weighted sums W of every band (summed over
+// the ranks), the residual and the iteration's finalization (scalar blocks).
+template <typename real>
+cudaError_t launch_apply(const UpdateParams<real> &p, const double *W, cudaStream_t st);
 // natural-order per-cell field -> skewed layout (both families)
 template <typename T>
 cudaError_t launch_skew(long long N, const SkewLayout &L, const T *src, T *dst, cudaStream_t st);

@@ -131,6 +131,7 @@ struct Workspace {
     DevBuf ein_fixed, part, fsum, e, gpart, phi, coef, invdiag, srck_f, srck_a, qb, cb4pi;
     DevBuf wgt_f, wgt_a, Kinv, scale_f, scale_a, msum, g, grad_out, inv_tt, qcoef, phi64, vws, qshift, q,
         eshift, tfwd_dummy;
+    DevBuf wsum;                       // sharded solves: per-cell band-weighted sums [N] (FP64)
     // direction subsets per tile width
     std::map<int, std::pair<std::vector<Subset>, std::vector<Subset>>> subsets;  // tile -> (fwd, adj)
     std::map<int, std::pair<DevBuf *, DevBuf *>> dsub;
@@ -214,6 +215,8 @@ struct bte_plan {
     bool solved = false;
     int solved_precision = -1;
     int solved_iters = 0;
+    // sharded solves (bte_shard_*): precision, tile, state set, iterations
+    int shard_prec = -1, shard_tile = 0, shard_par = 0, shard_iters = 0;
     int solved_tile = 0;
     int wall_stride = 1;
     std::vector<int> wall_face;
@@ -925,10 +928,12 @@ template <typename real>
 cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool adj, const real *tsrc,
                               const real *ein, bool store_e, bool use_done, cudaStream_t stream,
                               const FinalizeParams *fin = nullptr, const real *spec_in = nullptr,
-                              real *spec_out = nullptr) {
+                              real *spec_out = nullptr, int b0 = 0, int nb = 0) {
     const Tile tl = tile_of(tid);
     if (is_pipe3(tl.kind)) {
         Sweep3DParams<real> sp = sweep3d_params(p, ws, tid, adj);
+        sp.b0 = b0;
+        sp.nb = nb;
         sp.tsrc = skewed_source(ws, tsrc, pipe3_map(tl));
         if (!sp.tsrc) return cudaErrorInvalidValue;
         sp.ein = ein;
@@ -939,6 +944,8 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
     }
     if (tl.kind >= 1) {
         Sweep2DParams<real> sp = sweep2d_params(p, ws, tid, adj);
+        sp.b0 = b0;
+        sp.nb = nb;
         sp.tsrc = tsrc;
         sp.ein = ein;
         sp.store_e = store_e ? 1 : 0;
@@ -949,6 +956,8 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
         return launch_sweep2d<real>(sp, tl.dw, rowblock_rb(p), adj, stream);
     }
     SweepParams<real> sp = sweep_params(p, ws, tid, adj);
+    sp.b0 = b0;
+    sp.nb = nb;
     sp.tsrc = tsrc;
     sp.ein = ein;
     sp.store_e = store_e ? 1 : 0;
@@ -2372,6 +2381,102 @@ namespace bte {
 void set_global_error(const std::string &msg) { g_create_error = msg; }
 }  // namespace bte
 
+// ---------------------------------------------------------------------------
+// Sharded solves of one instance (bands split over ranks).  Every outer
+// iteration of the paper's solution procedure needs, per cell, the sum over
+// all bands of the band-weighted direction sums (the temperature update);
+// each band's sweep and its diffuse inflow depend only on T and on that
+// band.  So a rank sweeps its bands and forms their weighted sum W_r (and its
+// bands' next inflow), the ranks add their W_r (one FP64 allreduce of N
+// values per iteration), and every rank forms the same T from the sum.
+// ---------------------------------------------------------------------------
+template <typename real>
+int shard_begin_t(bte_plan *p, const bte_solve_opts *o) {
+    cudaStream_t stream = (cudaStream_t)o->stream;
+    Workspace<real> &ws = ws_of<real>(p);
+    int rc = ensure_workspace(p, ws);
+    if (rc) return rc;
+    p->cur_tau = p->tau;
+    if (o->tau) {
+        for (int b = 0; b < p->B; ++b)
+            if (!(o->tau[b] > 0.0) || !std::isfinite(o->tau[b])) return fail(p, BTE_EINVAL, "tau override must be > 0");
+        p->cur_tau.assign(o->tau, o->tau + p->B);
+    }
+    p->cur_Tw.assign(p->bc_T, p->bc_T + 6);
+    if (o->T_wall) p->cur_Tw.assign(o->T_wall, o->T_wall + 6);
+    p->cur_Q = o->Q_amp;
+    if ((rc = begin_state(p, o, ws, stream))) return rc;
+    if ((rc = upload_tables(p, ws))) return rc;
+    std::vector<int> cand = tile_candidates(p, (int)sizeof(real), o->tile_kind, o->dirs_per_lane, o->dirs_per_cta,
+                                            o->source_staging, o->warps_z, o->lane_axis);
+    if (cand.empty()) return fail(p, BTE_EINVAL, "no sweep tile supports this grid / tile request");
+    // the tile a solve of this plan autotuned in this precision, else the first candidate
+    int tid = cand[0];
+    if (p->solved_precision == (sizeof(real) == 4 ? BTE_FP32 : BTE_FP64) &&
+        std::find(cand.begin(), cand.end(), p->solved_tile) != cand.end())
+        tid = p->solved_tile;
+    if ((rc = ensure_subsets(p, ws, tid))) return rc;
+    CK(p, ws.wsum.ensure(sizeof(double) * p->N));
+    CK(p, cudaMemsetAsync(p->d_status.p, 0, sizeof(Status), stream));
+    CK(p, cudaMemsetAsync(p->d_counter.p, 0, sizeof(unsigned int), stream));
+    CK(p, cudaStreamSynchronize(stream));
+    p->stream = stream;
+    p->shard_prec = sizeof(real) == 4 ? BTE_FP32 : BTE_FP64;
+    p->shard_tile = tid;
+    p->shard_par = 0;
+    p->shard_iters = 0;
+    return BTE_OK;
+}
+
+template <typename real>
+int shard_sweep_t(bte_plan *p, int b0, int b1, double *W_out) {
+    Workspace<real> &ws = ws_of<real>(p);
+    cudaStream_t stream = p->stream;
+    const int par = p->shard_par, tid = p->shard_tile;
+    CK(p, launch_tile_sweep<real>(p, ws, tid, false, ws.tdev[par].template as<real>(), ws.ein[par].template as<real>(),
+                                  false, false, stream, nullptr, nullptr, nullptr, b0, b1 - b0));
+    UpdateParams<real> u = update_params(p, ws, tid, false, 0.0);
+    u.vec = 0;
+    u.defer = 0;
+    u.ignore_done = 1;
+    u.ub0 = b0;
+    u.ub1 = b1;
+    u.w_out = ws.wsum.template as<double>();
+    u.x_in = ws.T[par].template as<double>();
+    u.ein_out = ws.ein[par ^ 1].template as<real>();   // this rank's bands' next inflow
+    CK(p, launch_update<real>(u, stream));
+    CK(p, cudaMemcpyAsync(W_out, ws.wsum.p, sizeof(double) * p->N, cudaMemcpyDefault, stream));
+    CK(p, cudaStreamSynchronize(stream));
+    return BTE_OK;
+}
+
+template <typename real>
+int shard_apply_t(bte_plan *p, const double *W, double *T_out, double *eps_T) {
+    Workspace<real> &ws = ws_of<real>(p);
+    cudaStream_t stream = p->stream;
+    const int par = p->shard_par, tid = p->shard_tile;
+    CK(p, cudaMemcpyAsync(ws.wsum.p, W, sizeof(double) * p->N, cudaMemcpyDefault, stream));
+    UpdateParams<real> u = update_params(p, ws, tid, false, 0.0);
+    u.vec = 0;
+    u.defer = 0;
+    u.ignore_done = 1;
+    u.fin.nblocks = update_cell_block_count(p->N, false);
+    u.eps_hist = nullptr;
+    u.x_in = ws.T[par].template as<double>();
+    u.x_out = ws.T[par ^ 1].template as<double>();
+    u.xdev_out = ws.tdev[par ^ 1].template as<real>();
+    if (is_pipe3(tile_of(tid).kind)) u.xskew_out = ws.skt[pipe3_map(tile_of(tid))][par ^ 1].template as<real>();
+    CK(p, launch_apply<real>(u, ws.wsum.template as<double>(), stream));
+    CK(p, cudaMemcpyAsync(p->h_status, p->d_status.p, sizeof(Status), cudaMemcpyDeviceToHost, stream));
+    if (T_out) CK(p, cudaMemcpyAsync(T_out, ws.T[par ^ 1].p, sizeof(double) * p->N, cudaMemcpyDefault, stream));
+    CK(p, cudaStreamSynchronize(stream));
+    p->shard_par ^= 1;
+    ++p->shard_iters;
+    if (eps_T) *eps_T = p->h_status->last[0];
+    if (!std::isfinite(p->h_status->last[0])) return fail(p, BTE_ENUMERIC, "NaN or Inf in the sharded temperature");
+    return BTE_OK;
+}
+
 namespace {
 template <typename real>
 int get_state_t(bte_plan *p, double *T_out, double *ein_out) {
@@ -2576,6 +2681,49 @@ int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, 
 
 
 int bte_face_count(const bte_plan *p) { return p ? p->F : BTE_EINVAL; }
+
+int bte_shard_begin(bte_plan *p, const bte_solve_opts *o) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (!o) return fail(p, BTE_EINVAL, "opts are required");
+    if (!o->T_init && !(o->T_init_uniform > 0.0)) return fail(p, BTE_EINVAL, "T_init_uniform must be > 0");
+    if (!std::isfinite(o->Q_amp)) return fail(p, BTE_EINVAL, "Q_amp must be finite");
+    if (o->Q_amp_each) return fail(p, BTE_EINVAL, "Q_amp_each is for batched solves");
+    if (o->ein_init && !o->T_init) return fail(p, BTE_EINVAL, "ein_init resumes a state: it needs T_init");
+    if (o->face_order == 2) return fail(p, BTE_EINVAL, "sharded solves use step faces (face_order 0 or 1)");
+    if (p->Fs > 0) return fail(p, BTE_EINVAL, "sharded solves: specular faces carry per-direction state");
+    if (o->tile_kind < 0 || o->tile_kind > 3) return fail(p, BTE_EINVAL, "tile_kind must be 0, 1, 2 or 3");
+    p->solved = false;
+    p->xmode = 0;
+    p->cur_inv_dt = 0.0;
+    p->forced_T_ref = NAN;
+    p->shard_prec = -1;
+    int rc;
+    if (o->precision == BTE_FP32)
+        rc = shard_begin_t<float>(p, o);
+    else if (o->precision == BTE_FP64)
+        rc = shard_begin_t<double>(p, o);
+    else
+        rc = fail(p, BTE_EINVAL, "precision must be BTE_FP32 or BTE_FP64");
+    return guard_rc(p, rc);
+}
+
+int bte_shard_sweep(bte_plan *p, int b0, int b1, double *W_out) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (p->shard_prec < 0) return fail(p, BTE_ESTATE, "bte_shard_sweep needs bte_shard_begin");
+    if (!W_out || b0 < 0 || b1 <= b0 || b1 > p->B) return fail(p, BTE_EINVAL, "need 0 <= b0 < b1 <= B and W_out");
+    const int rc = p->shard_prec == BTE_FP32 ? shard_sweep_t<float>(p, b0, b1, W_out)
+                                             : shard_sweep_t<double>(p, b0, b1, W_out);
+    return guard_rc(p, rc);
+}
+
+int bte_shard_apply(bte_plan *p, const double *W, double *T_out, double *eps_T) {
+    if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
+    if (p->shard_prec < 0) return fail(p, BTE_ESTATE, "bte_shard_apply needs bte_shard_begin");
+    if (!W) return fail(p, BTE_EINVAL, "W is required");
+    const int rc = p->shard_prec == BTE_FP32 ? shard_apply_t<float>(p, W, T_out, eps_T)
+                                             : shard_apply_t<double>(p, W, T_out, eps_T);
+    return guard_rc(p, rc);
+}
 
 int bte_get_state(bte_plan *p, double *T_out, double *ein_out) {
     if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");

@@ -352,7 +352,7 @@ __device__ __forceinline__ void sweep_body(const SweepParams<real> &P, const int
 template <typename real, int DW, int LZ, bool Z, bool ADJ, bool EXT = false>
 __global__ void __launch_bounds__(SweepTile<DW, LZ, Z>::kMaxThreads)
 sweep_kernel(const __grid_constant__ SweepParams<real> P) {
-    sweep_body<real, DW, LZ, Z, ADJ, EXT>(P, blockIdx.x, blockIdx.y);
+    sweep_body<real, DW, LZ, Z, ADJ, EXT>(P, blockIdx.x, blockIdx.y + P.b0);
 }
 
 // Batched form for 2D instances (forward): blockIdx.z = the instance among
@@ -386,7 +386,7 @@ cudaError_t launch_sweep_t(const SweepParams<real> &p, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid(p.S, p.B);
+    dim3 grid(p.S, p.nb ? p.nb : p.B);
     kern<<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
 }

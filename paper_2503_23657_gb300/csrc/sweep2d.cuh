@@ -163,7 +163,7 @@ sweep2d_kernel(const __grid_constant__ Sweep2DParams<real> P) {
     real *s_wy = s_wx + P.ny;                                        // [nx] upwind y-wall values
 
     const int s = blockIdx.x;  // chunk = partial set
-    const int b = blockIdx.y;
+    const int b = blockIdx.y + P.b0;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nthr = blockDim.x;
@@ -339,7 +339,7 @@ cudaError_t launch_sweep2d_t(const Sweep2DParams<real> &p, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<dim3(p.S, p.B), threads, smem, st>>>(p);
+    kern<<<dim3(p.S, p.nb ? p.nb : p.B), threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -354,7 +354,7 @@ __device__ __forceinline__ void sweep2dp_body(const Sweep2DParams<real> &P, cons
 template <typename real, int DW, int K, bool PHI, bool STORE_E, bool STAGE>
 __global__ void __launch_bounds__(kPipeMaxThreads, 1)
 sweep2dp_kernel(const __grid_constant__ Sweep2DParams<real> P) {
-    sweep2dp_body<real, DW, K, PHI, STORE_E, STAGE>(P, blockIdx.x, blockIdx.y);
+    sweep2dp_body<real, DW, K, PHI, STORE_E, STAGE>(P, blockIdx.x, blockIdx.y + P.b0);
 }
 
 // Batched form: blockIdx.z picks the instance (through `inst`, which lists
@@ -388,7 +388,7 @@ cudaError_t launch_sweep2dp_v(const Sweep2DParams<real> &p, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    return launch_pdl(kern, dim3(p.S, p.B), dim3(threads), smem, st, p);
+    return launch_pdl(kern, dim3(p.S, p.nb ? p.nb : p.B), dim3(threads), smem, st, p);
 }
 
 template <typename real, int DW, int K, bool PHI, bool STAGE>

@@ -184,7 +184,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     __shared__ int s_stop;
 
     const int s = blockIdx.x;
-    const int b = blockIdx.y;
+    const int b = blockIdx.y + P.b0;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int WY = P.WY, H = P.H;
@@ -588,7 +588,7 @@ cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    return launch_pdl(kern, dim3(p.S, p.B), dim3(threads), smem, st, p);
+    return launch_pdl(kern, dim3(p.S, p.nb ? p.nb : p.B), dim3(threads), smem, st, p);
 }
 
 // the source-profile term only in forward sweeps with a source; e only when

@@ -96,6 +96,7 @@ __device__ __forceinline__ void update_faces(const UpdateParams<real> &P, const 
     if (fb >= (long long)P.F * P.B) return;
     const int b = (int)(fb / P.F);
     const int f = (int)(fb % P.F);
+    if (P.ub1 != 0 && (b < P.ub0 || b >= P.ub1)) return;   // sharded: another rank's band
     const int side = P.face_side[f];
     const int a = side >> 1;
     const bool plus = side & 1;
@@ -121,7 +122,7 @@ __device__ __forceinline__ void update_faces(const UpdateParams<real> &P, const 
 // The new value of cell c (region r, slot total tot, old value x_old): writes
 // it and returns its contribution to the residual (squared change, maximum).
 template <typename real>
-__device__ __forceinline__ void update_cell_value(const UpdateParams<real> &P, long long c, int r, real tot,
+__device__ __forceinline__ void update_cell_value(const UpdateParams<real> &P, long long c, int r, double tot,
                                                   double x_old, double &ss, double &mx) {
     ss = 0.0;
     mx = -INFINITY;
@@ -129,12 +130,12 @@ __device__ __forceinline__ void update_cell_value(const UpdateParams<real> &P, l
         double xn;
         real xd;
         if (!P.adjoint) {
-            const double dev = (double)tot * P.Kinv[r - 1];
+            const double dev = tot * P.Kinv[r - 1];
             xn = P.T_ref + dev;
             xd = (real)dev;
             mx = xn;
         } else {
-            xn = (P.g[c] + (double)tot) * P.Kinv[r - 1];
+            xn = (P.g[c] + tot) * P.Kinv[r - 1];
             xd = (real)xn;
             mx = fabs(xn);
         }
@@ -240,6 +241,25 @@ __device__ __forceinline__ void update_cells(const UpdateParams<real> &P, const 
         s1 += tree8(a1);
     }
     if (stop) return;  // converged earlier: this replayed iteration does nothing
+    if (P.w_out) {
+        // sharded solves: this rank's bands only, the band-weighted sum as
+        // the output (the same slot and fma order over the bands it has)
+        real accp = real(0);
+        if (r != 0) {
+            const real *wr = P.wgtr + (r - 1) * P.B;
+            for (int b = P.ub0 + ty; b < P.ub1; b += kBandSlots)
+                accp = fma(sum_sets(P.part + (long long)b * P.Spad * P.N + cc, P.S, P.N), wr[b], accp);
+        }
+        sband[ty][tx] = accp;
+        __syncthreads();
+        if (ty == 0 && cin) {
+            real tot = real(0);
+#pragma unroll
+            for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
+            P.w_out[c] = (double)tot;
+        }
+        return;
+    }
     real acc = real(0);
     if (r != 0) {
         const real *wr = P.wgtr + (r - 1) * P.B;
@@ -256,7 +276,7 @@ __device__ __forceinline__ void update_cells(const UpdateParams<real> &P, const 
         real tot = real(0);
 #pragma unroll
         for (int y = 0; y < kBandSlots; ++y) tot += sband[y][tx];
-        update_cell_value(P, c, r, tot, x_old, ss, mx);
+        update_cell_value(P, c, r, (double)tot, x_old, ss, mx);
     }
     fin_warp_reduce(ss, mx);
     update_block_tail(P, cb, cell_blocks, ss, mx, it_prev, &is_last);
@@ -351,7 +371,7 @@ __device__ __forceinline__ void update_cells_vec(const UpdateParams<real> &P, co
         real tot = real(0);
 #pragma unroll
         for (int y = 0; y < kBandSlots; ++y) tot += sslot[y][t];
-        update_cell_value(P, c, P.cell[c].y & kRegionMask, tot, P.x_in[c], ss, mx);
+        update_cell_value(P, c, P.cell[c].y & kRegionMask, (double)tot, P.x_in[c], ss, mx);
     }
     fin_warp_reduce(ss, mx);
     if (lane == 0) {
@@ -423,9 +443,34 @@ cudaError_t launch_finalize(const UpdateParams<real> *params, int n, cudaStream_
     return cudaGetLastError();
 }
 
+// Sharded solves: one thread per cell, 32 cells per block (the scalar cell
+// blocks' count, so the finalization reduces the same block partials): the
+// same per-cell step as the update from W (every band's weighted sum), then
+// the residual and the ticketed finalization.
+template <typename real>
+__global__ void __launch_bounds__(kCellsPerBlock) apply_kernel(const __grid_constant__ UpdateParams<real> P,
+                                                               const double *__restrict__ W) {
+    __shared__ int is_last;
+    const int cb = blockIdx.x;
+    const long long c = (long long)cb * kCellsPerBlock + threadIdx.x;
+    const int it_prev = (threadIdx.x == 0) ? *P.iter : 0;
+    double ss = 0.0, mx = -INFINITY;
+    if (c < P.N) update_cell_value(P, c, P.cell[c].y & kRegionMask, W[c], P.x_in[c], ss, mx);
+    fin_warp_reduce(ss, mx);
+    update_block_tail(P, cb, (int)gridDim.x, ss, mx, it_prev, &is_last);
+}
+
+template <typename real>
+cudaError_t launch_apply(const UpdateParams<real> &p, const double *W, cudaStream_t st) {
+    if (p.vec || p.defer || p.w_out) return cudaErrorInvalidValue;
+    apply_kernel<real><<<update_cell_blocks(p.N, false), kCellsPerBlock, 0, st>>>(p, W);
+    return cudaGetLastError();
+}
+
 template <typename real>
 cudaError_t launch_update(const UpdateParams<real> &p, cudaStream_t st) {
     const int blocks = update_face_blocks(p.F, p.B) + update_cell_blocks(p.N, p.vec != 0);
+    if (p.w_out && p.vec) return cudaErrorInvalidValue;   // partial updates use the scalar blocks
     if (p.vec) {
         if (p.N % 4 != 0) return cudaErrorInvalidValue;
         return launch_pdl(update_kernel<real, true>, dim3(blocks), dim3(kUpdThreads), 0, st, p);
@@ -604,6 +649,8 @@ cudaError_t launch_grad(const GradParams<real> &g, cudaStream_t st) {
 
 template cudaError_t launch_update<float>(const UpdateParams<float> &, cudaStream_t);
 template cudaError_t launch_update<double>(const UpdateParams<double> &, cudaStream_t);
+template cudaError_t launch_apply<float>(const UpdateParams<float> &, const double *, cudaStream_t);
+template cudaError_t launch_apply<double>(const UpdateParams<double> &, const double *, cudaStream_t);
 template cudaError_t launch_update_batch<float>(const UpdateParams<float> *, const int2 *, int, cudaStream_t);
 template cudaError_t launch_finalize<float>(const UpdateParams<float> *, int, cudaStream_t);
 template cudaError_t launch_finalize<double>(const UpdateParams<double> *, int, cudaStream_t);
