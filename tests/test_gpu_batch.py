@@ -196,3 +196,25 @@ def test_batch_per_instance_source_amplitudes(bte, mixed):
             assert np.abs(Ti - ref["T"])[act].max() < 1e-12 * np.abs(ref["T"][act]).max(), (i, p.name)
     with pytest.raises(ValueError):
         batch.solve(np.zeros(n), Q_amp=[1.0, 2.0])
+
+
+def test_full_ensemble_sampled_instances_vs_oracle(bte):
+    """The whole 256-instance ensemble (uneven squares n 32..160, 15 bands x
+    64 directions) batched for 10 iterations in FP32; the smallest, the
+    median and the largest instance against the oracle's 10 iterations."""
+    probs = bi.ensemble_2d()
+    plans = [bte.Plan(p) for p in probs]
+    batch = bte.Batch(plans)
+    k = 10
+    T = np.zeros(sum(p.n_cells for p in probs))
+    rc, st, bs = batch.solve(T, precision=0, tol=0.0, max_iter=k)
+    order = np.argsort([p.n_cells for p in probs], kind="stable")
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        p = probs[i]
+        ref = oracle.solve(p, max_iter=k, tol=0.0)
+        Ti = T[batch.offsets[i]:batch.offsets[i + 1]]
+        assert st[i]["iterations"] == k
+        assert np.abs(Ti - ref["T"]).max() < 1e-5 * np.abs(ref["T"]).max(), (i, p.name)
+    batch.close()
+    for pl in plans:
+        pl.close()
