@@ -779,8 +779,14 @@ SweepParams<real> sweep_params(bte_plan *p, Workspace<real> &ws, int tid, bool a
 }
 
 // An update runs 128-cell vector blocks when the cell count is a multiple
-// of 4 (one-plan and batched alike; both forms give the same values).
-inline bool upd_vec(const bte_plan *p) { return p->N % 4 == 0; }
+// of 4 (both forms give the same values).  A one-plan update takes them only
+// when they are at least two per SM (a small grid fills the GPU better with
+// the scalar 32-cell blocks); batched instances share one launch, so theirs
+// always do.
+inline bool upd_vec_batch(const bte_plan *p) { return p->N % 4 == 0; }
+inline bool upd_vec(const bte_plan *p) {
+    return upd_vec_batch(p) && p->N >= 2LL * std::max(p->sm_count, 1) * 128;
+}
 
 // Convergence bookkeeping of the plan's solve (forward: with eps history).
 FinalizeParams fin_params(bte_plan *p, double tol, bool adj) {
@@ -2107,6 +2113,7 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 sp.done = &st_all[i].done;
                 sp.status = &st_all[i].status;
                 FinalizeParams fin = fin_params(p, tol, false);
+                fin.nblocks = update_cell_block_count(p->N, upd_vec_batch(p));
                 fin.done = &st_all[i].done;
                 fin.iter = &st_all[i].iter;
                 fin.status = &st_all[i].status;
@@ -2116,6 +2123,7 @@ int batch_upload_params(bte_batch *bt, BatchState<real> &bs, const std::vector<i
                 sp.fin = fin;
                 sw[i] = sp;
                 UpdateParams<real> u = update_params(p, ws, tid, false, tol);
+                u.vec = upd_vec_batch(p) ? 1 : 0;
                 u.x_in = ws.T[par].template as<double>();
                 u.x_out = ws.T[par ^ 1].template as<double>();
                 u.xdev_out = ws.tdev[par ^ 1].template as<real>();
@@ -2830,7 +2838,7 @@ int bte_batch_create(int n, bte_plan *const *plans, bte_batch **out) {
         const bte_batch::Cls &c = bt->classes[ci];
         for (int q = 0; q < c.count; ++q) {
             const int i = bt->inst[c.begin + q];
-            const int nb = update_blocks(plans[i]->N, plans[i]->F, plans[i]->B, upd_vec(plans[i]));
+            const int nb = update_blocks(plans[i]->N, plans[i]->F, plans[i]->B, upd_vec_batch(plans[i]));
             for (int k = 0; k < nb; ++k) table.push_back(make_int2(i, k));
         }
     }
