@@ -517,10 +517,18 @@ def run_single(p, ctx):
               "parallelism": "replicas" if ctx["ws"] > 1 else "single",
               "store_e_every_iter": bool(args.store_e_every_iter), "tile": tile}
     line = base_line(ctx, value, t_max, "f64" if ctx["fp64"] else "f32", config)
+    # the stopping measure eps_T = RMS(dT)/T_max understates the change when
+    # the temperature range is small: the same RMS change over T_max - T_min
+    act = torch.as_tensor(p.mask > 0, device="cuda")
+    Ta = T[act]
+    t_range = float(Ta.max() - Ta.min())
+    dT_rms = fstats[-1]["eps_T"] * fstats[-1]["T_max"]
     line.update({"fwd_iterations": fstats[-1]["iterations"],
                  "adj_iterations": astats[-1]["iterations"] if astats else None,
                  "fwd_time_to_converge_ms": fwd_ms, "fwd_updates_per_s": fwd_ups,
-                 "step_ms_median": statistics.median(times)})
+                 "step_ms_median": statistics.median(times),
+                 "eps_T_final": fstats[-1]["eps_T"],
+                 "dT_rms_over_T_range_final": dT_rms / t_range if t_range > 0 else None})
     line.update(extra)
     line.update({
         "roofline": roofline, "cpu_baseline": ctx["cpu"],
@@ -632,7 +640,10 @@ def run_ensemble(probs, ctx):
         if i > 0:
             e2e_units += sum(s["iterations"] * u for s, u in zip(st2, per_iter))
             e2e_t += t1 - t0
+    # effective Knudsen number of each instance, (sum C v^2 tau / sum C v) / L (descriptive)
+    kn = sorted(float(np.sum(q.C * q.v ** 2 * q.tau) / np.sum(q.C * q.v) / q.length[0]) for q in probs)
     config = {"workload": ctx["name"], "instances_this_rank": len(probs), "cells_this_rank": n, "bands": probs[0].B,
+              "Kn_eff_min_median_max": [kn[0], kn[len(kn) // 2], kn[-1]],
               "directions": probs[0].D, "tol_eps_T": tol, "size_classes": bs["classes"],
               "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)",
               "parallelism": "instances sharded over ranks" if ctx["ws"] > 1 else "single",
