@@ -148,7 +148,8 @@ typedef struct {
                                2 = row-block kernel (unmasked 1D/2D, one region);
                                3 = row-pipeline kernel (unmasked 1D/2D, one region; on 3D
                                    grids the plane-pipeline kernel: masks and several
-                                   regions allowed, FP32 only) */
+                                   regions allowed; FP32 with 2, 4 or 8 directions per lane,
+                                   FP64 with 2 or 4) */
     int dirs_per_cta;       /* row kernels: directions per CTA (0 = autotuned) */
     int source_staging;     /* row-pipeline kernel: 0 = autotuned, 1 = per-cell source staged in
                                shared memory, 2 = read ahead from global memory */
