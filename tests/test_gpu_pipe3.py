@@ -185,6 +185,32 @@ def test_adjoint_passes_matches_general(bte):
         assert o[2] == pytest.approx(out[0][2], rel=1e-4)
 
 
+def test_fp64_adjoint_gradients_match_oracle(bte):
+    """FP64 adjoint through the plane pipeline (rows along y and along z, two
+    warps along the planes: five or six passes), whose final pass runs the
+    transposed sweep and then its gradient form, on a masked two-region grid
+    with a source: dJ/dtau, dJ/dT_wall and dJ/dQ_amp within 1e-9 of the
+    oracle's FP64 adjoint (1e-8 for the tiny dJ/dQ_amp), like the general
+    kernel's."""
+    p = bi.tiny(3, n=(14, 10, 12), B=2, masked=True, diffuse=(0, 3, 5), source=True, two_regions=True,
+                n_polar=2, n_az=16)
+    act = np.flatnonzero(p.mask)
+    g = np.zeros(p.n_cells)
+    g[act[[3, 50, 300, act.size - 7]]] = [1.0, -0.5, 0.25, 2.0]
+    r = oracle.solve(p, max_iter=100000, tol=1e-13)
+    a = oracle.adjoint(p, r["e"], r["T"], g, max_iter=100000, tol=1e-13)
+    plan = bte.Plan(p)
+    for kind, axis in ((1, 0), (3, 1), (3, 2)):
+        T = np.zeros(p.n_cells)
+        rc, st = plan.solve(T, precision=bte.BTE_FP64, tol=1e-13, max_iter=100000, tile_kind=kind,
+                            dirs_per_lane=4, lane_axis=axis, warps_z=2 if kind == 3 else 0)
+        assert st["lane_axis"] == axis and st["tile_kind"] == (3 if kind == 3 else 1)
+        rc, g_tau, g_Tw, g_Q, sa = plan.adjoint(g, tol=1e-13, max_iter=100000)
+        np.testing.assert_allclose(g_tau, a["g_tau"], rtol=1e-9)
+        np.testing.assert_allclose(g_Tw, a["g_Tw"], rtol=1e-9, atol=1e-9 * np.abs(a["g_Tw"]).max())
+        assert g_Q == pytest.approx(a["g_Q"], rel=1e-8)
+
+
 @pytest.mark.parametrize("name,kw", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("dw", [2, 4])
 @pytest.mark.parametrize("axis", [1, 2], ids=["rows_y", "rows_z"])
