@@ -12,6 +12,7 @@
 // one more sweep (outer-iterate checkpointing: T and the diffuse inflow
 // determine e).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -34,6 +35,16 @@ using namespace bte;
 namespace {
 
 constexpr double kFourPi = 4.0 * M_PI;
+
+// An NVTX range around a public entry point (named as the entry point): the
+// calls show in Nsight timelines next to their kernels; without a tool
+// attached the push and pop cost a function call each.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 thread_local std::string g_create_error;
 
 // Debug mode (environment variable BTE_DEBUG set to anything but 0, read
@@ -2560,6 +2571,7 @@ const char *validate_tables(const bte_plan *p) {
 
 int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands, const bte_quad *quad,
                const bte_bcs *bcs, const double *q_profile, bte_plan **out) {
+    NvtxRange nvtx_range("bte_create");
     if (!out) return fail(nullptr, BTE_EINVAL, "out is null");
     *out = nullptr;
     std::unique_ptr<bte_plan> p(new (std::nothrow) bte_plan());
@@ -2607,6 +2619,7 @@ int bte_create(const bte_grid *g, const uint8_t *mask, const bte_bands *bands, c
 }
 
 int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, void *e_out, bte_stats *st) {
+    NvtxRange nvtx_range("bte_solve");
     if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
     if (!o || !T_out) return fail(p, BTE_EINVAL, "opts and T_out are required");
     if (o->max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
@@ -2636,6 +2649,7 @@ int bte_solve(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out
 
 int bte_adjoint_ex(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double *g_tau, double *g_Twall,
                    double *g_Qamp, double *g_L, bte_stats *st) {
+    NvtxRange nvtx_range("bte_adjoint_ex");
     if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
     if (!dJ_dT) return fail(p, BTE_EINVAL, "dJ_dT is required");
     if (max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
@@ -2657,6 +2671,7 @@ int bte_adjoint(bte_plan *p, const double *dJ_dT, double tol, int max_iter, doub
 
 int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, double *T_out, double *T_hist,
                   bte_stats *st) {
+    NvtxRange nvtx_range("bte_transient");
     if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
     if (!o || !T_out) return fail(p, BTE_EINVAL, "opts and T_out are required");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, BTE_EINVAL, "dt must be finite and > 0");
@@ -2716,6 +2731,7 @@ int bte_shard_begin(bte_plan *p, const bte_solve_opts *o) {
 }
 
 int bte_shard_sweep(bte_plan *p, int b0, int b1, double *W_out) {
+    NvtxRange nvtx_range("bte_shard_sweep");
     if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
     if (p->shard_prec < 0) return fail(p, BTE_ESTATE, "bte_shard_sweep needs bte_shard_begin");
     if (!W_out || b0 < 0 || b1 <= b0 || b1 > p->B) return fail(p, BTE_EINVAL, "need 0 <= b0 < b1 <= B and W_out");
@@ -2725,6 +2741,7 @@ int bte_shard_sweep(bte_plan *p, int b0, int b1, double *W_out) {
 }
 
 int bte_shard_apply(bte_plan *p, const double *W, double *T_out, double *eps_T) {
+    NvtxRange nvtx_range("bte_shard_apply");
     if (!p) return fail(nullptr, BTE_EINVAL, "plan is null");
     if (p->shard_prec < 0) return fail(p, BTE_ESTATE, "bte_shard_apply needs bte_shard_begin");
     if (!W) return fail(p, BTE_EINVAL, "W is required");
@@ -2863,6 +2880,7 @@ int bte_batch_create(int n, bte_plan *const *plans, bte_batch **out) {
 }
 
 int bte_batch_solve(bte_batch *bt, const bte_solve_opts *o, double *T_out, bte_stats *st, bte_batch_stats *bs) {
+    NvtxRange nvtx_range("bte_batch_solve");
     if (!bt) return bfail(nullptr, BTE_EINVAL, "batch is null");
     if (!o || !T_out) return bfail(bt, BTE_EINVAL, "opts and T_out are required");
     if (o->max_iter < 1) return bfail(bt, BTE_EINVAL, "max_iter must be >= 1");
