@@ -49,6 +49,8 @@ WORKLOADS = {
     "slab": (lambda bi: bi.gray_slab(), "slab1d_200_B1_D16_fwd_eps1e-10_fp64", 1e-10, True, False),
     "hotspot": (lambda bi: bi.hotspot_3d(), "hotspot3d_64^3_B15_D128_fwd_eps1e-6", 1e-6, False, False),
     "finfet": (lambda bi: bi.finfet_3d(), "finfet3d_160x80x64_B15_D128_fwd+adj_eps1e-6", 1e-6, False, True),
+    "finfet_specular": (lambda bi: bi.finfet_specular_3d(),
+                        "finfet3d_specbase_160x80x64_B15_D128_fwd+adj_eps1e-6", 1e-6, False, True),
     "ensemble": (lambda bi: bi.ensemble_2d(), "ensemble2d_256x(32..160)^2_B15_D64_fwd_eps1e-6", 1e-6, False, False),
 }
 L2_FLUSH_BYTES = 512 << 20
@@ -175,7 +177,8 @@ def sweep_kernel_name(p, st):
     dw = st["dirs_per_lane"]
     phi = 0 if p.phi is None or p.Q_amp == 0.0 else 1
     if st["tile_kind"] == 3 and p.dim == 3:
-        return f"sweep3dp_kernel<float, {dw}, {phi}, 0, {int(st['lane_axis'] == 2)}>"
+        spec = int(any(int(t) == 2 for t in p.bc_type[:6]))   # the variant with specular faces
+        return f"sweep3dp_kernel<float, {dw}, {phi}, 0, {int(st['lane_axis'] == 2)}, {spec}>"
     if st["tile_kind"] == 3:
         return f"sweep2dp_kernel<float, {dw}, 8, {phi}, 0, {st['source_staged']}>"
     if st["tile_kind"] == 2:

@@ -258,6 +258,18 @@ def finfet_3d(scale: int = 1, n_polar: int = 8, n_az: int = 16,
         probes=probes.astype(np.int64), tol=1e-6)
 
 
+def finfet_specular_3d(**kw) -> Problem:
+    """The FinFET of ``finfet_3d`` with the paper's mixed boundaries of its
+    3D FinFET validation case: the base (substrate and oxide) reflects
+    specularly at its four side faces (x and y domain faces), the fin
+    surfaces (faces next to void cells) diffusely, the bottom is isothermal.
+    Same grid, bands, directions, source and probes."""
+    p = finfet_3d(**kw)
+    bct = p.bc_type.copy()
+    bct[0] = bct[1] = bct[2] = bct[3] = SPECULAR
+    return p.copy(name=p.name.replace("finfet3d", "finfet3d_specbase"), bc_type=bct)
+
+
 def ensemble_2d(n_instances: int = 256, n_min: int = 32, n_max: int = 160,
                 L_min: float = 1e-7, L_max: float = 1e-5):
     """Batched ensemble of uneven 2D squares: side cells ~ U{n_min..n_max},

@@ -109,8 +109,10 @@ typedef struct {
  * iterate, which leaves the converged fixed point unchanged).  A specular
  * face needs the mirror of every direction in the direction set (a product
  * set of Gauss-Legendre polar nodes and an even number of mid-point azimuths
- * has them); problems with specular faces are swept by the general kernel
- * (tile_kind 1).  At least one isothermal face must touch the solid. */
+ * has them); on 3D grids the plane pipeline (tile_kind 3) carries them, and
+ * the autotuner weighs it against the general kernel's extended variant
+ * (tile_kind 1); 1D and 2D problems with specular faces are swept by the
+ * latter.  At least one isothermal face must touch the solid. */
 typedef struct {
     int type[6];
     double T[6];
@@ -147,9 +149,9 @@ typedef struct {
     int tile_kind;          /* 0 = autotuned; 1 = general wavefront kernel (any grid);
                                2 = row-block kernel (unmasked 1D/2D, one region);
                                3 = row-pipeline kernel (unmasked 1D/2D, one region; on 3D
-                                   grids the plane-pipeline kernel: masks and several
-                                   regions allowed; FP32 with 2, 4 or 8 directions per lane,
-                                   FP64 with 2 or 4) */
+                                   grids the plane-pipeline kernel: masks, several regions
+                                   and specular faces allowed; FP32 with 2, 4 or 8
+                                   directions per lane, FP64 with 2 or 4) */
     int dirs_per_cta;       /* row kernels: directions per CTA (0 = autotuned) */
     int source_staging;     /* row-pipeline kernel: 0 = autotuned, 1 = per-cell source staged in
                                shared memory, 2 = read ahead from global memory */

@@ -34,10 +34,12 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 //   bits 4..9  side s (0:x- 1:x+ 2:y- 3:y+ 4:z- 5:z+) is a boundary face
 //              (outside the domain or next to a void cell)
 //   bits 10..15 side s is an isothermal domain face
+//   bits 16..21 side s is a specularly reflecting domain face
 // ---------------------------------------------------------------------------
 constexpr int kRegionMask = 0xF;
 constexpr int kSideShift = 4;
 constexpr int kIsoShift = 10;
+constexpr int kSpecShift = 16;
 constexpr int kMaxRegions = 15;
 
 __host__ __device__ inline int face_of(int base, int flags, int side) {
@@ -237,12 +239,20 @@ struct Sweep3DParams {
     int iso_fsum;                     // 1: face sums at isothermal domain faces too
     const real *__restrict__ tfwd;    // (grad) skewed forward T - T_ref
     const real *__restrict__ cb4pi;   // (grad) [B] C_b / (4 pi)
+    // specular faces (Fs > 0): per-direction inflow of the previous iterate
+    // and the next one's, stored under the mirror direction; the adjoint
+    // keeps mu = w nu there, the same values as the general kernel's adjoint
+    int Fs;
+    const int *__restrict__ sidx;     // [F] specular index of a face (-1: not specular)
+    const int *__restrict__ mirror;   // [3][D] direction with the axis-a component reversed
+    const real *__restrict__ spec_in; // [B][Fs][D]
+    real *__restrict__ spec_out;      // [B][Fs][D], or null (nothing stored)
     FinalizeParams fin;               // finalize the previous iteration (fin.pending null: nothing)
 };
 
 template <typename real>
 cudaError_t launch_sweep3dp(const Sweep3DParams<real> &p, int dirs_per_lane, cudaStream_t st);
-size_t sweep3dp_smem(int R, int WY, int H, int dw, int real_bytes);
+size_t sweep3dp_smem(int R, int WY, int H, int dw, int real_bytes, bool spec);
 constexpr int kPipe3Chunk = 4;        // steps between the CTA barriers of the 3D pipeline
 
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.

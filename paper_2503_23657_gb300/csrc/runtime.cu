@@ -448,8 +448,9 @@ bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H, int map) {
     // a lane's virtual columns (passes x nx) stay well inside the range in
     // which the kernel's float reciprocal division by nx is exact
     if ((long long)M * p->nx + 64 >= (1LL << 22)) return false;
-    return sweep3dp_smem(p->R, WY, H, dw, real_bytes) <= 225 * 1024;
+    return sweep3dp_smem(p->R, WY, H, dw, real_bytes, p->Fs > 0) <= 225 * 1024;
 }
+
 
 // Warps along z offered for the plane-pipeline kernel: the most that fit,
 // and about half of that (two CTAs per SM).
@@ -478,6 +479,9 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
                                  int cw_req = 0, int staging_req = 0, int wz_req = 0, int axis_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
+    // the plane pipeline carries specular faces too (3D grids)
+    const bool pipe3_only = p->Fs > 0 && p->xmode == 0 && p->dim == 3 &&
+                            (long long)p->B * p->Fs * p->D < (1LL << 31);   // 32-bit offsets in the kernel
     if (p->Fs > 0 || p->xmode != 0) {
         // specular faces, transient steps, second-order faces: the general
         // kernel's extended variant
@@ -487,9 +491,9 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
         if (lz != 0 && (kind_req == 0 || kind_req == 1) && (!dw_req || dw_req == kSpecDW) && mt > 0 &&
             WY * WZ * 32 <= mt)
             out.push_back(tile_id(0, kSpecDW, kSpecDW));
-        return out;
+        if (!pipe3_only) return out;
     }
-    if (lz != 0 && (kind_req == 0 || kind_req == 1)) {
+    if (lz != 0 && (kind_req == 0 || kind_req == 1) && !pipe3_only) {
         const bool z = p->dim == 3;
         const int WY = (p->ny + 31) / 32;
         const int WZ = z ? (p->nz + lz - 1) / lz : 1;
@@ -501,7 +505,7 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
     int stage = 0;
     int gmax = 0;
     for (int c : p->groups_cnt) gmax = std::max(gmax, c);
-    if (kind_req == 0 || kind_req == 3) {
+    if ((kind_req == 0 || kind_req == 3) && !pipe3_only) {
         for (int stage : {1, 0}) {
             if ((staging_req == 1 && !stage) || (staging_req == 2 && stage)) continue;
             for (int dw : {1, 2, 4, 8}) {
@@ -530,7 +534,7 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
             }
         }
     }
-    if ((kind_req == 0 || kind_req == 2) && rowblock_ok(p, real_bytes, &stage)) {
+    if ((kind_req == 0 || kind_req == 2) && !pipe3_only && rowblock_ok(p, real_bytes, &stage)) {
         for (int dw : {1, 2, 4}) {
             if (dw_req && dw != dw_req) continue;
             for (int warps : {1, 2, 4, 8, 16}) {
@@ -937,6 +941,11 @@ Sweep3DParams<real> sweep3d_params(bte_plan *p, Workspace<real> &ws, int tid, bo
     sp.qb = ws.qb.template as<real>();
     sp.done = p->d_status.as<int>();
     sp.adj = adj ? 1 : 0;
+    if (p->Fs > 0) {
+        sp.Fs = p->Fs;
+        sp.sidx = p->d_sidx.as<int>();
+        sp.mirror = p->d_mirror.as<int>();
+    }
     return sp;
 }
 
@@ -955,6 +964,9 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
         if (!sp.tsrc) return cudaErrorInvalidValue;
         sp.ein = ein;
         sp.store_e = store_e ? 1 : 0;
+        sp.spec_in = spec_in;
+        sp.spec_out = spec_out;
+        if (p->Fs > 0 && !spec_in) return cudaErrorInvalidValue;
         if (!use_done) sp.done = nullptr;
         if (use_done && fin) sp.fin = *fin;  // finalize the previous iteration
         return launch_sweep3dp<real>(sp, tl.dw, stream);
@@ -1463,6 +1475,10 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
         a3.ein = ws.mein[parity].template as<real>();
         a3.done = nullptr;
         a3.iso_fsum = 1;   // the wall-temperature gradients read them
+        if (p->Fs > 0) {
+            a3.spec_in = ws.mspec[parity].template as<real>();
+            a3.spec_out = ws.mspec[parity ^ 1].template as<real>();
+        }
         e = launch_sweep3dp<real>(a3, tile_of(dw).dw, stream);
         if (e != cudaSuccess) return e;
         Sweep3DParams<real> g3 = sweep3d_params(p, ws, dw, true);
@@ -1474,6 +1490,7 @@ cudaError_t enqueue_adjoint(bte_plan *p, Workspace<real> &ws, int dw, int parity
         g3.part = ws.gpart.template as<real>();
         g3.tfwd = ws.skt[map][p->solved_iters & 1].template as<real>();   // T^n of the solve
         g3.cb4pi = ws.cb4pi.template as<real>();
+        if (p->Fs > 0) g3.spec_in = ws.mspec[parity].template as<real>();
         e = launch_sweep3dp<real>(g3, tile_of(dw).dw, stream);
     } else {
         SweepParams<real> sp = sweep_params(p, ws, dw, true);
@@ -1520,7 +1537,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
     // extended variant when it also forms the cell-size partials)
     // the final pass runs on the solve's own tile where that is the plane
     // pipeline (its gradient form), else on a general tile
-    const bool pipe_grad = is_pipe3(tile_of(dw).kind) && !g_L && p->Fs == 0;
+    const bool pipe_grad = is_pipe3(tile_of(dw).kind) && !g_L;
     int gtile = dw;
     if (!pipe_grad) {
         std::vector<int> gen = tile_candidates(p, (int)sizeof(real), 1, g_L ? kSpecDW : 0);
@@ -1941,6 +1958,7 @@ int build_plan(bte_plan *p, const bte_grid *g, const uint8_t *mask, const bte_ba
                             const bool spec = outside && p->bc_type[side] == BTE_BC_SPECULAR;
                             p->face_kind.push_back(iso ? 0 : (spec ? 2 : 1));
                             if (iso) flags |= 1 << (kIsoShift + side);
+                            if (spec) flags |= 1 << (kSpecShift + side);
                             p->sidx.push_back(spec ? p->Fs : -1);
                             if (spec) {
                                 p->spec_faces.push_back(p->F);
@@ -2553,6 +2571,8 @@ const char *validate_tables(const bte_plan *p) {
             if (!((bm >> side) & 1u)) continue;
             const int f = face_of(base, flags, side);
             if (p->face_cell[f] != c || p->face_side[f] != side) return "cell face index does not point at its face";
+            if ((((unsigned)flags >> (kSpecShift + side)) & 1u) != (p->face_kind[f] == 2 ? 1u : 0u))
+                return "specular flag of a cell side differs from its face kind";
         }
     }
     for (int v : p->wall_face)

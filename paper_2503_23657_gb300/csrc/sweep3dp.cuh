@@ -35,6 +35,15 @@
 //     source profile are read from diagonal-skewed copies (SkewLayout), in
 //     which the 32 cells of a warp's step are consecutive: one coalesced
 //     segment per warp and array instead of 32 scattered rows;
+//   * specularly reflecting domain faces (Methods, Boundary conditions): the
+//     inflow of direction d through such a face is the previous iterate's
+//     value of the mirror direction of d in the same cell, read per
+//     direction in the warp steps that meet one (rare, like the x and z
+//     boundaries); a cell whose downwind side is specular stores its values
+//     under the mirror directions for the next iterate.  The adjoint keeps
+//     mu = w nu in those arrays (the general kernel's convention; its
+//     transposed coupling is the same rule, the mirror swap preserving
+//     |s_a|);
 //   * forward and adjoint run the same recurrence: the adjoint unknown mu_d
 //     of the transposed system (Eq. adjoint) scaled by 1 / w_d obeys the
 //     forward recurrence with the adjoint source and boundary values, and
@@ -153,21 +162,51 @@ __device__ __forceinline__ void p3_cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shared-memory carve-up, in elements of real.
-struct P3Smem {
-    int invd, srck, fw, zr, yr, tile, total;
+// compile-time selector of a variant of the per-step direction loop
+template <int V>
+struct P3Kind {
+    static constexpr int value = V;
 };
-__host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW) {
+
+// Shared-memory carve-up, in elements of real (spec: the variant with
+// specular faces).
+struct P3Smem {
+    int invd, srck, fw, zr, yr, tile, mir, iw, spec, total;
+};
+__host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW, bool spec) {
     const int NW = WY * H;
     P3Smem s;
     s.invd = 0;                                        // [R][DW] 1 / diagonal
     s.srck = s.invd + p3_round4(R * DW);               // [R] source factor
     s.fw = s.srck + p3_round4(R);                      // [3][DW] face-sum weights
-    s.zr = s.fw + p3_round4(3 * DW);                   // [NW + WY][RZ][32][DW] z rings
-    s.yr = s.zr + (NW + WY) * kP3RZ * 32 * DW;         // [NW + 2][RY][DW] y rings
+    s.zr = s.fw + p3_round4(3 * DW);                   // [NW][RZ][32][DW] z rings
+    s.yr = s.zr + NW * kP3RZ * 32 * DW;                // [NW + 2][RY][DW] y rings
     s.tile = s.yr + (NW + 2) * kP3RY * DW;             // [NW][32][33] partial-sum tiles
-    s.total = s.tile + NW * 32 * 33;
+    s.mir = s.tile + NW * 32 * 33;                     // [3][DW] mirror directions (int)
+    s.iw = s.mir + (spec ? p3_round4(3 * DW) : 0);     // [DW] 1 / w
+    s.spec = s.iw + (spec ? p3_round4(DW) : 0);        // [NW][32][DW] specular inflow of the next step
+    s.total = s.spec + (spec ? NW * 32 * DW : 0);
     return s;
+}
+
+// Asynchronous global -> shared copy of DW consecutive values in pieces of
+// 16 bytes where `wide` says both addresses are aligned to them, else of one
+// value each.  The caller commits the group.
+template <int DW, typename real>
+__device__ __forceinline__ void p3_cp_async_row(real *dst, const real *src, bool wide) {
+    constexpr int kBytes = DW * (int)sizeof(real);
+    constexpr int kOne = (int)sizeof(real);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const char *g = reinterpret_cast<const char *>(src);
+    if (kBytes % 16 == 0 && wide) {
+#pragma unroll
+        for (int o = 0; o < kBytes; o += 16)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + o), "l"(g + o) : "memory");
+    } else {
+#pragma unroll
+        for (int o = 0; o < kBytes; o += kOne)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d + o), "l"(g + o), "n"(kOne) : "memory");
+    }
 }
 
 // EM: 0 = a source-iteration sweep; 1 = the same that also writes e; 2 =
@@ -175,7 +214,7 @@ __host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW) {
 // sum_d w_d (nu_d - Theta)(e_d - e0) = sum_d (mu_d - w_d Theta)(e_d - e0),
 // e the forward solution's values and e0 = C_b (T - T_ref)/(4 pi) (the
 // partials of dJ/dtau), and no face sums are formed
-template <typename real, int DW, bool PHI, int EM, bool ZROWS>
+template <typename real, int DW, bool PHI, int EM, bool ZROWS, bool SPEC>
 __global__ void __launch_bounds__(kP3MaxThreads, 1)
 sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     constexpr int K = kPipe3Chunk, RZ = kP3RZ, RY = kP3RY;
@@ -196,11 +235,12 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const int n2 = a1 == 1 ? P.nz : P.ny;          // planes
     const int s1 = a1 == 1 ? nx : nx * P.ny;       // cell stride of the next row
     const int s2 = a1 == 1 ? nx * P.ny : nx;       // cell stride of the next plane
-    const P3Smem L = p3_smem(R, WY, H, DW);
+    const P3Smem L = p3_smem(R, WY, H, DW, SPEC);
     real *sm = reinterpret_cast<real *>(smem_raw);
     real *s_invd = sm + L.invd;
     real *s_srck = sm + L.srck;
     real *s_fw = sm + L.fw;
+    const real *s_iw = sm + L.iw;   // (specular faces) 1 / w of the subset's directions
 
     // the next kernel may be launched now (it waits for this grid); all
     // reads below see what the previous kernel wrote
@@ -233,6 +273,17 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         for (int q = threadIdx.x; q < RY * DW; q += blockDim.x) yz[q] = real(0);
         real *zz = sm + L.zr;
         for (int q = threadIdx.x; q < WY * RZ * 32 * DW; q += blockDim.x) zz[q] = real(0);
+    }
+    if constexpr (SPEC) {
+        // mirror directions of the subset, per physical axis
+        int *mir = reinterpret_cast<int *>(sm + L.mir);
+        for (int q = threadIdx.x; q < 3 * DW; q += blockDim.x) {
+            const int a = q / DW, dd = q - a * DW;
+            mir[q] = dd < ndir ? P.mirror[a * P.D + d0 + dd] : 0;
+        }
+        real *iw = sm + L.iw;
+        for (int dd = threadIdx.x; dd < DW; dd += blockDim.x)
+            iw[dd] = dd < ndir ? real(1) / P.coef[((long long)b * P.D + d0 + dd) * 8 + 3] : real(0);
     }
     for (int q = threadIdx.x; q < 3 * DW; q += blockDim.x) {
         const int a = q / DW, dd = q - a * DW;
@@ -277,6 +328,12 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const real qb = PHI ? P.qb[b] : real(0);
     const real cb4pi = (EM == 2) ? P.cb4pi[b] : real(0);
     const unsigned iso_skip = P.iso_fsum ? 0u : 63u;
+    // the sides of the specular faces a cell's inflow comes through (none
+    // without specular faces)
+    const unsigned spec_up = SPEC ? ((1u << up_x) | (1u << up_1) | (1u << up_2)) : 0u;
+    // 16-byte copies of the inflow rows where they are aligned (D and d0)
+    constexpr int kRowVec = 16 / (int)sizeof(real);
+    const bool spec_wide = (P.D % kRowVec) == 0 && (d0 % kRowVec) == 0;
     const real *einb = P.ein + (long long)b * P.F;
     const int j = 32 * wy + lane;
     const bool rowv = j < n1;
@@ -316,9 +373,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     // z rings: slot (local step mod RZ) of this lane; the writer (warp below
     // in z) and the reader handle a given column at the same local step.
     // Warp w reads ring w and writes ring w + WY: the first plane warps read
-    // rings they fill themselves from the wrap buffer (two steps ahead), the
-    // last plane warps write rings nobody reads, so every warp runs the same
-    // code.  y rings: warp w writes ring w for the warp above it in y (the top
+    // rings they fill themselves from the wrap buffer (two steps ahead); the
+    // last plane warps have no ring to write (their one predicated store is
+    // all that differs; rings nobody reads would take the shared memory that
+    // lets two CTAs of 8 warps share an SM).  y rings: warp w writes ring w for the warp above it in y (the top
     // row warps write ring NW + 1, read by nobody), the bottom row warps read
     // ring NW (zeros).
     real *const zr_out = sm + L.zr + (warp + WY) * RZ * 32 * DW + lane * DW;
@@ -411,6 +469,28 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     for (int q = 0; q < 4; ++q) fetch_record(q);
     fetch_data(0, 0, 0);
     fetch_data(1, 1, 1);
+    // specular faces: the inflow of the next step's cell through its one
+    // specular upwind face is copied into this warp's shared-memory slot a
+    // step ahead (spec_side: that face's side, -1 none, -2 several: a domain
+    // edge, whose rows the step reads itself)
+    int spec_side = -1;
+    real *const spec_slot = sm + L.spec + (warp * 32 + lane) * DW;
+    auto fetch_spec = [&](int q) {
+        const int fb1 = rx[q], fl1 = ry[q];
+        const unsigned sb = ((unsigned)fl1 >> kSpecShift) & spec_up;
+        spec_side = -1;
+        if (sb != 0u) {
+            if ((sb & (sb - 1u)) == 0u) {
+                spec_side = __ffs((int)sb) - 1;
+                const int off = (b * P.Fs + P.sidx[face_of(fb1, fl1, spec_side)]) * P.D + d0;
+                p3_cp_async_row<DW>(spec_slot, P.spec_in + off, spec_wide);
+            } else {
+                spec_side = -2;
+            }
+        }
+        p3_cp_commit();
+    };
+    if constexpr (SPEC) fetch_spec(0);
 
     for (int t0 = 0; t0 < T; t0 += K) {
         const int tau0 = t0 - delta;
@@ -418,7 +498,6 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int tau = tau0 + k;
-                const int u = tau - lane;
                 // this step's cell (record read four steps ago, data two)
                 const int c = EM ? rc[EM ? k : 0] : -1;
                 const int fb = rx[k], fl = ry[k], iw = riw[k];
@@ -436,7 +515,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 // ring slot was filled by the copy issued two steps ago)
                 const int zslot = (tau & (RZ - 1)) * 32 * DW;
                 real zin[DW], yin[DW];
-                if (wrap_rd) p3_cp_wait<1>();
+                if constexpr (SPEC)
+                    p3_cp_wait<0>();   // this step's inflow slot (and the ring slots) are in
+                else if (wrap_rd)
+                    p3_cp_wait<1>();
                 p3_load<DW>(zr_in + zslot, zin);
                 p3_load<DW>(yr_in + (tau & (RY - 1)) * DW, yin);  // lane 0: u == tau
                 // reads for later steps
@@ -458,17 +540,38 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 // that no solid cell reads (their downwind neighbours take
                 // boundary values) and that the update kernel ignores
                 real acc = real(0);
-                // x and z boundaries are met in few warp steps (a row's first
-                // column, a pass's first plane, void neighbours): the selects
-                // for them only run when a lane of the warp needs them
-                if (__any_sync(0xffffffffu, bx || bz)) {
+                // the directions of this step; the variant: 0 = only row-axis
+                // boundaries, 1 = also x and z boundaries, 2 = also specular
+                // faces (the per-direction inflow: the previous iterate's
+                // value of the mirror direction, forward e; adjoint mu = w nu,
+                // taken as nu; spx, spy, spz: offsets of the inflow rows in
+                // spec_in, -1 where the side is not specular)
+                int spx = -1, spy = -1, spz = -1;
+                const int ssd = SPEC ? spec_side : -1;   // the side of this step's slot
+                auto dirs = [&](auto kind) {
+                    constexpr int V = decltype(kind)::value;
 #pragma unroll
                     for (int dd = 0; dd < DW; ++dd) {
                         real vy = __shfl_up_sync(0xffffffffu, old[dd], 1);
                         if (lane == 0) vy = yin[dd];
-                        const real vx = bx ? Ex : old[dd];
+                        real vx = old[dd], vz = zin[dd];
+                        if constexpr (V >= 1) {
+                            vx = bx ? Ex : vx;
+                            vz = bz ? Ez : vz;
+                        }
                         vy = by ? Ey : vy;
-                        const real vz = bz ? Ez : zin[dd];
+                        if constexpr (V == 2) {
+                            if (dd < ndir) {
+                                const real sc = adj ? s_iw[dd] : real(1);
+                                const real sv = spec_slot[dd] * sc;
+                                vx = ssd == up_x ? sv : vx;
+                                vy = ssd == up_1 ? sv : vy;
+                                vz = ssd == up_2 ? sv : vz;
+                                if (spx >= 0) vx = P.spec_in[spx + dd] * sc;
+                                if (spy >= 0) vy = P.spec_in[spy + dd] * sc;
+                                if (spz >= 0) vz = P.spec_in[spz + dd] * sc;
+                            }
+                        }
                         real r0 = fma(ax[dd], vx, base);
                         r0 = fma(ay[dd], vy, r0);
                         r0 = fma(az[dd], vz, r0);
@@ -479,25 +582,32 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                         else
                             acc = fma(w[dd], en, acc);
                     }
-                } else {
-#pragma unroll
-                    for (int dd = 0; dd < DW; ++dd) {
-                        real vy = __shfl_up_sync(0xffffffffu, old[dd], 1);
-                        if (lane == 0) vy = yin[dd];
-                        vy = by ? Ey : vy;
-                        real r0 = fma(ax[dd], old[dd], base);
-                        r0 = fma(ay[dd], vy, r0);
-                        r0 = fma(az[dd], zin[dd], r0);
-                        const real en = r0 * invd[dd];
-                        old[dd] = en;
-                        if constexpr (GRAD)
-                            acc = fma(w[dd] * (en - tsv), gde[dd], acc);
-                        else
-                            acc = fma(w[dd], en, acc);
+                };
+                // x and z boundaries are met in few warp steps (a row's first
+                // column, a pass's first plane, void neighbours), specular
+                // faces in fewer: their selects and loads only run when a lane
+                // of the warp needs them
+                const unsigned sup = SPEC ? ((unsigned)fl >> kSpecShift) & spec_up : 0u;
+                if (__any_sync(0xffffffffu, bx || bz || sup != 0u)) {
+                    if (SPEC && __any_sync(0xffffffffu, sup != 0u)) {
+                        if (ssd == -2) {
+                            // a domain edge: the rows of all its specular
+                            // sides (B Fs D < 2^31: checked on the host)
+                            const int rb = b * P.Fs;
+                            if ((sup >> up_x) & 1u) spx = (rb + P.sidx[face_of(fb, fl, up_x)]) * P.D + d0;
+                            if ((sup >> up_1) & 1u) spy = (rb + P.sidx[face_of(fb, fl, up_1)]) * P.D + d0;
+                            if ((sup >> up_2) & 1u) spz = (rb + P.sidx[face_of(fb, fl, up_2)]) * P.D + d0;
+                        }
+                        dirs(P3Kind<2>{});
+                    } else {
+                        dirs(P3Kind<1>{});
                     }
+                } else {
+                    dirs(P3Kind<0>{});
                 }
+                if constexpr (SPEC) fetch_spec((k + 1) & 3);
                 tile_l[tau & 31] = acc;
-                p3_store<DW>(zr_out + zslot, old);
+                if (h + 1 < H) p3_store<DW>(zr_out + zslot, old);
                 if (lane == 31) p3_store<DW>(yr_out + ((tau - 31) & (RY - 1)) * DW, old);
                 if (wrap_wr && iw >= 0) p3_store<DW>(wrap_c + ((long long)iw * ld_wrap + j) * DW, old);
                 // face sums at the boundary sides the traversal leaves by
@@ -510,12 +620,25 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                         const int dn = (a == 0 ? up_x : (a == 1 ? up_1 : up_2)) ^ 1;
                         const int pa = a == 0 ? 0 : (a == 1 ? a1 : a2);   // physical axis
                         if (!((fsm >> dn) & 1u)) continue;
+                        const int f = face_of(fb, fl, dn);
+                        if (SPEC && ((((unsigned)fl >> kSpecShift) >> dn) & 1u)) {
+                            // a specular face: the next iterate's inflow of
+                            // the mirror directions (adjoint: mu = w nu)
+                            if (P.spec_out != nullptr) {
+                                real *so = P.spec_out + (b * P.Fs + P.sidx[f]) * P.D;
+                                const int *mr = reinterpret_cast<const int *>(sm + L.mir) + pa * DW;
+#pragma unroll
+                                for (int dd = 0; dd < DW; ++dd)
+                                    if (dd < ndir) so[mr[dd]] = adj ? old[dd] * w[dd] : old[dd];
+                            }
+                            continue;
+                        }
                         real fw[DW];
                         p3_load<DW>(s_fw + pa * DW, fw);
                         real fs = real(0);
 #pragma unroll
                         for (int dd = 0; dd < DW; ++dd) fs = fma(fw[dd], old[dd], fs);
-                        fs_sb[face_of(fb, fl, dn)] = fs;
+                        fs_sb[f] = fs;
                     }
                 }
                 if (STORE_E && act && c >= 0) {
@@ -570,20 +693,20 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         }
         __syncthreads();
     }
-    if (wrap_rd) p3_cp_wait<0>();   // no copy outlives the kernel
+    if (SPEC || wrap_rd) p3_cp_wait<0>();   // no copy outlives the kernel
 }
 
 template <typename real>
-size_t sweep3dp_smem_bytes(int R, int WY, int H, int dw) {
-    return (size_t)p3_smem(R, WY, H, dw).total * sizeof(real);
+size_t sweep3dp_smem_bytes(int R, int WY, int H, int dw, bool spec) {
+    return (size_t)p3_smem(R, WY, H, dw, spec).total * sizeof(real);
 }
 
-template <typename real, int DW, bool PHI, int EM, bool ZROWS>
+template <typename real, int DW, bool PHI, int EM, bool ZROWS, bool SPEC>
 cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
     const int threads = p.WY * p.H * 32;
     if (p.H < 1 || p.WY < 1 || threads > kP3MaxThreads) return cudaErrorInvalidConfiguration;
-    const size_t smem = sweep3dp_smem_bytes<real>(p.R, p.WY, p.H, DW);
-    auto kern = sweep3dp_kernel<real, DW, PHI, EM, ZROWS>;
+    const size_t smem = sweep3dp_smem_bytes<real>(p.R, p.WY, p.H, DW, SPEC);
+    auto kern = sweep3dp_kernel<real, DW, PHI, EM, ZROWS, SPEC>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -593,25 +716,27 @@ cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
 
 // the source-profile term only in forward sweeps with a source; e only when
 // asked; the gradient form only in adjoint sweeps
-template <typename real, int DW, bool ZROWS>
+template <typename real, int DW, bool ZROWS, bool SPEC>
 cudaError_t launch_sweep3dp_z(const Sweep3DParams<real> &p, cudaStream_t st) {
     const bool phi = !p.adj && p.phi != nullptr;
     if (p.grad) {
         if (!p.adj || p.store_e || !p.tfwd || !p.cb4pi || !p.e) return cudaErrorInvalidValue;
-        return launch_sweep3dp_v<real, DW, false, 2, ZROWS>(p, st);
+        return launch_sweep3dp_v<real, DW, false, 2, ZROWS, SPEC>(p, st);
     }
     if (p.store_e)
-        return phi ? launch_sweep3dp_v<real, DW, true, 1, ZROWS>(p, st)
-                   : launch_sweep3dp_v<real, DW, false, 1, ZROWS>(p, st);
-    return phi ? launch_sweep3dp_v<real, DW, true, 0, ZROWS>(p, st)
-               : launch_sweep3dp_v<real, DW, false, 0, ZROWS>(p, st);
+        return phi ? launch_sweep3dp_v<real, DW, true, 1, ZROWS, SPEC>(p, st)
+                   : launch_sweep3dp_v<real, DW, false, 1, ZROWS, SPEC>(p, st);
+    return phi ? launch_sweep3dp_v<real, DW, true, 0, ZROWS, SPEC>(p, st)
+               : launch_sweep3dp_v<real, DW, false, 0, ZROWS, SPEC>(p, st);
 }
 
 // rows along y or along z
-template <typename real, int DW>
+// (SPEC: the variant with specular faces, a problem that has some)
+template <typename real, int DW, bool SPEC>
 cudaError_t launch_sweep3dp_t(const Sweep3DParams<real> &p, cudaStream_t st) {
-    if (p.lane_axis == 1) return launch_sweep3dp_z<real, DW, false>(p, st);
-    if (p.lane_axis == 2) return launch_sweep3dp_z<real, DW, true>(p, st);
+    if (SPEC != (p.Fs > 0) || (SPEC && !p.spec_in)) return cudaErrorInvalidValue;
+    if (p.lane_axis == 1) return launch_sweep3dp_z<real, DW, false, SPEC>(p, st);
+    if (p.lane_axis == 2) return launch_sweep3dp_z<real, DW, true, SPEC>(p, st);
     return cudaErrorInvalidConfiguration;
 }
 
