@@ -127,11 +127,16 @@ class ClockSampler:
 # proportion to the bands: every band is an independent set of CTAs).
 NCU_TRAFFIC = {
     # FinFET 160x80x64, 15 bands, forward launch, full size (one-pass capture),
-    # mean of two launches: 450.6 MB read + 1290.7 MB written
-    ("sweep3dp_kernel<float, 8, 1, 0, 1>", "3:8:8:2:8:2", "2b5386a11c8a"): 1741335552,
+    # mean of two launches: 1205.96 MB read + 2192.89 MB written (two 8-warp
+    # CTAs per SM: the per-CTA wrap planes of all 240 resident CTAs and the
+    # partial sums leave L2)
+    ("sweep3dp_kernel<float, 8, 1, 0, 1, 0>", "3:8:8:2:4:2", "5cc464bb0506"): 3398849664,
     # 64^3 hotspot, 15 bands, forward launch, full size, mean of two launches:
-    # 69.9 MB read + 239.1 MB written
-    ("sweep3dp_kernel<float, 8, 1, 0, 0>", "3:8:8:2:8:1", "2b5386a11c8a"): 308942592,
+    # 66.1 MB read + 251.6 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 0, 0>", "3:8:8:2:4:1", "5cc464bb0506"): 317668096,
+    # FinFET with specular base side faces, forward launch, full size, mean
+    # of two launches: 1328.86 MB read + 2366.81 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 1, 1>", "3:8:8:2:4:2", "5cc464bb0506"): 3695668864,
 }
 KERNEL_SOURCES = {
     "sweep3dp_kernel": ["sweep3dp.cuh", "bte_internal.cuh", "finalize.cuh", "tma.cuh"],
