@@ -271,8 +271,9 @@ int bte_adjoint_ex(bte_plan *p, const double *dJ_dT, double tol, int max_iter, d
  * steady problem with 1/dt added to the diagonal and e^m/dt to the source,
  * solved by the same source iteration to eps_T < o->tol (at most o->max_iter
  * iterations per step); the temperature follows from the same energy
- * balance of the scattering term (Eq. updatee0_t).  Step faces; general
- * kernel (tile_kind 0 or 1).
+ * balance of the scattering term (Eq. updatee0_t).  Step faces; the general
+ * kernel (tile_kind 1) or, on 3D grids, the plane pipeline (tile_kind 3),
+ * whichever the autotuner finds faster (tile_kind 0).
  *   T_out   N doubles: T after the last step (host or device), required
  *   T_hist  n_steps * N doubles: T after every step (host or device), or NULL
  *   st      totals over the steps (iterations, seconds), or NULL

@@ -284,12 +284,12 @@ class Plan:
 
     def transient(self, dt, n_steps, T_out, T_hist=None, precision=BTE_FP64, tol=1e-10, max_iter=100000,
                   T_init=None, T_init_uniform=None, Q_amp=None, tau=None, T_wall=None, stream=None, poll_every=32,
-                  check=True):
+                  tile_kind=0, dirs_per_lane=0, warps_z=0, lane_axis=0, check=True):
         """Run bte_transient: n_steps implicit-Euler steps of length dt.
         Returns (rc, stats dict)."""
         keep = []
         o = self._opts(precision, tol, max_iter, T_init, T_init_uniform, Q_amp, tau, T_wall, stream, poll_every,
-                       0, False, 0, 0, 0, 0, 0, 1, keep)
+                       dirs_per_lane, False, tile_kind, 0, 0, warps_z, lane_axis, 1, keep)
         st = Stats()
         rc = self._lib.bte_transient(self._h, ctypes.byref(o), float(dt), int(n_steps), _addr(T_out), _addr(T_hist),
                                      ctypes.byref(st))

@@ -248,11 +248,16 @@ struct Sweep3DParams {
     const real *__restrict__ spec_in; // [B][Fs][D]
     real *__restrict__ spec_out;      // [B][Fs][D], or null (nothing stored)
     FinalizeParams fin;               // finalize the previous iteration (fin.pending null: nothing)
+    // extra source of forward sweeps (implicit-Euler steps): xscale * xsrc
+    // [N][B][D] (padded by 16 values) is added to every direction's
+    // right-hand side; null: none
+    const real *__restrict__ xsrc;
+    real xscale;
 };
 
 template <typename real>
 cudaError_t launch_sweep3dp(const Sweep3DParams<real> &p, int dirs_per_lane, cudaStream_t st);
-size_t sweep3dp_smem(int R, int WY, int H, int dw, int real_bytes, bool spec);
+size_t sweep3dp_smem(int R, int WY, int H, int dw, int real_bytes, int variant);
 constexpr int kPipe3Chunk = 4;        // steps between the CTA barriers of the 3D pipeline
 
 // Temperature (forward) / adjoint-temperature (adjoint) update, FP64.

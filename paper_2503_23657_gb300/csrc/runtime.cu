@@ -448,7 +448,8 @@ bool pipe3_ok(const bte_plan *p, int real_bytes, int dw, int H, int map) {
     // a lane's virtual columns (passes x nx) stay well inside the range in
     // which the kernel's float reciprocal division by nx is exact
     if ((long long)M * p->nx + 64 >= (1LL << 22)) return false;
-    return sweep3dp_smem(p->R, WY, H, dw, real_bytes, p->Fs > 0) <= 225 * 1024;
+    const int variant = (p->Fs > 0 ? 1 : 0) | (p->xmode == 1 ? 2 : 0);
+    return sweep3dp_smem(p->R, WY, H, dw, real_bytes, variant) <= 225 * 1024;
 }
 
 
@@ -479,8 +480,9 @@ std::vector<int> tile_candidates(const bte_plan *p, int real_bytes, int kind_req
                                  int cw_req = 0, int staging_req = 0, int wz_req = 0, int axis_req = 0) {
     std::vector<int> out;
     const int lz = tile_layers(p);
-    // the plane pipeline carries specular faces too (3D grids)
-    const bool pipe3_only = p->Fs > 0 && p->xmode == 0 && p->dim == 3 &&
+    // the plane pipeline carries specular faces and the extra source of
+    // transient steps too (3D grids)
+    const bool pipe3_only = p->dim == 3 && (p->Fs > 0 || p->xmode == 1) && p->xmode != 2 &&
                             (long long)p->B * p->Fs * p->D < (1LL << 31);   // 32-bit offsets in the kernel
     if (p->Fs > 0 || p->xmode != 0) {
         // specular faces, transient steps, second-order faces: the general
@@ -967,6 +969,10 @@ cudaError_t launch_tile_sweep(bte_plan *p, Workspace<real> &ws, int tid, bool ad
         sp.spec_in = spec_in;
         sp.spec_out = spec_out;
         if (p->Fs > 0 && !spec_in) return cudaErrorInvalidValue;
+        if (!adj && p->xmode == 1) {
+            sp.xsrc = ws.xsrc;
+            sp.xscale = ws.xscale;
+        }
         if (!use_done) sp.done = nullptr;
         if (use_done && fin) sp.fin = *fin;  // finalize the previous iteration
         return launch_sweep3dp<real>(sp, tl.dw, stream);
@@ -1737,8 +1743,9 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
 
 // Transient: n_steps implicit-Euler steps of length dt, every one a solve of
 // the steady machinery with 1/dt on the diagonal (upload_tables) and the
-// previous step's e over dt as the extra source of the general kernel's
-// extended variant; T_ref stays that of the initial state over the run.
+// previous step's e over dt as the extra source of the sweep (the plane
+// pipeline's extra-source variant on 3D grids, else the general kernel's
+// extended variant); T_ref stays that of the initial state over the run.
 template <typename real>
 int transient_t(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, double *T_out, double *T_hist,
                 bte_stats *st) {
@@ -1770,7 +1777,7 @@ int transient_t(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, do
     }
     const double T_ref = sum / (double)p->n_active;
     for (long long c = 0; c < N; ++c) td[c] = p->mask[c] ? (real)(T0[c] - T_ref) : (real)0;
-    CK(p, ws.eprev.ensure(sizeof(real) * NBD));
+    CK(p, ws.eprev.ensure(sizeof(real) * (NBD + 16)));   // (padded: the plane pipeline copies whole subsets)
     CK(p, ws.ttmp.ensure(sizeof(real) * (N + 16)));
     CK(p, ws.Tstep.ensure(sizeof(double) * N));
     std::vector<real> cb(p->B);
@@ -2699,7 +2706,8 @@ int bte_transient(bte_plan *p, const bte_solve_opts *o, double dt, int n_steps, 
     if (o->max_iter < 1) return fail(p, BTE_EINVAL, "max_iter must be >= 1");
     if (o->face_order == 2) return fail(p, BTE_EINVAL, "transient steps use step faces (face_order 0 or 1)");
     if (o->face_order < 0 || o->face_order > 2) return fail(p, BTE_EINVAL, "face_order must be 0, 1 or 2");
-    if (o->tile_kind != 0 && o->tile_kind != 1) return fail(p, BTE_EINVAL, "transient steps use the general kernel");
+    if (o->tile_kind != 0 && o->tile_kind != 1 && !(o->tile_kind == 3 && p->dim == 3))
+        return fail(p, BTE_EINVAL, "transient steps use the general kernel (or, on 3D grids, the plane pipeline)");
     if (!o->T_init && !(o->T_init_uniform > 0.0)) return fail(p, BTE_EINVAL, "T_init_uniform must be > 0");
     if (!std::isfinite(o->Q_amp)) return fail(p, BTE_EINVAL, "Q_amp must be finite");
     if (o->Q_amp_each) return fail(p, BTE_EINVAL, "Q_amp_each is for batched solves");

@@ -168,12 +168,13 @@ struct P3Kind {
     static constexpr int value = V;
 };
 
-// Shared-memory carve-up, in elements of real (spec: the variant with
-// specular faces).
+// Shared-memory carve-up, in elements of real (X: the variant, bit 0 =
+// specular faces, bit 1 = an extra per-direction source).
 struct P3Smem {
-    int invd, srck, fw, zr, yr, tile, mir, iw, spec, total;
+    int invd, srck, fw, zr, yr, tile, mir, iw, spec, xs, total;
 };
-__host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW, bool spec) {
+__host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW, int X) {
+    const bool spec = (X & 1) != 0, xsrc = (X & 2) != 0;
     const int NW = WY * H;
     P3Smem s;
     s.invd = 0;                                        // [R][DW] 1 / diagonal
@@ -185,7 +186,8 @@ __host__ __device__ inline P3Smem p3_smem(int R, int WY, int H, int DW, bool spe
     s.mir = s.tile + NW * 32 * 33;                     // [3][DW] mirror directions (int)
     s.iw = s.mir + (spec ? p3_round4(3 * DW) : 0);     // [DW] 1 / w
     s.spec = s.iw + (spec ? p3_round4(DW) : 0);        // [NW][32][DW] specular inflow of the next step
-    s.total = s.spec + (spec ? NW * 32 * DW : 0);
+    s.xs = s.spec + (spec ? NW * 32 * DW : 0);         // [NW][32][DW] extra source of the next step
+    s.total = s.xs + (xsrc ? NW * 32 * DW : 0);
     return s;
 }
 
@@ -214,9 +216,14 @@ __device__ __forceinline__ void p3_cp_async_row(real *dst, const real *src, bool
 // sum_d w_d (nu_d - Theta)(e_d - e0) = sum_d (mu_d - w_d Theta)(e_d - e0),
 // e the forward solution's values and e0 = C_b (T - T_ref)/(4 pi) (the
 // partials of dJ/dtau), and no face sums are formed
-template <typename real, int DW, bool PHI, int EM, bool ZROWS, bool SPEC>
+template <typename real, int DW, bool PHI, int EM, bool ZROWS, int X>
 __global__ void __launch_bounds__(kP3MaxThreads, 1)
 sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
+    // X bit 0: specular faces; bit 1: the extra source xscale * xsrc[c][b][d]
+    // of forward sweeps (implicit-Euler time steps: e of the previous step
+    // over dt)
+    constexpr bool SPEC = (X & 1) != 0, XS = (X & 2) != 0;
+    constexpr bool RC = EM != 0 || XS;   // the cell index of every step is tracked
     constexpr int K = kPipe3Chunk, RZ = kP3RZ, RY = kP3RY;
     static_assert(K == 4, "the prefetch slots assume four steps per chunk");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -235,7 +242,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     const int n2 = a1 == 1 ? P.nz : P.ny;          // planes
     const int s1 = a1 == 1 ? nx : nx * P.ny;       // cell stride of the next row
     const int s2 = a1 == 1 ? nx * P.ny : nx;       // cell stride of the next plane
-    const P3Smem L = p3_smem(R, WY, H, DW, SPEC);
+    const P3Smem L = p3_smem(R, WY, H, DW, X);
     real *sm = reinterpret_cast<real *>(smem_raw);
     real *s_invd = sm + L.invd;
     real *s_srck = sm + L.srck;
@@ -331,9 +338,10 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     // the sides of the specular faces a cell's inflow comes through (none
     // without specular faces)
     const unsigned spec_up = SPEC ? ((1u << up_x) | (1u << up_1) | (1u << up_2)) : 0u;
-    // 16-byte copies of the inflow rows where they are aligned (D and d0)
+    // 16-byte copies of the rows of DW directions where they are aligned (D
+    // and d0)
     constexpr int kRowVec = 16 / (int)sizeof(real);
-    const bool spec_wide = (P.D % kRowVec) == 0 && (d0 % kRowVec) == 0;
+    const bool row_wide = (P.D % kRowVec) == 0 && (d0 % kRowVec) == 0;
     const real *einb = P.ein + (long long)b * P.F;
     const int j = 32 * wy + lane;
     const bool rowv = j < n1;
@@ -386,7 +394,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
 
     // record slots (local step mod 4) and data slots (local step mod 2)
     constexpr bool STORE_E = EM == 1, GRAD = EM == 2;
-    int rs[4], rc[EM ? 4 : 1], rx[4], ry[4], riw[4];
+    int rs[4], rc[RC ? 4 : 1], rx[4], ry[4], riw[4];
     real dt[2], dp[2], dex[2], dey[2], dez[2];
     real dtf[GRAD ? 2 : 1], dev[GRAD ? 2 : 1][DW];   // gradient form: forward T - T_ref and e
     // tracker of the record read next (local step tau + 4): its virtual
@@ -401,11 +409,11 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         const int sk = v ? sk_t : sk_pad;
         rs[q] = sk;
         const int ui = nx - cnt;
-        if (EM) {
-            const int X = negx ? nx - 1 - ui : ui;
+        if (RC) {
+            const int Xc = negx ? nx - 1 - ui : ui;
             const int k = h + H * um;
             const int Z = neg2 ? n2 - 1 - k : k;
-            rc[EM ? q : 0] = v ? X + s1 * Y + s2 * Z : -1;
+            rc[RC ? q : 0] = v ? Xc + s1 * Y + s2 * Z : -1;
         }
         // wrap buffer column: read by the first warp of a pass (the value is
         // used only past the first pass), written by the last one
@@ -473,24 +481,37 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
     // specular upwind face is copied into this warp's shared-memory slot a
     // step ahead (spec_side: that face's side, -1 none, -2 several: a domain
     // edge, whose rows the step reads itself)
+    // The extra source of the next step's cell comes the same way (a cell
+    // outside the grid or void keeps the slot's previous finite values).
     int spec_side = -1;
     real *const spec_slot = sm + L.spec + (warp * 32 + lane) * DW;
-    auto fetch_spec = [&](int q) {
-        const int fb1 = rx[q], fl1 = ry[q];
-        const unsigned sb = ((unsigned)fl1 >> kSpecShift) & spec_up;
-        spec_side = -1;
-        if (sb != 0u) {
-            if ((sb & (sb - 1u)) == 0u) {
-                spec_side = __ffs((int)sb) - 1;
-                const int off = (b * P.Fs + P.sidx[face_of(fb1, fl1, spec_side)]) * P.D + d0;
-                p3_cp_async_row<DW>(spec_slot, P.spec_in + off, spec_wide);
-            } else {
-                spec_side = -2;
+    real *const xs_slot = sm + L.xs + (warp * 32 + lane) * DW;
+    if constexpr (XS) {
+#pragma unroll
+        for (int dd = 0; dd < DW; ++dd) xs_slot[dd] = real(0);
+    }
+    auto fetch_next = [&](int q) {
+        if constexpr (SPEC) {
+            const int fb1 = rx[q], fl1 = ry[q];
+            const unsigned sb = ((unsigned)fl1 >> kSpecShift) & spec_up;
+            spec_side = -1;
+            if (sb != 0u) {
+                if ((sb & (sb - 1u)) == 0u) {
+                    spec_side = __ffs((int)sb) - 1;
+                    const int off = (b * P.Fs + P.sidx[face_of(fb1, fl1, spec_side)]) * P.D + d0;
+                    p3_cp_async_row<DW>(spec_slot, P.spec_in + off, row_wide);
+                } else {
+                    spec_side = -2;
+                }
             }
+        }
+        if constexpr (XS) {
+            const int c1 = rc[q];
+            if (c1 >= 0) p3_cp_async_row<DW>(xs_slot, P.xsrc + ((long long)c1 * P.B + b) * P.D + d0, row_wide);
         }
         p3_cp_commit();
     };
-    if constexpr (SPEC) fetch_spec(0);
+    if constexpr (SPEC || XS) fetch_next(0);
 
     for (int t0 = 0; t0 < T; t0 += K) {
         const int tau0 = t0 - delta;
@@ -499,7 +520,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
             for (int k = 0; k < K; ++k) {
                 const int tau = tau0 + k;
                 // this step's cell (record read four steps ago, data two)
-                const int c = EM ? rc[EM ? k : 0] : -1;
+                const int c = RC ? rc[RC ? k : 0] : -1;
                 const int fb = rx[k], fl = ry[k], iw = riw[k];
                 const real tsv = dt[k & 1];
                 const real phv = PHI ? dp[k & 1] : real(0);
@@ -515,8 +536,8 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 // ring slot was filled by the copy issued two steps ago)
                 const int zslot = (tau & (RZ - 1)) * 32 * DW;
                 real zin[DW], yin[DW];
-                if constexpr (SPEC)
-                    p3_cp_wait<0>();   // this step's inflow slot (and the ring slots) are in
+                if constexpr (SPEC || XS)
+                    p3_cp_wait<0>();   // this step's slots (and the ring slots) are in
                 else if (wrap_rd)
                     p3_cp_wait<1>();
                 p3_load<DW>(zr_in + zslot, zin);
@@ -572,7 +593,13 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                                 if (spz >= 0) vz = P.spec_in[spz + dd] * sc;
                             }
                         }
-                        real r0 = fma(ax[dd], vx, base);
+                        real r0;
+                        if constexpr (XS) {
+                            r0 = fma(P.xscale, xs_slot[dd], base);
+                            r0 = fma(ax[dd], vx, r0);
+                        } else {
+                            r0 = fma(ax[dd], vx, base);
+                        }
                         r0 = fma(ay[dd], vy, r0);
                         r0 = fma(az[dd], vz, r0);
                         const real en = r0 * invd[dd];
@@ -605,7 +632,7 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
                 } else {
                     dirs(P3Kind<0>{});
                 }
-                if constexpr (SPEC) fetch_spec((k + 1) & 3);
+                if constexpr (SPEC || XS) fetch_next((k + 1) & 3);
                 tile_l[tau & 31] = acc;
                 if (h + 1 < H) p3_store<DW>(zr_out + zslot, old);
                 if (lane == 31) p3_store<DW>(yr_out + ((tau - 31) & (RY - 1)) * DW, old);
@@ -693,20 +720,20 @@ sweep3dp_kernel(const __grid_constant__ Sweep3DParams<real> P) {
         }
         __syncthreads();
     }
-    if (SPEC || wrap_rd) p3_cp_wait<0>();   // no copy outlives the kernel
+    if (SPEC || XS || wrap_rd) p3_cp_wait<0>();   // no copy outlives the kernel
 }
 
 template <typename real>
-size_t sweep3dp_smem_bytes(int R, int WY, int H, int dw, bool spec) {
-    return (size_t)p3_smem(R, WY, H, dw, spec).total * sizeof(real);
+size_t sweep3dp_smem_bytes(int R, int WY, int H, int dw, int x) {
+    return (size_t)p3_smem(R, WY, H, dw, x).total * sizeof(real);
 }
 
-template <typename real, int DW, bool PHI, int EM, bool ZROWS, bool SPEC>
+template <typename real, int DW, bool PHI, int EM, bool ZROWS, int X>
 cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
     const int threads = p.WY * p.H * 32;
     if (p.H < 1 || p.WY < 1 || threads > kP3MaxThreads) return cudaErrorInvalidConfiguration;
-    const size_t smem = sweep3dp_smem_bytes<real>(p.R, p.WY, p.H, DW, SPEC);
-    auto kern = sweep3dp_kernel<real, DW, PHI, EM, ZROWS, SPEC>;
+    const size_t smem = sweep3dp_smem_bytes<real>(p.R, p.WY, p.H, DW, X);
+    auto kern = sweep3dp_kernel<real, DW, PHI, EM, ZROWS, X>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -716,27 +743,33 @@ cudaError_t launch_sweep3dp_v(const Sweep3DParams<real> &p, cudaStream_t st) {
 
 // the source-profile term only in forward sweeps with a source; e only when
 // asked; the gradient form only in adjoint sweeps
-template <typename real, int DW, bool ZROWS, bool SPEC>
+template <typename real, int DW, bool ZROWS, int X>
 cudaError_t launch_sweep3dp_z(const Sweep3DParams<real> &p, cudaStream_t st) {
     const bool phi = !p.adj && p.phi != nullptr;
     if (p.grad) {
         if (!p.adj || p.store_e || !p.tfwd || !p.cb4pi || !p.e) return cudaErrorInvalidValue;
-        return launch_sweep3dp_v<real, DW, false, 2, ZROWS, SPEC>(p, st);
+        if constexpr ((X & 2) != 0) {
+            return cudaErrorInvalidValue;   // the extra source belongs to forward sweeps
+        } else {
+            return launch_sweep3dp_v<real, DW, false, 2, ZROWS, X>(p, st);
+        }
     }
     if (p.store_e)
-        return phi ? launch_sweep3dp_v<real, DW, true, 1, ZROWS, SPEC>(p, st)
-                   : launch_sweep3dp_v<real, DW, false, 1, ZROWS, SPEC>(p, st);
-    return phi ? launch_sweep3dp_v<real, DW, true, 0, ZROWS, SPEC>(p, st)
-               : launch_sweep3dp_v<real, DW, false, 0, ZROWS, SPEC>(p, st);
+        return phi ? launch_sweep3dp_v<real, DW, true, 1, ZROWS, X>(p, st)
+                   : launch_sweep3dp_v<real, DW, false, 1, ZROWS, X>(p, st);
+    return phi ? launch_sweep3dp_v<real, DW, true, 0, ZROWS, X>(p, st)
+               : launch_sweep3dp_v<real, DW, false, 0, ZROWS, X>(p, st);
 }
 
 // rows along y or along z
-// (SPEC: the variant with specular faces, a problem that has some)
-template <typename real, int DW, bool SPEC>
+// (X: the variant: bit 0 for a problem with specular faces, bit 1 for a
+// sweep with an extra source)
+template <typename real, int DW, int X>
 cudaError_t launch_sweep3dp_t(const Sweep3DParams<real> &p, cudaStream_t st) {
-    if (SPEC != (p.Fs > 0) || (SPEC && !p.spec_in)) return cudaErrorInvalidValue;
-    if (p.lane_axis == 1) return launch_sweep3dp_z<real, DW, false, SPEC>(p, st);
-    if (p.lane_axis == 2) return launch_sweep3dp_z<real, DW, true, SPEC>(p, st);
+    if (((X & 1) != 0) != (p.Fs > 0) || ((X & 1) && !p.spec_in)) return cudaErrorInvalidValue;
+    if (((X & 2) != 0) != (p.xsrc != nullptr) || ((X & 2) && p.adj)) return cudaErrorInvalidValue;
+    if (p.lane_axis == 1) return launch_sweep3dp_z<real, DW, false, X>(p, st);
+    if (p.lane_axis == 2) return launch_sweep3dp_z<real, DW, true, X>(p, st);
     return cudaErrorInvalidConfiguration;
 }
 

@@ -4,9 +4,9 @@
 
 namespace bte {
 cudaError_t launch_sweep3dp_spec_f32(const Sweep3DParams<float> &p, int dw, cudaStream_t st) {
-    if (dw == 2) return launch_sweep3dp_t<float, 2, true>(p, st);
-    if (dw == 4) return launch_sweep3dp_t<float, 4, true>(p, st);
-    if (dw == 8) return launch_sweep3dp_t<float, 8, true>(p, st);
+    if (dw == 2) return launch_sweep3dp_t<float, 2, 1>(p, st);
+    if (dw == 4) return launch_sweep3dp_t<float, 4, 1>(p, st);
+    if (dw == 8) return launch_sweep3dp_t<float, 8, 1>(p, st);
     return cudaErrorInvalidConfiguration;
 }
 }  // namespace bte

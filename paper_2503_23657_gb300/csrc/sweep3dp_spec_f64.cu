@@ -4,8 +4,8 @@
 
 namespace bte {
 cudaError_t launch_sweep3dp_spec_f64(const Sweep3DParams<double> &p, int dw, cudaStream_t st) {
-    if (dw == 2) return launch_sweep3dp_t<double, 2, true>(p, st);
-    if (dw == 4) return launch_sweep3dp_t<double, 4, true>(p, st);
+    if (dw == 2) return launch_sweep3dp_t<double, 2, 1>(p, st);
+    if (dw == 4) return launch_sweep3dp_t<double, 4, 1>(p, st);
     return cudaErrorInvalidConfiguration;
 }
 }  // namespace bte

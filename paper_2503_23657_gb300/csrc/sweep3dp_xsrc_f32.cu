@@ -1,0 +1,13 @@
+// Instantiations of the plane-pipeline 3D sweep with an extra source
+// (implicit-Euler time steps), with and without specular faces: float.
+#include "sweep3dp.cuh"
+
+namespace bte {
+cudaError_t launch_sweep3dp_xsrc_f32(const Sweep3DParams<float> &p, int dw, cudaStream_t st) {
+    const bool spec = p.Fs > 0;
+    if (dw == 2) return spec ? launch_sweep3dp_t<float, 2, 3>(p, st) : launch_sweep3dp_t<float, 2, 2>(p, st);
+    if (dw == 4) return spec ? launch_sweep3dp_t<float, 4, 3>(p, st) : launch_sweep3dp_t<float, 4, 2>(p, st);
+    if (dw == 8) return spec ? launch_sweep3dp_t<float, 8, 3>(p, st) : launch_sweep3dp_t<float, 8, 2>(p, st);
+    return cudaErrorInvalidConfiguration;
+}
+}  // namespace bte

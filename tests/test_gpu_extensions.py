@@ -126,6 +126,45 @@ def test_transient_steps(bte, name, dim, kw):
         assert rel(hd[m].cpu().numpy(), ref["T_hist"][m], act) < 1e-5
 
 
+# 3D transient steps on the plane pipeline (its extra-source variant, also
+# with specular faces): a single-pass and a several-pass grid
+PIPE_TCASES = [CASES[3], CASES[4],
+               ("3d_passes", 3, dict(n=(20, 9, 14), B=2, masked=True, diffuse=(0, 3), source=True, n_polar=2,
+                                     n_az=8)),
+               ("3d_passes_spec", 3, dict(n=(18, 11, 12), B=2, specular=(2, 5), diffuse=(3,), source=True,
+                                          two_regions=True, n_polar=2, n_az=8))]
+
+
+@pytest.mark.parametrize("name,dim,kw", PIPE_TCASES, ids=[c[0] for c in PIPE_TCASES])
+def test_transient_steps_plane_pipeline(bte, name, dim, kw):
+    p = bi.tiny(dim, **kw)
+    dt, n = 2e-11, 4
+    ref = oracle.transient(p, dt, n, tol=1e-15)
+    plan = bte.Plan(p)
+    act = p.mask > 0
+    for dw in (2, 4):
+        T = np.zeros(p.n_cells)
+        hist = np.zeros((n, p.n_cells))
+        rc, st = plan.transient(dt, n, T, T_hist=hist, precision=bte.BTE_FP64, tol=1e-15, tile_kind=3,
+                                dirs_per_lane=dw)
+        assert st["tile_kind"] == 3 and st["dirs_per_lane"] == dw
+        for m in range(n):
+            assert rel(hist[m], ref["T_hist"][m], act) < 1e-12
+    for dw in (4, 8):
+        Td = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+        hd = torch.zeros((n, p.n_cells), dtype=torch.float64, device="cuda")
+        rc, st = plan.transient(dt, n, Td, T_hist=hd, precision=bte.BTE_FP32, tol=1e-9, tile_kind=3,
+                                dirs_per_lane=dw)
+        assert st["tile_kind"] == 3
+        for m in range(n):
+            assert rel(hd[m].cpu().numpy(), ref["T_hist"][m], act) < 1e-5
+    # a steady solve on the same plan afterwards has no extra source
+    T = np.zeros(p.n_cells)
+    plan.solve(T, precision=bte.BTE_FP64, tol=0.0, max_iter=3, tile_kind=3, dirs_per_lane=4)
+    r = oracle.solve(p, max_iter=3, tol=0.0)
+    assert rel(T, r["T"], act) < 1e-12
+
+
 def test_transient_adiabatic_heating_rate(bte):
     """Energy balance of the GPU time steps: a 2D box heated uniformly with
     one isothermal face far from the source; the stored energy rises by the
