@@ -52,7 +52,13 @@ WORKLOADS = {
     "finfet_specular": (lambda bi: bi.finfet_specular_3d(),
                         "finfet3d_specbase_160x80x64_B15_D128_fwd+adj_eps1e-6", 1e-6, False, True),
     "ensemble": (lambda bi: bi.ensemble_2d(), "ensemble2d_256x(32..160)^2_B15_D64_fwd_eps1e-6", 1e-6, False, False),
+    "hotspot_transient": (lambda bi: bi.hotspot_3d(), "hotspot3d_64^3_B15_D128_transient_10x10ps_eps1e-6", 1e-6,
+                          False, False),
 }
+# implicit-Euler workloads: time step (s) and steps per bench step, each step
+# solved to eps_T < tol from the previous one (the paper's Conclusion names
+# transient transport as its extension)
+TRANSIENT = {"hotspot_transient": (1e-11, 10)}
 L2_FLUSH_BYTES = 512 << 20
 TIME_EVERY = 8   # sweeps timed with CUDA events: one in every TIME_EVERY iterations
 
@@ -127,16 +133,16 @@ class ClockSampler:
 # proportion to the bands: every band is an independent set of CTAs).
 NCU_TRAFFIC = {
     # FinFET 160x80x64, 15 bands, forward launch, full size (one-pass capture),
-    # mean of two launches: 1205.96 MB read + 2192.89 MB written (two 8-warp
+    # mean of two launches: 1203.2 MB read + 2193.8 MB written (two 8-warp
     # CTAs per SM: the per-CTA wrap planes of all 240 resident CTAs and the
     # partial sums leave L2)
-    ("sweep3dp_kernel<float, 8, 1, 0, 1, 0>", "3:8:8:2:4:2", "5cc464bb0506"): 3398849664,
+    ("sweep3dp_kernel<float, 8, 1, 0, 1, 0>", "3:8:8:2:4:2", "4ca13341a79c"): 3396967040,
     # 64^3 hotspot, 15 bands, forward launch, full size, mean of two launches:
-    # 66.1 MB read + 251.6 MB written
-    ("sweep3dp_kernel<float, 8, 1, 0, 0, 0>", "3:8:8:2:4:1", "5cc464bb0506"): 317668096,
+    # 66.5 MB read + 251.7 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 0, 0>", "3:8:8:2:4:1", "4ca13341a79c"): 318187904,
     # FinFET with specular base side faces, forward launch, full size, mean
-    # of two launches: 1328.86 MB read + 2366.81 MB written
-    ("sweep3dp_kernel<float, 8, 1, 0, 1, 1>", "3:8:8:2:4:2", "5cc464bb0506"): 3695668864,
+    # of two launches: 1328.4 MB read + 2366.5 MB written
+    ("sweep3dp_kernel<float, 8, 1, 0, 1, 1>", "3:8:8:2:4:2", "4ca13341a79c"): 3694982656,
 }
 KERNEL_SOURCES = {
     "sweep3dp_kernel": ["sweep3dp.cuh", "bte_internal.cuh", "finalize.cuh", "tma.cuh"],
@@ -211,7 +217,17 @@ def oracle_sample(p, seconds, rate=4e7):
     return q, 1, f"the first {nb} of {p.B} bands"
 
 
-def cpu_baseline_oracle(probs, iters=0):
+def oracle_iterations(q, k, transient=None):
+    """k source iterations of the oracle on problem q: of the steady problem,
+    or of the first implicit-Euler step (transient = (dt, steps))."""
+    import oracle
+    if transient:
+        oracle.transient(q, transient[0], 1, max_iter=k, tol=0.0)
+    else:
+        oracle.solve(q, max_iter=k, tol=0.0)
+
+
+def cpu_baseline_oracle(probs, iters=0, transient=None):
     """The FP64 oracle (single thread) on a bounded sample of the workload:
     forward source iterations of (the first instances of) it, restricted to
     its first bands where one full iteration would take too long."""
@@ -223,7 +239,7 @@ def cpu_baseline_oracle(probs, iters=0):
     for p in probs:
         q, k, what = oracle_sample(p, 15.0)
         k = iters or k
-        oracle.solve(q, max_iter=k, tol=0.0)
+        oracle_iterations(q, k, transient)
         units += k * q.n_active * q.B * q.D
         if time.perf_counter() - t0 > 20.0:
             break
@@ -245,11 +261,12 @@ def run_reference(args, ws, rank):
     probs = probs if isinstance(probs, list) else [probs]
     p, k_iter, what = oracle_sample(probs[0], 3.0)
     units_step = k_iter * p.n_active * p.B * p.D
+    tr = TRANSIENT.get(args.workload)
     for _ in range(args.warmup):
-        oracle.solve(p, max_iter=1, tol=0.0)
+        oracle_iterations(p, 1, tr)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.solve(p, max_iter=k_iter, tol=0.0)
+        oracle_iterations(p, k_iter, tr)
     dt = time.perf_counter() - t0
     val = units_step * args.steps / dt
     line = {
@@ -343,7 +360,7 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         p0 = probs[0]
-        cpu = cpu_baseline_oracle(probs, args.cpu_iters)
+        cpu = cpu_baseline_oracle(probs, args.cpu_iters, TRANSIENT.get(args.workload))
 
     import __graft_entry__
     __graft_entry__.build()
@@ -353,6 +370,8 @@ def main():
                with_adj=with_adj, cpu=cpu)
     if args.workload == "ensemble":
         line = run_ensemble(probs, ctx)
+    elif args.workload in TRANSIENT:
+        line = run_transient(probs[0], ctx)
     else:
         line = run_single(probs[0], ctx)
         if args.workload == "finfet" and ws == 1 and not args.no_ensemble:
@@ -544,6 +563,82 @@ def run_single(p, ctx):
                 "h2d_bytes_per_step": (2 if ctx["with_adj"] else 1) * 8 * p.n_cells,
                 "d2h_bytes_per_step": 8 * p.n_cells + (8 * (p.B + 7) if ctx["with_adj"] else 0)},
         "gpu_launches": launches, "clocks": clk})
+    return line
+
+
+def run_transient(p, ctx):
+    """Implicit-Euler time steps (bte_transient): a bench step is `steps` time
+    steps of length dt from the equilibrium at 300 K, each solved to eps_T <
+    tol (FP32 sweeps, FP64 temperatures); the value counts the source
+    iterations of all of them."""
+    torch, m, args, tol = ctx["torch"], ctx["m"], ctx["args"], ctx["tol"]
+    dt, nsteps = TRANSIENT[args.workload]
+    plan = m.Plan(p)
+    sp = torch.cuda.current_stream().cuda_stream
+    T = torch.zeros(p.n_cells, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    per_update = p.n_active * p.B * p.D
+    tile_kind, tile_dw, tile_cw, tile_st, tile_wz, tile_ax = (
+        int(x) for x in (args.tile + ":0:0:0:0:0:0").split(":")[:6])
+    topt = dict(tile_kind=tile_kind, dirs_per_lane=tile_dw, warps_z=tile_wz, lane_axis=tile_ax)
+
+    def step():
+        rc, st = plan.transient(dt, nsteps, T, precision=m.BTE_FP32, tol=tol, stream=sp, **topt)
+        return st
+
+    plan.set_sweep_timing(TIME_EVERY)
+    times, res, clk = timed_steps(ctx, step, flush)
+    plan.set_sweep_timing(0)
+    units = sum(st["iterations"] for st in res) * per_update
+    t_total = sum(times) / 1e3
+    units_all, t_max = aggregate(ctx, units, t_total)
+    last = res[-1]
+    # the sweep launches of the last time step's solve, event-timed
+    sweep_ms = last["sweep_seconds"] / max(last["sweep_launches"], 1) * 1e3
+    dw = last["dirs_per_lane"]
+    tile = f"{last['tile_kind']}:{dw}:{last['dirs_per_cta']}:{2 - last['source_staged']}"
+    if last["warps_z"]:
+        tile += f":{last['warps_z']}:{last['lane_axis']}"
+    if last["tile_kind"] == 3 and p.dim == 3:
+        spec = int(any(int(t) == 2 for t in p.bc_type[:6]))
+        kernel = f"sweep3dp_kernel<float, {dw}, {0 if p.phi is None else 1}, 0, {int(last['lane_axis'] == 2)}, " \
+                 f"{2 + spec}>"
+    else:
+        kernel = f"sweep_kernel<float, {dw}, lz, {int(p.dim == 3)}, 0>"
+    roofline = roofline_object(kernel, tile, sweep_ms, per_update, p.B, p.D, {
+        "sweep_launches_timed": last["sweep_launches"],
+        "extra_source_bytes_per_update": 4.0,
+        "note": "the extra source (e of the previous step over dt) is read once per update (4 B), beyond the "
+                "steady sweep's algorithmic bytes"})
+    extra = {}
+    if not args.no_fp64:
+        T64 = torch.zeros_like(T)
+        rc, s64 = plan.transient(dt, nsteps, T64, precision=m.BTE_FP64, tol=tol, stream=sp)
+        extra = {"fp64_iterations": s64["iterations"],
+                 "T_fp32_vs_fp64_rel": float((T - T64).abs().max() / T64.abs().max())}
+    # end to end with host buffers
+    T_h = torch.zeros(p.n_cells, dtype=torch.float64).pin_memory()
+    e2e_units, e2e_t = 0, 0.0
+    for i in range(max(2, min(args.steps, 4))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = plan.transient(dt, nsteps, T_h, precision=m.BTE_FP32, tol=tol, stream=sp, **topt)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_units += st["iterations"] * per_update
+            e2e_t += t1 - t0
+    config = {"workload": ctx["name"], "cells": p.n_cells, "solid_cells": p.n_active, "bands": p.B,
+              "directions": p.D, "tol_eps_T": tol, "dt_s": dt, "time_steps_per_step": nsteps,
+              "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)",
+              "parallelism": "replicas" if ctx["ws"] > 1 else "single", "tile": tile}
+    line = base_line(ctx, units_all / t_max, t_max, "f32", config)
+    line.update({"iterations_per_step": statistics.median(st["iterations"] for st in res)})
+    line.update(extra)
+    line.update({
+        "roofline": roofline, "cpu_baseline": ctx["cpu"],
+        "e2e": {"value": e2e_units / e2e_t if e2e_t > 0 else None, "unit": "updates/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * p.n_cells},
+        "gpu_launches": sum(st["kernel_launches"] for st in res), "clocks": clk})
     return line
 
 
