@@ -1,5 +1,9 @@
 // Instantiations of the plane-pipeline 3D sweep with an extra source
-// (implicit-Euler time steps), with and without specular faces: float.
+// (implicit-Euler time steps, the extension the paper's Conclusion
+// announces), with and without specular faces: float.  The forward sweeps of
+// a time step add xscale * xsrc[c][b][d] (e of the previous step over dt) to
+// every direction's right-hand side; the kernel copies the next step's row of
+// DW values into shared memory a step ahead.
 #include "sweep3dp.cuh"
 
 namespace bte {
