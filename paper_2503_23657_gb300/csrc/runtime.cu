@@ -740,8 +740,10 @@ int ensure_workspace(bte_plan *p, Workspace<real> &ws) {
         CK(p, ws.ein[i].ensure(sizeof(real) * B * F));
         CK(p, ws.T[i].ensure(sizeof(double) * N));
     }
+    // (16 values of padding: the plane pipeline copies rows of whole subsets,
+    // which may reach past the last face's row when a subset is not full)
     if (p->Fs > 0)
-        for (int i = 0; i < 2; ++i) CK(p, ws.spec[i].ensure(sizeof(real) * B * (size_t)p->Fs * p->D));
+        for (int i = 0; i < 2; ++i) CK(p, ws.spec[i].ensure(sizeof(real) * (B * (size_t)p->Fs * p->D + 16)));
     // the partial sets are sized by the tiles in use (ensure_subsets)
     std::vector<real> ph(N + 16, (real)0);
     for (size_t c = 0; c < N && !p->phi.empty(); ++c) ph[c] = (real)p->phi[c];
@@ -1561,7 +1563,7 @@ int adjoint_t(bte_plan *p, const double *dJ_dT, double tol, int max_iter, double
         CK(p, ws.theta[i].ensure(sizeof(double) * N));
     }
     if (p->Fs > 0) {
-        for (int i = 0; i < 2; ++i) CK(p, ws.mspec[i].ensure(sizeof(real) * (size_t)B * p->Fs * p->D));
+        for (int i = 0; i < 2; ++i) CK(p, ws.mspec[i].ensure(sizeof(real) * ((size_t)B * p->Fs * p->D + 16)));
     }
     CK(p, ws.gpart.ensure(sizeof(real) * Spad * B * N));
     if (g_L) CK(p, ws.glpart.ensure(sizeof(real) * 3 * Spad * B * N));
