@@ -1265,7 +1265,13 @@ int solve_t(bte_plan *p, const bte_solve_opts *o, double *T_out, double *q_out, 
     // e of the final iterate is always regenerated on the device (outputs and
     // the adjoint read it)
     const size_t NBD = (size_t)p->N * p->B * p->D;
-    CK(p, ws.e.ensure(sizeof(real) * NBD));
+    {
+        // zeros where no sweep writes (void cells): the e of a transient step
+        // is the next step's extra source, read for every cell
+        const void *e0 = ws.e.p;
+        CK(p, ws.e.ensure(sizeof(real) * NBD));
+        if (ws.e.p != e0) CK(p, cudaMemsetAsync(ws.e.p, 0, sizeof(real) * NBD, stream));
+    }
     if (p->xmode == 2) {
         CK(p, ws.del.ensure(sizeof(real) * 3 * NBD));
         CK(p, ws.corr.ensure(sizeof(real) * NBD));
