@@ -15,7 +15,9 @@ library.  The GPU parity tests compare libbte against these files:
 
     python tests/golden/make_goldens.py [hotspot] [finfet] [finfet_s2]
 
-Each job runs in a process of its own (spawned, so no state is shared).
+Each job runs in a process of its own (spawned, so no state is shared); the
+half-resolution FinFET's truth run is a job of its own that runs next to
+its solve and hands the probe temperatures over through a temporary file.
 The full-size jobs hold e and its previous iterate in FP64 (about 8 GB for
 the hotspot, 25 GB for the FinFET).
 """
@@ -62,7 +64,12 @@ def job_finfet():
     return f"finfet k=20: {time.time() - t0:.0f} s"
 
 
-def job_finfet_s2():
+TRUTH_S2 = os.path.join(HERE, "_finfet_s2_truth.npz")   # passed between the two half-resolution jobs
+
+
+def job_finfet_s2_truth():
+    """The truth run of the half-resolution FinFET (its probe temperatures),
+    in a process of its own next to the solve of job_finfet_s2."""
     _setup()
     import bte_inputs as bi
     import oracle
@@ -71,8 +78,27 @@ def job_finfet_s2():
     truth = bi.finfet_3d(scale=2, tau_b_scale=1.2, T_sub=301.0, Q_amp=0.8e19)
     rt = oracle.solve(truth, max_iter=100000, tol=1e-8)
     probes = np.asarray(p.probes)
-    T_obs = rt["T"][probes]
+    tmp = TRUTH_S2 + ".tmp.npz"
+    np.savez(tmp, T_obs=rt["T"][probes], iters=rt["iters"])
+    os.replace(tmp, TRUTH_S2)
+    return f"finfet s2 truth ({rt['iters']} it): {time.time() - t0:.0f} s"
+
+
+def job_finfet_s2():
+    _setup()
+    import bte_inputs as bi
+    import oracle
+    t0 = time.time()
+    p = bi.finfet_3d(scale=2)
+    probes = np.asarray(p.probes)
     r = oracle.solve(p, max_iter=100000, tol=1e-8)
+    # the truth run's probe temperatures (job_finfet_s2_truth)
+    while not os.path.exists(TRUTH_S2):
+        time.sleep(10.0)
+    with np.load(TRUTH_S2) as tr:
+        T_obs = tr["T_obs"].copy()
+        rt = {"iters": int(tr["iters"])}
+    os.remove(TRUTH_S2)
     g = np.zeros(p.n_cells)
     np.add.at(g, probes, r["T"][probes] - T_obs)
     a = oracle.adjoint(p, r["e"], r["T"], g, max_iter=100000, tol=1e-10)
@@ -82,7 +108,8 @@ def job_finfet_s2():
     return f"finfet s2 converged ({r['iters']} it) + adjoint ({a['iters']} it): {time.time() - t0:.0f} s"
 
 
-JOBS = {"hotspot": job_hotspot, "finfet": job_finfet, "finfet_s2": job_finfet_s2}
+JOBS = {"hotspot": job_hotspot, "finfet": job_finfet, "finfet_s2": job_finfet_s2,
+        "finfet_s2_truth": job_finfet_s2_truth}
 
 
 def _run(name):
@@ -90,7 +117,9 @@ def _run(name):
 
 
 if __name__ == "__main__":
-    names = sys.argv[1:] or list(JOBS)
+    names = sys.argv[1:] or ["hotspot", "finfet", "finfet_s2"]
+    if "finfet_s2" in names and "finfet_s2_truth" not in names:
+        names.append("finfet_s2_truth")   # its truth run, in parallel
     ctx = mp.get_context("spawn")
     with ctx.Pool(len(names)) as pool:
         for msg in pool.imap_unordered(_run, names):
